@@ -1,0 +1,509 @@
+#!/usr/bin/env python
+"""Benchmark: batched FP64 analytical Jacobians per second on B300 (pyJac method, arXiv:1605.03262).
+
+One step = one pass of the whole hot path over one batch: thermodynamics, rate coefficients and
+rates of every reaction, the per-reaction Jacobian terms, the species gathers and the dense
+(N+1)^2 Jacobian of every state, written to HBM (one kernel launch through the C ABI).
+
+Workload of the headline line: synthetic 53-species, 325-reaction model (5 elements; 70 %
+Arrhenius, 15 % third-body, 12 % Troe/Lindemann falloff, 3 % SRI; all reversible through the
+equilibrium constant) and 65,536 states (T uniform 800-2500 K, P log-uniform 1-50 atm,
+Y ~ Dirichlet(0.5)), FP64. The same line carries the other three model sizes under "per_config".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU runs are launched with torch.distributed.run; each rank evaluates its own batch of the
+same size (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1605_03262_b300 import synth  # noqa: E402
+
+METRIC = "Jacobians/sec (FP64, 1 B300) per mechanism size vs roofline; p50/p99 serving latency"
+UNIT = "Jacobians/s"
+HEADLINE_CFG = 1
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic FP64 work per Jacobian (the roofline numerator)
+
+def _distinct(side):
+    d = {}
+    for s, nu in side:
+        d[s] = d.get(s, 0) + nu
+    return d
+
+
+def work_model(model) -> dict:
+    """FP64 operations the method needs per Jacobian, by kind.
+
+    arith: FP64 add/mul/FMA operations of the formulation (each one FP64 pipe issue); exp, log,
+    div: calls of the transcendental functions and divisions. The counts follow the evaluation
+    order of the kernels (reaction terms once per reaction, gathers through the static lists, one
+    FMA per dense entry) and are a property of the model, not of a measurement."""
+    N, R = model.n_species, model.n_reactions
+    arith, n_exp, n_log, n_div = 24.0, 0.0, 2.0, 4.0          # per state: ln T, ln P, 1/T, 1/sum, 1/rho, 1/cp
+    arith += N * (33 + 3 + 2 + 5 + 5)                       # thermo, reductions, [X], gather finish, energy sums
+    pairs = contributions = colent = 0
+    nnz = set()
+    for r in model.reactions:
+        reac, prod = _distinct(r.reac), _distinct(r.prod)
+        nsp = len(reac) + len(prod)
+        net = {}
+        for s, nu in reac.items():
+            net[s] = net.get(s, 0) - nu
+        for s, nu in prod.items():
+            net[s] = net.get(s, 0) + nu
+        net = [s for s, v in net.items() if v != 0]
+        slots = set(reac) | set(prod)
+        if r.kind in (synth.KIND_THIRD_BODY, synth.KIND_FALLOFF, synth.KIND_CHEM):
+            if r.tb_mode == synth.TB_SPECIES:
+                slots.add(r.tb_species)
+            else:
+                slots |= {s for s, a in r.eff if a != 1.0}
+        a = 4 + 4 * nsp + 20 + nsp + 2 * len(slots)         # ln k, products/partials, R, q, theta, sigma, a, dH, b'
+        if r.rev_mode == synth.REV_KC:
+            a += 4 * nsp + 3
+            n_exp += 1
+        elif r.rev_mode == synth.REV_EXPLICIT:
+            a += 4
+            n_exp += 1
+        if r.kind in (synth.KIND_ELEMENTARY, synth.KIND_THIRD_BODY):
+            n_exp += 1
+            if r.kind == synth.KIND_THIRD_BODY:
+                a += 2 * len(r.eff) + 3
+        elif r.kind in (synth.KIND_FALLOFF, synth.KIND_CHEM):
+            a += 8 + 2 * len(r.eff) + 14                      # k0, kinf, Pr, c, phi, psi, dc/dT
+            n_exp += 2
+            n_div += 1
+            if r.ftype == synth.F_TROE:
+                a += 30
+                n_exp += 3 + (1 if r.troe_has_T2 else 0)
+                n_log += 2
+                n_div += 2
+            elif r.ftype == synth.F_SRI:
+                a += 20
+                n_exp += 3
+                n_log += 2
+                n_div += 2
+            if r.kind == synth.KIND_CHEM:
+                n_div += 1
+        elif r.kind == synth.KIND_PLOG:
+            a += 12
+            n_exp += 1
+            n_div += 1
+        else:
+            nt, npc = r.cheb_shape
+            a += 2 * nt * npc + 6 * (nt + npc) + 8
+            n_exp += 1
+        arith += a
+        pairs += len(net)
+        colent += len(slots)
+        for k in net:
+            for l in slots:
+                nnz.add((k, l))
+                contributions += 1
+    arith += 3 * pairs + 2 * contributions + 2 * len(nnz) + colent + N
+    arith += N * (N - 1) + 4 * (N - 1) + 6                  # dense species block, energy row, J00
+    return {"arith": arith, "exp": n_exp, "log": n_log, "div": n_div, "nnz": len(nnz),
+            "contributions": contributions}
+
+
+def dfma_equivalents(work: dict, ratios: dict) -> float:
+    """FP64-pipe time per Jacobian in units of one FMA issue: arithmetic ops plus each call weighted
+    by its measured throughput relative to FMA."""
+    return work["arith"] + work["exp"] * ratios["exp"] + work["log"] * ratios["log"] + work["div"] * ratios["div"]
+
+
+# ---------------------------------------------------------------------------------------------
+# measurement helpers
+
+def calibrate():
+    """Measured FP64 FMA peak, exp/log/div cost in FMA issues, store-only bandwidth."""
+    from paper_1605_03262_b300 import build as pjbuild
+    lib = ctypes.CDLL(pjbuild.build_calib())
+    lib.pjc_fp64_fma_tflops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.pjc_fp64_func_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.pjc_store_gbs.argtypes = [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]
+    tf = ctypes.c_double()
+    best_tf = 0.0
+    for _ in range(3):
+        if lib.pjc_fp64_fma_tflops(4096, ctypes.byref(tf)) == 0:
+            best_tf = max(best_tf, tf.value)
+    fma_rate = best_tf * 1e12 / 2.0
+    ratios = {}
+    for op, name in ((0, "exp"), (1, "log"), (2, "div")):
+        r = ctypes.c_double()
+        best = 0.0
+        for _ in range(2):
+            if lib.pjc_fp64_func_rate(op, 256, ctypes.byref(r)) == 0:
+                best = max(best, r.value)
+        ratios[name] = fma_rate / best if best > 0 else float("nan")
+    g = ctypes.c_double()
+    gbs = 0.0
+    for _ in range(2):
+        if lib.pjc_store_gbs(4 << 30, ctypes.byref(g)) == 0:
+            gbs = max(gbs, g.value)
+    return {"fp64_tflops": best_tf, "ratios": ratios, "store_gbs": gbs}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload_name(cfg: int) -> str:
+    c = synth.CONFIGS[cfg]
+    return "%s: %d states, synthetic %d-species %d-reaction model" % (c["name"], c["n_states"], c["n_species"],
+                                                                     c["n_reactions"])
+
+
+# ---------------------------------------------------------------------------------------------
+# the CUDA arm
+
+def time_device(g, Td, Pd, Yd, J, steps, warmup, flush):
+    """Per-step CUDA-event time of the Jacobian launch, L2 flushed before every step."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        g.eval_jacobian(Td, Pd, Yd, out=J, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        g.eval_jacobian(Td, Pd, Yd, out=J, stream=stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def run_config(cfg, steps, warmup, rank, cal, n_states=None):
+    import torch
+    import paper_1605_03262_b300 as pj
+    model = synth.config_model(cfg)
+    T, P, Y = synth.config_states(cfg, n_states, seed_offset=1000 + rank)
+    n, N = Y.shape
+    g = pj.Model(synth.to_bytes(model))
+    Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+    J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    ms = time_device(g, Td, Pd, Yd, J, steps, warmup, flush)
+    work = work_model(model)
+    dfe = dfma_equivalents(work, cal["ratios"])
+    ms_mean = float(np.mean(ms))
+    achieved = 2.0 * dfe * n / (ms_mean * 1e-3) / 1e12
+    launch = g.get_launch()
+    res = {
+        "n_states": n, "n_species": N, "n_reactions": model.n_reactions, "ms_per_step": ms_mean,
+        "ms_min": float(np.min(ms)), "jacobians_per_s": n / (ms_mean * 1e-3),
+        "fp64_dfma_equiv_per_jacobian": dfe, "work": work,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": cal["fp64_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / cal["fp64_tflops"] if cal["fp64_tflops"] else None},
+        "hbm_write_gbs": n * (N + 1) ** 2 * 8 / (ms_mean * 1e-3) / 1e9,
+        "launch": {"warps_per_state": launch[0], "states_per_cta": launch[1], "ctas_per_sm": launch[2]},
+    }
+    del J, flush
+    return res, (g, model, T, P, Y, Td, Pd, Yd)
+
+
+def e2e_host(g, T, P, Y, steps):
+    """End to end through the C ABI on pinned host buffers (copies inside the timed region)."""
+    import torch
+    n, N = Y.shape
+    Th, Ph, Yh = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (T, P, Y))
+    Jh = torch.empty((n, N + 1, N + 1), dtype=torch.float64).pin_memory()
+    g.eval_jacobian_host(Th, Ph, Yh, Jh)      # warm-up (allocates staging)
+    times = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.eval_jacobian_host(Th, Ph, Yh, Jh)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    return {"value": n / t, "unit": UNIT, "h2d_bytes_per_step": int(n * (N + 2) * 8),
+            "d2h_bytes_per_step": int(n * (N + 1) ** 2 * 8), "s_per_step": t}
+
+
+def cpu_baseline(cfg, budget_s=12.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same workload."""
+    import oracle
+    model = synth.config_model(cfg)
+    om = oracle.load_model(synth.to_bytes(model))
+    cores = oracle.max_threads()
+    T, P, Y = synth.config_states(cfg, 4 * cores)
+    t0 = time.perf_counter()
+    om.jacobian(T, P, Y)
+    per = (time.perf_counter() - t0) / len(T)
+    ns = int(max(cores, min(synth.CONFIGS[cfg]["n_states"], budget_s / max(per, 1e-9))))
+    T, P, Y = synth.config_states(cfg, ns)
+    t0 = time.perf_counter()
+    om.jacobian(T, P, Y)
+    dt = time.perf_counter() - t0
+    return {"value": ns / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the %d states of %s, oracle FP64 C with OpenMP over states"
+                      % (ns, synth.CONFIGS[cfg]["n_states"], synth.CONFIGS[cfg]["name"]),
+            "seconds": dt}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    cal = calibrate()
+    gpu_index = torch.cuda.current_device()
+    _barrier(ws)
+    with ClockSampler(gpu_index) as clk:
+        res, ctx = run_config(HEADLINE_CFG, args.steps, args.warmup, rank, cal)
+    clocks = clk.summary()
+    g, model, T, P, Y = ctx[:5]
+    torch.cuda.synchronize()
+    _barrier(ws)
+    ms_max = _max_over_ranks(ws, res["ms_per_step"])
+    n_total = _sum_over_ranks(ws, float(res["n_states"]))
+    value = n_total / (ms_max * 1e-3)
+    e2e = e2e_host(g, T, P, Y, max(1, min(args.steps, 3))) if not args.no_e2e else None
+    if e2e is not None and ws > 1:
+        e2e["value"] = _sum_over_ranks(ws, e2e["value"])
+    per_config = {}
+    if not args.headline_only:
+        for cfg in (0, 2, 3):
+            r, _ = run_config(cfg, max(3, args.steps // 2), args.warmup, rank, cal)
+            per_config[synth.CONFIGS[cfg]["name"]] = {k: r[k] for k in ("n_states", "ms_per_step", "jacobians_per_s",
+                                                                        "roofline", "hbm_write_gbs", "launch",
+                                                                        "fp64_dfma_equiv_per_jacobian")}
+            torch.cuda.empty_cache()
+    per_config[synth.CONFIGS[HEADLINE_CFG]["name"]] = {k: res[k] for k in ("n_states", "ms_per_step",
+                                                                            "jacobians_per_s", "roofline",
+                                                                            "hbm_write_gbs", "launch",
+                                                                            "fp64_dfma_equiv_per_jacobian")}
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    roof = dict(res["roofline"])
+    roof["traffic"] = None
+    roof["peak_source"] = "measured FP64 FMA throughput on this GPU in this run (libpjcalib)"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(HEADLINE_CFG), "model": synth.CONFIGS[HEADLINE_CFG]["name"],
+                   "n_states_per_gpu": res["n_states"], "n_species": res["n_species"],
+                   "n_reactions": res["n_reactions"], "parallelism": "states sharded over %d GPU(s)" % ws,
+                   "l2": "flushed before every timed step (256 MB write)", "launch": res["launch"]},
+        "roofline": roof,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+        "calibration": cal,
+        "per_config": per_config,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(HEADLINE_CFG)
+    print(json.dumps(line))
+    sys.stdout.flush()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------------
+# the reference arm: the oracle, timed on the host cores
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cfg = HEADLINE_CFG
+    model = synth.config_model(cfg)
+    om = oracle.load_model(synth.to_bytes(model))
+    cores = oracle.max_threads()
+    T, P, Y = synth.config_states(cfg, 2 * cores)
+    t0 = time.perf_counter()
+    om.jacobian(T, P, Y)
+    per = (time.perf_counter() - t0) / len(T)
+    budget = 150.0 / max(1, args.steps + args.warmup)        # whole run within a few minutes
+    ns = int(max(cores, min(synth.CONFIGS[cfg]["n_states"], budget / max(per, 1e-9))))
+    T, P, Y = synth.config_states(cfg, ns)
+    for _ in range(args.warmup):
+        om.jacobian(T, P, Y)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        om.jacobian(T, P, Y)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = ns / t
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": workload_name(cfg), "model": synth.CONFIGS[cfg]["name"],
+                   "sample_states_per_step": ns},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "first %d of the %d states per step, oracle FP64 C with OpenMP over states"
+                                   % (ns, synth.CONFIGS[cfg]["n_states"])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_profile_case(spec: str, warmup: int):
+    """--profile CFG:N -- a small case for ncu: warm-up launches, then one Jacobian launch of the
+    first N states of configuration CFG (inputs larger than L2 once N is a few thousand)."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    cfg, n = (int(x) for x in spec.split(":"))
+    torch.cuda.set_device(0)
+    model = synth.config_model(cfg)
+    T, P, Y = synth.config_states(cfg, n, seed_offset=1000)
+    g = pj.Model(synth.to_bytes(model))
+    Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+    J = torch.empty((n, model.n_species + 1, model.n_species + 1), dtype=torch.float64, device="cuda")
+    for _ in range(warmup + 1):
+        g.eval_jacobian(Td, Pd, Yd, out=J)
+    torch.cuda.synchronize()
+    print("profile case done: cfg %d, %d states, launch %s" % (cfg, n, g.get_launch()))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other model sizes")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, metavar="CFG:N", help="one small profiling case (for ncu)")
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args.profile, args.warmup)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * pyjac_b300: batched FP64 chemical source terms and analytical constant-pressure Jacobian on
+ * NVIDIA B300 (sm_103a). C ABI of libpyjacb300.so.
+ *
+ * The operations are those of Niemeyer, Curtis & Sung, "pyJac: analytical Jacobian generator for
+ * chemical kinetics" (arXiv:1605.03262):
+ *   - source terms f = dPhi/dt of the constant-pressure composition vector, Eqs. e:ode and e:dTdt
+ *     (Section 2.1), with thermodynamics of Section 2.2 (Eqs. e:cpk, e:hk, e:sk) and reaction rates
+ *     of Section 2.3 (Arrhenius Eq. e:arrhenius, third-body, Lindemann/Troe/SRI falloff and
+ *     chemically activated reactions Eq. e:rxn_pressure, PLOG Eq. e:plog, Chebyshev Eq. e:cheb,
+ *     reverse rates via the equilibrium constant Eq. e:kri or explicit Arrhenius parameters);
+ *   - the analytical Jacobian J = df/dPhi of Section 3 (Eqs. e:jac_spec, e:jac_dydt, e:jac_dydy,
+ *     e:jac_dt), evaluated in the reuse order of Section 4 (Algorithm 2).
+ *
+ * Conventions for every evaluation entry point:
+ *   - Units are SI: T in K, P in Pa, mass fractions Y dimensionless, time in s.
+ *   - A state is (T, P, Y_1..Y_N). All N mass fractions are read and used as given; Y_N is not
+ *     recomputed from the others.
+ *   - dydt: N+1 doubles per state, {dT/dt, dY_1/dt, ..., dY_N/dt}.
+ *   - jac: (N+1)^2 doubles per state, row-major. Row/column 0 is temperature, rows/columns 1..N are
+ *     species 1..N. Column j (1 <= j <= N-1) is the derivative along Y_j with Y_N = 1 - sum of the
+ *     others (Eq. e:y_nsp), i.e. d/dY_j - d/dY_N at fixed T and P. Column N is identically zero
+ *     because Y_N is not a state variable; row N is the last species (the paper's placeholder row).
+ *   - Batched arrays are state-major: state s of Y starts at Y + s*ldy, of dydt at dydt + s*ldd,
+ *     of jac at jac + s*ldj (leading dimensions in doubles).
+ *   - Pointers of the plain entry points are device pointers on the model's device; they must be
+ *     8-byte aligned. The caller owns every state and output buffer.
+ *   - Evaluation is asynchronous on the given CUDA stream (cudaStream_t passed as void*; NULL = the
+ *     legacy default stream). Arguments are checked on the host before any launch. There is no
+ *     device-side validation of physical inputs: non-finite or non-positive inputs give non-finite
+ *     outputs.
+ *   - Results are deterministic: a state's outputs are bitwise identical whatever the batch it is
+ *     evaluated in and whatever launch shape is configured.
+ *
+ * Status codes: every int-returning function returns PJ_OK or a negative PJ_E* code; the calling
+ * thread's last error message is available from pj_last_error().
+ */
+#ifndef PYJAC_B300_H
+#define PYJAC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PJ_API __attribute__((visibility("default")))
+#else
+#define PJ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PJ_OK 0
+#define PJ_EINVAL (-1)       /* invalid argument (null pointer, bad size, stride or alignment) */
+#define PJ_EFORMAT (-2)      /* malformed or truncated model buffer */
+#define PJ_ECUDA (-3)        /* a CUDA runtime call failed; the message names it */
+#define PJ_ENOMEM (-4)       /* host or device allocation failed */
+#define PJ_ETIMEOUT (-5)     /* a bounded device wait gave up */
+#define PJ_EUNSUPPORTED (-6) /* valid model outside what the kernels support (sizes, slots) */
+
+typedef struct pj_mech pj_mech;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+PJ_API int pj_version(void);
+
+/* Message of the last failed call on the calling thread ("" if none). The pointer stays valid
+ * until the next call on the same thread. */
+PJ_API const char *pj_last_error(void);
+
+/*
+ * Load a kinetic model from the binary model format (magic "PYJACMEC", version 1; species with
+ * molecular weights and two-range NASA7 coefficients, reactions with stoichiometry, pressure
+ * dependence, reversibility, third-body efficiencies, falloff, PLOG and Chebyshev parameters; all
+ * SI). The model's device image is built on the current CUDA device; buf is only read during the
+ * call. On success *out owns that device memory until pj_mech_free. Errors: PJ_EINVAL (null
+ * arguments), PJ_EFORMAT (malformed buffer), PJ_EUNSUPPORTED (more than 4 distinct species on one
+ * side of a reaction or a stoichiometric coefficient above 4), PJ_ECUDA / PJ_ENOMEM.
+ */
+PJ_API int pj_mech_load(const void *buf, size_t len, pj_mech **out);
+
+/* pj_mech_load on the contents of a file. */
+PJ_API int pj_mech_load_file(const char *path, pj_mech **out);
+
+/* Release a model and its device memory. NULL is ignored. The caller must make sure no evaluation
+ * that uses the model is still running on any stream. */
+PJ_API void pj_mech_free(pj_mech *m);
+
+/* Sizes of a loaded model: number of species N, reactions, bytes of its device image. Any output
+ * pointer may be NULL. */
+PJ_API int pj_mech_info(const pj_mech *m, int *n_species, int *n_reactions, size_t *dev_bytes);
+
+/*
+ * Source terms f (Eqs. e:ode, e:dTdt) for n states. T[n], P[n], Y[n][ldy >= N] in, dydt[n][ldd >= N+1]
+ * out; device pointers; asynchronous on stream. n == 0 is a no-op. Errors: PJ_EINVAL (null model or
+ * pointer, n < 0, ldy < N, ldd < N+1, misaligned or host pointer), PJ_ECUDA (launch failure).
+ */
+PJ_API int pj_eval_dydt(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
+                 double *dydt, int64_t ldd, void *stream);
+
+/*
+ * Analytical Jacobian (Section 3, evaluated in the Section 4 reuse order) for n states, and
+ * optionally the source terms. T[n], P[n], Y[n][ldy >= N] in; jac[n][ldj >= (N+1)^2] out; dydt may
+ * be NULL, else dydt[n][ldd >= N+1] out. Device pointers; asynchronous on stream. Errors as
+ * pj_eval_dydt, plus PJ_EINVAL for ldj < (N+1)^2 and PJ_EUNSUPPORTED when one state's working set
+ * does not fit in shared memory.
+ */
+PJ_API int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
+                     int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream);
+
+/*
+ * End-to-end variant of pj_eval_jacobian on HOST buffers (pinned host memory gives full copy
+ * bandwidth; pageable memory works but is slower). The states are processed in chunks of
+ * chunk_states (<= 0: the library picks); each chunk is copied to the device, evaluated and copied
+ * back, with copies and kernels of consecutive chunks overlapped on two internal streams. Device
+ * staging buffers are allocated on first use and kept with the model until pj_mech_free. The call
+ * is synchronous: it returns after every output is in host memory. Same argument rules as
+ * pj_eval_jacobian except that the pointers are host pointers.
+ */
+PJ_API int pj_eval_jacobian_host(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
+                          int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, int64_t chunk_states);
+
+/* Launch shape of the evaluation kernels for one model (which: 0 = Jacobian, 1 = source terms).
+ * warps_per_state in {1, 2, 4, 8, 16}: warps that cooperate on one state; states_per_cta: states
+ * a CTA evaluates concurrently (CTA size = warps_per_state * 32 * states_per_cta <= 512; at most
+ * 15 when warps_per_state > 1); ctas_per_sm: resident CTAs the grid is sized for. Results do not
+ * depend on the shape. pj_set_launch returns PJ_EINVAL for shapes outside these limits or whose
+ * shared memory exceeds the device's per-CTA limit. */
+typedef struct {
+    int warps_per_state;
+    int states_per_cta;
+    int ctas_per_sm;
+} pj_launch;
+
+PJ_API int pj_set_launch(pj_mech *m, int which, const pj_launch *cfg);
+PJ_API int pj_get_launch(const pj_mech *m, int which, pj_launch *cfg);
+
+/* Shared memory (bytes) one CTA of the given shape needs for this model, or PJ_EINVAL. */
+PJ_API int pj_launch_smem_bytes(const pj_mech *m, int which, const pj_launch *cfg, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYJAC_B300_H */

@@ -40,30 +40,47 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            vp, i64, dp, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
-            lib.pjo_mech_load.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(vp)]
-            lib.pjo_mech_load.restype = i32
-            lib.pjo_mech_free.argtypes = [vp]
-            lib.pjo_mech_free.restype = None
-            lib.pjo_mech_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
-            lib.pjo_mech_info.restype = i32
-            lib.pjo_set_threads.argtypes = [i32]
-            lib.pjo_set_threads.restype = None
-            lib.pjo_max_threads.argtypes = []
-            lib.pjo_max_threads.restype = i32
-            lib.pjo_eval_dydt.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64]
-            lib.pjo_eval_dydt.restype = i32
-            lib.pjo_eval_jacobian.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp, dp, i64, dp]
-            lib.pjo_eval_jacobian.restype = i32
-            lib.pjo_jacobian_complex_step.argtypes = [vp, i64, dp, dp, dp, i64, ctypes.c_double, dp, i64]
-            lib.pjo_jacobian_complex_step.restype = i32
-            lib.pjo_reaction_rates.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
-            lib.pjo_reaction_rates.restype = i32
-            lib.pjo_species_thermo.argtypes = [vp, ctypes.c_double, dp, dp, dp, dp]
-            lib.pjo_species_thermo.restype = i32
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def compile_variant(src_dir: str, out_so: str) -> str:
+    """Compile the oracle sources found in src_dir (same file names) into out_so. Used by the tests
+    that plant mistakes in a copy of the oracle to show that its pins catch them."""
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+           "-o", out_so, os.path.join(src_dir, "pyjac_oracle.c"), "-lm"]
+    subprocess.run(cmd, check=True, cwd=src_dir, capture_output=True)
+    return out_so
+
+
+def load_variant(so_path: str):
+    """ctypes handle of an oracle library compiled by compile_variant (for OracleModel(lib=...))."""
+    return _bind(ctypes.CDLL(os.path.abspath(so_path)))
+
+
+def _bind(lib):
+    vp, i64, dp, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    lib.pjo_mech_load.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.pjo_mech_load.restype = i32
+    lib.pjo_mech_free.argtypes = [vp]
+    lib.pjo_mech_free.restype = None
+    lib.pjo_mech_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.pjo_mech_info.restype = i32
+    lib.pjo_set_threads.argtypes = [i32]
+    lib.pjo_set_threads.restype = None
+    lib.pjo_max_threads.argtypes = []
+    lib.pjo_max_threads.restype = i32
+    lib.pjo_eval_dydt.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64]
+    lib.pjo_eval_dydt.restype = i32
+    lib.pjo_eval_jacobian.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp, dp, i64, dp]
+    lib.pjo_eval_jacobian.restype = i32
+    lib.pjo_jacobian_complex_step.argtypes = [vp, i64, dp, dp, dp, i64, ctypes.c_double, dp, i64]
+    lib.pjo_jacobian_complex_step.restype = i32
+    lib.pjo_reaction_rates.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
+    lib.pjo_reaction_rates.restype = i32
+    lib.pjo_species_thermo.argtypes = [vp, ctypes.c_double, dp, dp, dp, dp]
+    lib.pjo_species_thermo.restype = i32
+    return lib
 
 
 def _ptr(a):
@@ -88,8 +105,9 @@ def max_threads() -> int:
 class OracleModel:
     """A kinetic model loaded into the oracle from the binary model format."""
 
-    def __init__(self, blob: bytes):
-        lib = _load()
+    def __init__(self, blob: bytes, lib=None):
+        lib = lib if lib is not None else _load()
+        self._lib = lib
         self._blob = bytes(blob)
         self._buf = ctypes.create_string_buffer(self._blob, len(self._blob))
         h = ctypes.c_void_p()
@@ -103,8 +121,8 @@ class OracleModel:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
-            _lib.pjo_mech_free(h)
+        if h is not None and getattr(self, "_lib", None) is not None:
+            self._lib.pjo_mech_free(h)
             self._h = None
 
     # -- batch evaluations -------------------------------------------------------------------
@@ -113,7 +131,7 @@ class OracleModel:
         T, P, Y = _f64(T).ravel(), _f64(P).ravel(), _f64(Y)
         n, N = Y.shape
         out = np.empty((n, N + 1))
-        rc = _load().pjo_eval_dydt(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, _ptr(out), N + 1)
+        rc = self._lib.pjo_eval_dydt(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, _ptr(out), N + 1)
         if rc:
             raise RuntimeError("oracle dydt failed (%d)" % rc)
         return out
@@ -129,7 +147,7 @@ class OracleModel:
         f = np.empty((n, N + 1))
         Js = np.empty_like(J) if with_scale else None
         fs = np.empty_like(f) if with_scale else None
-        rc = _load().pjo_eval_jacobian(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, _ptr(J), (N + 1) ** 2,
+        rc = self._lib.pjo_eval_jacobian(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, _ptr(J), (N + 1) ** 2,
                                        _ptr(Js), _ptr(f), N + 1, _ptr(fs))
         if rc:
             raise RuntimeError("oracle jacobian failed (%d)" % rc)
@@ -139,7 +157,7 @@ class OracleModel:
         T, P, Y = _f64(T).ravel(), _f64(P).ravel(), _f64(Y)
         n, N = Y.shape
         J = np.empty((n, N + 1, N + 1))
-        rc = _load().pjo_jacobian_complex_step(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, h, _ptr(J),
+        rc = self._lib.pjo_jacobian_complex_step(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, h, _ptr(J),
                                                (N + 1) ** 2)
         if rc:
             raise RuntimeError("oracle complex step failed (%d)" % rc)
@@ -150,7 +168,7 @@ class OracleModel:
         Y = _f64(Y).ravel()
         R = self.n_reactions
         kf, kr, c, Rf, Rr, q = (np.empty(R) for _ in range(6))
-        rc = _load().pjo_reaction_rates(self._h, float(T), float(P), _ptr(Y), _ptr(kf), _ptr(kr), _ptr(c),
+        rc = self._lib.pjo_reaction_rates(self._h, float(T), float(P), _ptr(Y), _ptr(kf), _ptr(kr), _ptr(c),
                                         _ptr(Rf), _ptr(Rr), _ptr(q))
         if rc:
             raise RuntimeError("oracle rates failed (%d)" % rc)
@@ -159,11 +177,11 @@ class OracleModel:
     def species_thermo(self, T: float):
         N = self.n_species
         cpR, HRT, SR, B = (np.empty(N) for _ in range(4))
-        rc = _load().pjo_species_thermo(self._h, float(T), _ptr(cpR), _ptr(HRT), _ptr(SR), _ptr(B))
+        rc = self._lib.pjo_species_thermo(self._h, float(T), _ptr(cpR), _ptr(HRT), _ptr(SR), _ptr(B))
         if rc:
             raise RuntimeError("oracle thermo failed (%d)" % rc)
         return dict(cpR=cpR, HRT=HRT, SR=SR, B=B)
 
 
-def load_model(blob: bytes) -> OracleModel:
-    return OracleModel(blob)
+def load_model(blob: bytes, lib=None) -> OracleModel:
+    return OracleModel(blob, lib=lib)

@@ -1,0 +1,239 @@
+"""B300-native batched FP64 chemical source terms and analytical Jacobian (pyJac, arXiv:1605.03262).
+
+Thin Python binding of the C ABI in ``include/pyjac_b300.h`` (``libpyjacb300.so``, built for
+sm_103a by :mod:`paper_1605_03262_b300.build`). PyTorch provides device memory and streams; every
+step of the computation runs in the library's CUDA kernels. There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises.
+
+Main entry points:
+    Model(blob)                         load a kinetic model (binary model format, see synth)
+    Model.eval_dydt(T, P, Y)            source terms, (n, N+1) CUDA tensor
+    Model.eval_jacobian(T, P, Y)        Jacobian (n, N+1, N+1) [and dydt] CUDA tensors
+    Model.eval_jacobian_host(...)       same on host (ideally pinned) buffers, copies inside
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Tuple
+
+__all__ = ["Model", "LibraryError", "library", "load_library", "PJ_STATUS", "LIB_PATH"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpyjacb300.so")
+
+PJ_STATUS = {0: "PJ_OK", -1: "PJ_EINVAL", -2: "PJ_EFORMAT", -3: "PJ_ECUDA", -4: "PJ_ENOMEM", -5: "PJ_ETIMEOUT",
+             -6: "PJ_EUNSUPPORTED"}
+
+
+class LibraryError(RuntimeError):
+    """A C-ABI call returned a negative status."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__("%s (%d): %s" % (PJ_STATUS.get(status, "?"), status, message))
+        self.status = status
+
+
+class pj_launch(ctypes.Structure):
+    _fields_ = [("warps_per_state", ctypes.c_int), ("states_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpyjacb300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError("libpyjacb300.so not found at %s; build it with "
+                              "`python -m paper_1605_03262_b300.build`" % path)
+        lib = ctypes.CDLL(path)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+        sig = {
+            "pj_version": ([], i32),
+            "pj_last_error": ([], ctypes.c_char_p),
+            "pj_mech_load": ([vp, sz, ctypes.POINTER(vp)], i32),
+            "pj_mech_load_file": ([ctypes.c_char_p, ctypes.POINTER(vp)], i32),
+            "pj_mech_free": ([vp], None),
+            "pj_mech_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(sz)], i32),
+            "pj_eval_dydt": ([vp, i64, vp, vp, vp, i64, vp, i64, vp], i32),
+            "pj_eval_jacobian": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
+            "pj_eval_jacobian_host": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, i64], i32),
+            "pj_set_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
+            "pj_get_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
+            "pj_launch_smem_bytes": ([vp, i32, ctypes.POINTER(pj_launch), ctypes.POINTER(sz)], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def library():
+    return load_library()
+
+
+def _check(status: int):
+    if status != 0:
+        msg = library().pj_last_error()
+        raise LibraryError(status, msg.decode() if msg else "")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _as_f64_cuda(x, name, device):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(x, dtype=torch.float64)
+    if x.dtype != torch.float64:
+        raise TypeError("%s must be float64" % name)
+    if x.device.type != "cuda":
+        x = x.to(device)
+    return x
+
+
+class Model:
+    """A kinetic model resident on the current CUDA device."""
+
+    def __init__(self, blob: bytes):
+        lib = library()
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(lib.pj_mech_load(buf, len(blob), ctypes.byref(h)))
+        self._h = h
+        ns, nr, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(lib.pj_mech_info(h, ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(nb)))
+        self.n_species, self.n_reactions, self.device_bytes = ns.value, nr.value, nb.value
+        torch = _torch()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def from_file(cls, path: str) -> "Model":
+        with open(path, "rb") as f:
+            return cls(f.read())
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            library().pj_mech_free(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -- launch shape ------------------------------------------------------------------------
+    def get_launch(self, which: str = "jacobian") -> Tuple[int, int, int]:
+        c = pj_launch()
+        _check(library().pj_get_launch(self._h, 0 if which == "jacobian" else 1, ctypes.byref(c)))
+        return c.warps_per_state, c.states_per_cta, c.ctas_per_sm
+
+    def set_launch(self, warps_per_state: int, states_per_cta: int, ctas_per_sm: int = 1,
+                   which: str = "jacobian") -> None:
+        c = pj_launch(warps_per_state, states_per_cta, ctas_per_sm)
+        _check(library().pj_set_launch(self._h, 0 if which == "jacobian" else 1, ctypes.byref(c)))
+
+    def launch_smem_bytes(self, warps_per_state: int, states_per_cta: int, ctas_per_sm: int = 1,
+                          which: str = "jacobian") -> int:
+        c = pj_launch(warps_per_state, states_per_cta, ctas_per_sm)
+        b = ctypes.c_size_t()
+        _check(library().pj_launch_smem_bytes(self._h, 0 if which == "jacobian" else 1, ctypes.byref(c),
+                                              ctypes.byref(b)))
+        return b.value
+
+    # -- evaluation on device tensors ----------------------------------------------------------
+    def _inputs(self, T, P, Y):
+        T = _as_f64_cuda(T, "T", self.device).contiguous().reshape(-1)
+        P = _as_f64_cuda(P, "P", self.device).contiguous().reshape(-1)
+        Y = _as_f64_cuda(Y, "Y", self.device)
+        if Y.dim() != 2 or Y.shape[1] < self.n_species or Y.stride(1) != 1:
+            raise ValueError("Y must be (n, >= N) with unit stride along species")
+        n = Y.shape[0]
+        if T.shape[0] != n or P.shape[0] != n:
+            raise ValueError("T, P and Y must describe the same number of states")
+        return T, P, Y, n
+
+    def eval_dydt(self, T, P, Y, out=None, stream=None):
+        """Source terms {dT/dt, dY_1/dt..dY_N/dt} for every state: (n, N+1) float64 CUDA tensor."""
+        torch = _torch()
+        T, P, Y, n = self._inputs(T, P, Y)
+        N = self.n_species
+        if out is None:
+            out = torch.empty((n, N + 1), dtype=torch.float64, device=self.device)
+        _check(library().pj_eval_dydt(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out),
+                                      out.stride(0), _stream_handle(stream)))
+        return out
+
+    def eval_jacobian(self, T, P, Y, out=None, dydt: bool = False, dydt_out=None, stream=None):
+        """Analytical Jacobian (n, N+1, N+1) [, dydt (n, N+1)] as float64 CUDA tensors."""
+        torch = _torch()
+        T, P, Y, n = self._inputs(T, P, Y)
+        N = self.n_species
+        if out is None:
+            out = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device=self.device)
+        ldj = out.stride(0)
+        f = None
+        if dydt or dydt_out is not None:
+            f = dydt_out if dydt_out is not None else torch.empty((n, N + 1), dtype=torch.float64, device=self.device)
+        _check(library().pj_eval_jacobian(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out), ldj,
+                                          _ptr(f), f.stride(0) if f is not None else 0, _stream_handle(stream)))
+        return (out, f) if f is not None else out
+
+    # -- evaluation on host buffers (end to end) -----------------------------------------------
+    def eval_jacobian_host(self, T, P, Y, jac, dydt=None, chunk_states: int = 0):
+        """Jacobian of host (CPU) float64 tensors/arrays into host output ``jac`` (n, N+1, N+1).
+
+        Copies in and out happen inside the call (pinned memory gives full bandwidth)."""
+        n = Y.shape[0]
+        N = self.n_species
+        _check(library().pj_eval_jacobian_host(
+            self._h, n, _host_ptr(T), _host_ptr(P), _host_ptr(Y), _host_stride0(Y), _host_ptr(jac),
+            _host_stride0(jac), _host_ptr(dydt) if dydt is not None else None,
+            _host_stride0(dydt) if dydt is not None else 0, int(chunk_states)))
+        return jac
+
+
+def _host_ptr(a):
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if a.device.type != "cpu" or a.dtype != torch.float64:
+            raise TypeError("host buffers must be float64 CPU tensors")
+        return a.data_ptr()
+    import numpy as np
+    if a.dtype != np.float64:
+        raise TypeError("host buffers must be float64")
+    return a.ctypes.data
+
+
+def _host_stride0(a):
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        return a.stride(0)
+    return a.strides[0] // 8

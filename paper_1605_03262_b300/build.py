@@ -1,0 +1,63 @@
+"""Build of libpyjacb300.so (sm_103a) with nvcc, in the package directory."""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC_DIR = os.path.join(HERE, "csrc")
+SOURCES = ["pj_model.cu", "pj_kernels.cu", "pj_api.cu", "pj_host.cu"]
+HEADERS = ["pj_internal.h"]
+LIB = os.path.join(HERE, "libpyjacb300.so")
+CALIB_SRC = "pj_calib.cu"
+CALIB_LIB = os.path.join(HERE, "libpjcalib.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
+         "-Xcompiler", "-fvisibility=hidden", "-Xcompiler", "-Wall"]
+
+
+def sources():
+    return [os.path.join(SRC_DIR, s) for s in SOURCES]
+
+
+def _inputs():
+    return sources() + [os.path.join(SRC_DIR, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pyjac_b300.h")]
+
+
+def needs_build() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(f) > t for f in _inputs())
+
+
+def build_calib(force: bool = False) -> str:
+    """Measurement kernels for the benchmark's roofline denominators (libpjcalib.so)."""
+    src = os.path.join(SRC_DIR, CALIB_SRC)
+    if not force and os.path.exists(CALIB_LIB) and os.path.getmtime(CALIB_LIB) >= os.path.getmtime(src):
+        return CALIB_LIB
+    tmp = CALIB_LIB + ".tmp.%d" % os.getpid()
+    cmd = [os.environ.get("NVCC", "nvcc")] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                                                     "-Xcompiler", "-fvisibility=hidden", "-o", tmp, src]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, CALIB_LIB)
+    return CALIB_LIB
+
+
+def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    build_calib(force=force)
+    if not force and not needs_build():
+        return LIB
+    nvcc = os.environ.get("NVCC", "nvcc")
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    cmd = [nvcc] + ARCH + FLAGS + list(extra) + ["-I", os.path.join(ROOT, "include"), "-o", tmp] + sources()
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    extra = sys.argv[1:]
+    print(build(force=True, verbose=True, extra=extra))

@@ -1,0 +1,339 @@
+// C ABI of libpyjacb300.so: argument checking, model upload and kernel launch (include/pyjac_b300.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <iterator>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/pyjac_b300.h"
+#include "pj_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(PJ_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+struct DeviceProps {
+    int sms = 0;
+    int smem_optin = 0;
+};
+
+DeviceProps device_props(int dev) {
+    static std::mutex mu;
+    static std::vector<DeviceProps> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    if (int(cache.size()) <= dev) cache.resize(dev + 1);
+    if (cache[dev].sms == 0) {
+        cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&cache[dev].smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return cache[dev];
+}
+
+int rows_per_chunk(int N) { return std::max(1, std::min(4, 256 / (N + 1))); }
+
+size_t smem_bytes(const pj_mech *m, bool jac, const pj::LaunchCfg &c) {
+    pj::Scratch sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, rows_per_chunk(m->N));
+    return (size_t(pj::shared_const_doubles(m->N)) + size_t(sc.total) * c.groups) * sizeof(double);
+}
+
+bool valid_shape(const pj::LaunchCfg &c) {
+    const int w = c.wps;
+    if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16)) return false;
+    if (c.groups < 1 || c.ctas_per_sm < 1 || c.ctas_per_sm > 32) return false;
+    if (w * 32 * c.groups > 512) return false;
+    if (w > 1 && c.groups > 15) return false;   // named barriers 1..15
+    return true;
+}
+
+// Largest number of states per CTA that fits shared memory, for a given warps-per-state.
+pj::LaunchCfg default_cfg(const pj_mech *m, bool jac, int wps) {
+    DeviceProps dp = device_props(m->device);
+    pj::LaunchCfg c;
+    c.wps = wps;
+    c.ctas_per_sm = 1;
+    int gmax = std::min(wps > 1 ? 15 : 16, 512 / (32 * wps));
+    c.groups = 0;
+    for (int g = gmax; g >= 1; --g) {
+        pj::LaunchCfg t = c;
+        t.groups = g;
+        if (smem_bytes(m, jac, t) <= size_t(dp.smem_optin)) {
+            c.groups = g;
+            break;
+        }
+    }
+    return c;
+}
+
+pj::LaunchCfg pick_default(const pj_mech *m, bool jac) {
+    const int N = m->N;
+    int wps = jac ? (N <= 64 ? 1 : N <= 160 ? 2 : N <= 320 ? 4 : 8) : (N <= 128 ? 1 : 2);
+    pj::LaunchCfg c = default_cfg(m, jac, wps);
+    while (c.groups == 0 && wps < 16) {   // grow the group until one state fits
+        wps *= 2;
+        c = default_cfg(m, jac, wps);
+    }
+    return c;
+}
+
+bool is_aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
+int check_device_ptr(const void *p, int dev, const char *name) {
+    if (!p) return fail(PJ_EINVAL, std::string(name) + " is NULL");
+    if (!is_aligned8(p)) return fail(PJ_EINVAL, std::string(name) + " is not 8-byte aligned");
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PJ_EINVAL, std::string(name) + " is not a CUDA-accessible pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(PJ_EINVAL, std::string(name) + " is not a device pointer");
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return fail(PJ_EINVAL, std::string(name) + " lives on another device than the model");
+    return PJ_OK;
+}
+
+template <class T>
+size_t push(std::vector<char> &blob, const std::vector<T> &v) {
+    size_t off = (blob.size() + 255) & ~size_t(255);
+    blob.resize(off + v.size() * sizeof(T) + (v.empty() ? sizeof(T) : 0));
+    if (!v.empty()) std::memcpy(blob.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+}
+
+int launch(const pj_mech *m, bool jac, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
+           double *jacp, int64_t ldj, double *dydt, int64_t ldd, cudaStream_t stream) {
+    const pj::LaunchCfg &c = jac ? m->jac_cfg : m->dydt_cfg;
+    if (c.groups < 1)
+        return fail(PJ_EUNSUPPORTED, "one state's working set does not fit in shared memory for this model");
+    pj::KParams p{};
+    p.m = m->dev;
+    p.sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, rows_per_chunk(m->N));
+    p.n = n;
+    p.T = T;
+    p.P = P;
+    p.Y = Y;
+    p.ldy = ldy;
+    p.jac = jacp;
+    p.ldj = ldj;
+    p.dydt = dydt;
+    p.ldd = ldd;
+    p.groups = c.groups;
+    p.shared_const = pj::shared_const_doubles(m->N);
+    DeviceProps dp = device_props(m->device);
+    long long need = (n + c.groups - 1) / c.groups;
+    int blocks = int(std::min<long long>(need, (long long)dp.sms * c.ctas_per_sm));
+    size_t smem = smem_bytes(m, jac, c);
+    cudaError_t e = pj::launch_eval(p, jac, c.wps, blocks, smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return PJ_OK;
+}
+
+int check_model_device(const pj_mech *m) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != m->device) return fail(PJ_EINVAL, "the current CUDA device is not the model's device");
+    return PJ_OK;
+}
+
+}  // namespace
+
+int pj::set_error(int code, const std::string &msg) { return fail(code, msg); }
+
+extern "C" {
+
+int pj_version(void) { return 10000; }
+
+const char *pj_last_error(void) { return g_err.c_str(); }
+
+int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
+    if (!buf || !out) return fail(PJ_EINVAL, "pj_mech_load: null argument");
+    *out = nullptr;
+    pj::HostImage im;
+    try {
+        im = pj::build_image(buf, len);
+    } catch (const pj::FormatError &ex) {
+        return fail(PJ_EFORMAT, std::string("model format: ") + ex.what());
+    } catch (const pj::Unsupported &ex) {
+        return fail(PJ_EUNSUPPORTED, std::string("unsupported model: ") + ex.what());
+    } catch (const std::bad_alloc &) {
+        return fail(PJ_ENOMEM, "host allocation failed while building the model image");
+    }
+    std::vector<char> blob;
+    size_t o_rx = push(blob, im.rx), o_par = push(blob, im.par), o_effsp = push(blob, im.eff_sp),
+           o_effeps = push(blob, im.eff_eps), o_sinfo = push(blob, im.slot_info), o_seps = push(blob, im.slot_eps),
+           o_th = push(blob, im.thermo), o_tmid = push(blob, im.Tmid), o_W = push(blob, im.W),
+           o_iW = push(blob, im.invW), o_D = push(blob, im.Delta), o_spp = push(blob, im.sp_ptr),
+           o_spr = push(blob, im.sp_rxn), o_spn = push(blob, im.sp_nu), o_cp = push(blob, im.col_ptr),
+           o_cs = push(blob, im.col_slot), o_cr = push(blob, im.col_rxn), o_rp = push(blob, im.row_ptr),
+           o_nc = push(blob, im.nnz_col), o_ncp = push(blob, im.nnz_cptr), o_nw = push(blob, im.nnz_wr),
+           o_cns = push(blob, im.con_slot), o_cnn = push(blob, im.con_nu), o_cN = push(blob, im.colN_nnz);
+    pj_mech *m = new (std::nothrow) pj_mech();
+    if (!m) return fail(PJ_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    e = cudaMalloc(&m->dev_blob, blob.size());
+    if (e != cudaSuccess) {
+        delete m;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PJ_ENOMEM : PJ_ECUDA,
+                    std::string("cudaMalloc of the model image: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(m->dev_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->dev_blob);
+        delete m;
+        return cuda_fail(e, "cudaMemcpy of the model image");
+    }
+    char *b = static_cast<char *>(m->dev_blob);
+    pj::DevModel &d = m->dev;
+    d.N = im.N;
+    d.R = im.R;
+    d.nslot = int(im.slot_info.size());
+    d.nnz = int(im.nnz_col.size());
+    d.ncontrib = int(im.con_slot.size());
+    d.ncolent = int(im.col_slot.size());
+    d.rx = reinterpret_cast<const pj::RxnDev *>(b + o_rx);
+    d.par = reinterpret_cast<const double *>(b + o_par);
+    d.eff_sp = reinterpret_cast<const int *>(b + o_effsp);
+    d.eff_eps = reinterpret_cast<const double *>(b + o_effeps);
+    d.slot_info = reinterpret_cast<const int *>(b + o_sinfo);
+    d.slot_eps = reinterpret_cast<const double *>(b + o_seps);
+    d.thermo = reinterpret_cast<const double *>(b + o_th);
+    d.Tmid = reinterpret_cast<const double *>(b + o_tmid);
+    d.W = reinterpret_cast<const double *>(b + o_W);
+    d.invW = reinterpret_cast<const double *>(b + o_iW);
+    d.Delta = reinterpret_cast<const double *>(b + o_D);
+    d.sp_ptr = reinterpret_cast<const int *>(b + o_spp);
+    d.sp_rxn = reinterpret_cast<const int *>(b + o_spr);
+    d.sp_nu = reinterpret_cast<const double *>(b + o_spn);
+    d.col_ptr = reinterpret_cast<const int *>(b + o_cp);
+    d.col_slot = reinterpret_cast<const int *>(b + o_cs);
+    d.col_rxn = reinterpret_cast<const int *>(b + o_cr);
+    d.row_ptr = reinterpret_cast<const int *>(b + o_rp);
+    d.nnz_col = reinterpret_cast<const int *>(b + o_nc);
+    d.nnz_cptr = reinterpret_cast<const int *>(b + o_ncp);
+    d.nnz_wr = reinterpret_cast<const double *>(b + o_nw);
+    d.con_slot = reinterpret_cast<const int *>(b + o_cns);
+    d.con_nu = reinterpret_cast<const double *>(b + o_cnn);
+    d.colN_nnz = reinterpret_cast<const int *>(b + o_cN);
+    d.lnPatmR = std::log(pj::kPatm / pj::kR);
+    m->N = im.N;
+    m->R = im.R;
+    m->NE = im.NE;
+    m->dev_bytes = blob.size();
+    m->perm = im.perm;
+    m->jac_cfg = pick_default(m, true);
+    m->dydt_cfg = pick_default(m, false);
+    *out = m;
+    return PJ_OK;
+}
+
+int pj_mech_load_file(const char *path, pj_mech **out) {
+    if (!path || !out) return fail(PJ_EINVAL, "pj_mech_load_file: null argument");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return fail(PJ_EINVAL, std::string("cannot open ") + path);
+    std::vector<char> buf((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
+    return pj_mech_load(buf.data(), buf.size(), out);
+}
+
+void pj_mech_free(pj_mech *m) {
+    if (!m) return;
+    if (m->dev_blob) cudaFree(m->dev_blob);
+    pj_host_staging_release(m);
+    delete m;
+}
+
+int pj_mech_info(const pj_mech *m, int *n_species, int *n_reactions, size_t *dev_bytes) {
+    if (!m) return fail(PJ_EINVAL, "pj_mech_info: null model");
+    if (n_species) *n_species = m->N;
+    if (n_reactions) *n_reactions = m->R;
+    if (dev_bytes) *dev_bytes = m->dev_bytes;
+    return PJ_OK;
+}
+
+int pj_eval_dydt(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
+                 double *dydt, int64_t ldd, void *stream) {
+    if (!m) return fail(PJ_EINVAL, "pj_eval_dydt: null model");
+    if (n < 0) return fail(PJ_EINVAL, "pj_eval_dydt: n < 0");
+    if (ldy < m->N) return fail(PJ_EINVAL, "pj_eval_dydt: ldy < number of species");
+    if (ldd < m->N + 1) return fail(PJ_EINVAL, "pj_eval_dydt: ldd < number of species + 1");
+    if (n == 0) return PJ_OK;
+    int rc;
+    if ((rc = check_model_device(m)) || (rc = check_device_ptr(T, m->device, "T")) ||
+        (rc = check_device_ptr(P, m->device, "P")) || (rc = check_device_ptr(Y, m->device, "Y")) ||
+        (rc = check_device_ptr(dydt, m->device, "dydt")))
+        return rc;
+    return launch(m, false, n, T, P, Y, ldy, nullptr, 0, dydt, ldd, static_cast<cudaStream_t>(stream));
+}
+
+int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
+                     int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream) {
+    if (!m) return fail(PJ_EINVAL, "pj_eval_jacobian: null model");
+    if (n < 0) return fail(PJ_EINVAL, "pj_eval_jacobian: n < 0");
+    if (ldy < m->N) return fail(PJ_EINVAL, "pj_eval_jacobian: ldy < number of species");
+    const int64_t nn = int64_t(m->N + 1) * (m->N + 1);
+    if (ldj < nn) return fail(PJ_EINVAL, "pj_eval_jacobian: ldj < (number of species + 1)^2");
+    if (dydt && ldd < m->N + 1) return fail(PJ_EINVAL, "pj_eval_jacobian: ldd < number of species + 1");
+    if (n == 0) return PJ_OK;
+    int rc;
+    if ((rc = check_model_device(m)) || (rc = check_device_ptr(T, m->device, "T")) ||
+        (rc = check_device_ptr(P, m->device, "P")) || (rc = check_device_ptr(Y, m->device, "Y")) ||
+        (rc = check_device_ptr(jac, m->device, "jac")))
+        return rc;
+    if (dydt && (rc = check_device_ptr(dydt, m->device, "dydt"))) return rc;
+    return launch(m, true, n, T, P, Y, ldy, jac, ldj, dydt, ldd, static_cast<cudaStream_t>(stream));
+}
+
+int pj_set_launch(pj_mech *m, int which, const pj_launch *cfg) {
+    if (!m || !cfg || (which != 0 && which != 1)) return fail(PJ_EINVAL, "pj_set_launch: bad argument");
+    pj::LaunchCfg c;
+    c.wps = cfg->warps_per_state;
+    c.groups = cfg->states_per_cta;
+    c.ctas_per_sm = cfg->ctas_per_sm;
+    if (!valid_shape(c)) return fail(PJ_EINVAL, "pj_set_launch: launch shape outside the supported limits");
+    if (smem_bytes(m, which == 0, c) > size_t(device_props(m->device).smem_optin))
+        return fail(PJ_EINVAL, "pj_set_launch: shape needs more shared memory than one CTA can have");
+    (which == 0 ? m->jac_cfg : m->dydt_cfg) = c;
+    return PJ_OK;
+}
+
+int pj_get_launch(const pj_mech *m, int which, pj_launch *cfg) {
+    if (!m || !cfg || (which != 0 && which != 1)) return fail(PJ_EINVAL, "pj_get_launch: bad argument");
+    const pj::LaunchCfg &c = which == 0 ? m->jac_cfg : m->dydt_cfg;
+    cfg->warps_per_state = c.wps;
+    cfg->states_per_cta = c.groups;
+    cfg->ctas_per_sm = c.ctas_per_sm;
+    return PJ_OK;
+}
+
+int pj_launch_smem_bytes(const pj_mech *m, int which, const pj_launch *cfg, size_t *bytes) {
+    if (!m || !cfg || !bytes || (which != 0 && which != 1)) return fail(PJ_EINVAL, "pj_launch_smem_bytes: bad argument");
+    pj::LaunchCfg c;
+    c.wps = cfg->warps_per_state;
+    c.groups = cfg->states_per_cta;
+    c.ctas_per_sm = cfg->ctas_per_sm;
+    if (!valid_shape(c)) return fail(PJ_EINVAL, "pj_launch_smem_bytes: launch shape outside the supported limits");
+    *bytes = smem_bytes(m, which == 0, c);
+    return PJ_OK;
+}
+
+}  // extern "C"

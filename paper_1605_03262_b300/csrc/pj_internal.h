@@ -1,0 +1,141 @@
+// Internal definitions of the B300 library: the device image of a kinetic model and the kernel
+// parameter block. Not part of the public C ABI (include/pyjac_b300.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace pj {
+
+constexpr double kR = 8.31446261815324;   // J/(mol K)
+constexpr double kPatm = 101325.0;        // Pa
+constexpr int kMaxSlots = 4;              // distinct species per side of a reaction
+constexpr int kMaxNu = 4;                 // stoichiometric coefficient bound
+constexpr int kThermoStride = 36;         // doubles per species: two ranges x 18
+
+enum Kind : uint8_t { kElem = 0, kThird = 1, kFalloff = 2, kChem = 3, kPlog = 4, kCheb = 5 };
+enum Rev : uint8_t { kIrrev = 0, kRevKc = 1, kRevExplicit = 2 };
+enum FType : uint8_t { kLindemann = 0, kTroe = 1, kSri = 2 };
+enum TbMode : uint8_t { kTbNone = 0, kTbMix = 1, kTbSpecies = 2 };
+enum KForm : uint8_t { kKfGeneral = 0, kKfConst = 1, kKfIntPow = 2 };
+
+// One reaction of the device image (class-sorted order). 64 bytes.
+struct alignas(16) RxnDev {
+    uint8_t kind, rev, ftype, tbmode;
+    uint8_t nr, np, kform, flags;        // flags bit0: Troe T** term present
+    int16_t rsp[kMaxSlots];              // reactant species (distinct)
+    int16_t psp[kMaxSlots];              // product species (distinct)
+    int8_t rnu[kMaxSlots];
+    int8_t pnu[kMaxSlots];
+    int16_t tbsp;                        // third-body species m (tbmode == kTbSpecies)
+    int16_t neff;                        // number of non-unity efficiencies (tbmode == kTbMix)
+    int32_t eff_off;                     // offset into eff_sp / eff_eps
+    int32_t par_off;                     // offset into the parameter pool
+    int32_t slot_off;                    // first b-slot of this reaction
+    int32_t nslot;                       // number of b-slots (species whose column this reaction touches)
+    int32_t kpow;                        // integer temperature exponent (kform == kKfIntPow)
+    int32_t pad;
+};
+static_assert(sizeof(RxnDev) == 64, "RxnDev layout");
+
+// Pointers into one device allocation holding a model's image.
+struct DevModel {
+    int N, R, nslot, nnz, ncontrib, ncolent;
+    const RxnDev *rx;
+    const double *par;        // parameter pool
+    const int *eff_sp;
+    const double *eff_eps;    // alpha - 1
+    const int *slot_info;     // species | (reactant slot + 1) << 16 | (product slot + 1) << 24
+    const double *slot_eps;   // epsilon of the slot species in this reaction
+    const double *thermo;     // N x kThermoStride
+    const double *Tmid;
+    const double *W;
+    const double *invW;
+    const double *Delta;      // 1/W_j - 1/W_N (0 for j = N-1)
+    const int *sp_ptr;        // species gather CSR (N + 1)
+    const int *sp_rxn;
+    const double *sp_nu;
+    const int *col_ptr;       // energy-row column CSR over b-slots (N + 1)
+    const int *col_slot;
+    const int *col_rxn;
+    const int *row_ptr;       // sparse block rows (N + 1) over nnz entries
+    const int *nnz_col;
+    const int *nnz_cptr;      // contributions CSR (nnz + 1)
+    const double *nnz_wr;     // W_k / W_j
+    const int *con_slot;
+    const double *con_nu;
+    const int *colN_nnz;      // per row k: nnz index of column N-1, or -1
+    double lnPatmR;           // ln(p_atm / R)
+};
+
+// Offsets (in doubles) of one state's scratch in shared memory.
+struct Scratch {
+    int C, B, dB, H, cpk, Jk0, A, Ck, f, HS, q, th, a, dH, b, rows, total;
+    int rows_per_chunk;       // rows staged per warp chunk
+};
+
+struct KParams {
+    DevModel m;
+    Scratch sc;
+    long long n;
+    const double *T, *P, *Y;
+    long long ldy;
+    double *jac;
+    long long ldj;
+    double *dydt;
+    long long ldd;
+    int groups;               // states processed concurrently per CTA
+    int shared_const;         // doubles of per-CTA constants at the start of shared memory
+};
+
+struct LaunchCfg {
+    int wps = 1;              // warps per state
+    int groups = 4;           // states per CTA
+    int ctas_per_sm = 1;
+};
+
+struct FormatError : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+struct Unsupported : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+
+// Host copy of a model's device image (pj_model.cu).
+struct HostImage {
+    std::vector<RxnDev> rx;
+    std::vector<double> par, eff_eps, slot_eps, thermo, Tmid, W, invW, Delta, sp_nu, nnz_wr, con_nu;
+    std::vector<int> eff_sp, slot_info, sp_ptr, sp_rxn, col_ptr, col_slot, col_rxn, row_ptr, nnz_col, nnz_cptr,
+        con_slot, colN_nnz;
+    std::vector<int> perm;
+    int N = 0, R = 0, NE = 0;
+};
+
+HostImage build_image(const void *buf, size_t len);                 // throws FormatError / Unsupported
+Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_chunk);
+int shared_const_doubles(int N);
+cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream);
+int set_error(int code, const std::string &msg);   // records the calling thread's last error, returns code
+
+}  // namespace pj
+
+struct pj_host_staging;
+
+struct pj_mech {
+    int N = 0, R = 0, NE = 0;
+    pj::DevModel dev{};
+    void *dev_blob = nullptr;
+    size_t dev_bytes = 0;
+    std::vector<int> perm;          // sorted position -> original reaction index
+    pj::LaunchCfg jac_cfg, dydt_cfg;
+    int jac_cfg_set = 0, dydt_cfg_set = 0;
+    int device = 0;
+    pj_host_staging *staging = nullptr;   // device buffers of pj_eval_jacobian_host (lazy)
+};
+
+void pj_host_staging_release(pj_mech *m);

@@ -1,0 +1,614 @@
+// sm_103a kernels: batched FP64 chemical source terms and analytical constant-pressure Jacobian.
+//
+// Method (paper Sections 2-4). Per state (T, P, Y_1..Y_N) with Y_N taken as given, column j of the
+// Jacobian (j = 1..N-1) is the derivative D_j = d/dY_j - d/dY_N at fixed T and P; column N is zero.
+// With Delta_j = 1/W_j - 1/W_N the Section 3.1 derivatives give, for every reaction i,
+//   D_j [X_l] = -[X_l] W Delta_j + (delta_lj - delta_lN) rho / W_l,
+//   D_j R_i   = -W Delta_j sigma_i + rho (G_ij / W_j - G_iN / W_N),
+//       sigma_i = (sum nu') R_f - (sum nu'') R_r,   G_il = k_f dPi'/d[X_l] - k_r dPi''/d[X_l],
+//   D_j c_i   = psi_i D_j [M]_i,  psi_i = dc_i/d[M]_i,
+//   D_j [M]_i = -W Delta_j E_i + rho (eps_ij / W_j - eps_iN / W_N),
+//       eps_il = alpha_il - 1 and E_i = [M]_i - p/(RT) for the mixture (dp/dY_j = 0, Appendix B),
+//       eps_il = delta_lm and E_i = [X_m] for a single third-body species m.
+// Hence D_j q_i = Delta_j a_i + rho (b'_ij / W_j - b'_iN / W_N) with
+//   a_i = -W (c_i sigma_i + psi_i R_i E_i),   b'_il = c_i G_il + psi_i R_i eps_il,
+// and Eq. e:jac_spec becomes, for species rows k,
+//   J_{k,j} = A_k Delta_j + C_k + Sparse_{k,j},
+//   A_k = (W_k/rho) (sum_i nu_ki a_i + W omega_k),  Sparse_{k,j} = (W_k/W_j) sum_i nu_ki b'_ij,
+//   C_k = -Sparse_{k,N}.
+// The temperature column is J_{k,0} = (W_k/rho) sum_i nu_ki theta_i with
+// theta_i = dq_i/dT + q_i/T (the paper's Theta_dT times rho, Eq. e:jac_temperature_update).
+// The energy row (Eq. e:jac_dt) uses sum_k h_k J_{k,j} = HA Delta_j + HS_j - HS_N with
+// HA = sum_k h_k A_k and HS_j = (1/W_j) sum_i dH_i b'_ij, dH_i = sum_k nu_ki H_k.
+// This is the paper's Algorithm 2 reuse: every per-reaction product is formed once (reaction
+// stage), scattered to species by static gather lists (gather stage), and the dense (N+1)^2
+// block is written at one FMA per entry plus the reaction-local sparse terms (row stage).
+//
+// Parallel layout: a "group" of WPS warps evaluates one state at a time; a CTA holds several
+// groups and loops persistently over states. All of a state's intermediates live in shared
+// memory. Reductions over species use a fixed 32-lane order that every warp repeats, so the
+// result of a state is bitwise independent of the launch shape.
+#include <cstdint>
+
+#include "pj_internal.h"
+
+namespace pj {
+
+constexpr double kInvLn10 = 0.43429448190325182765;
+constexpr double kLn10 = 2.30258509299404568402;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    // xor butterfly: a + b is commutative, so every lane ends with the same bits
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int WPS>
+__device__ __forceinline__ void group_sync(int grp) {
+    if constexpr (WPS == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(WPS * 32) : "memory");
+    }
+}
+
+__device__ __forceinline__ double ipow(double x, int n) {
+    double x2 = x * x;
+    return n == 1 ? x : n == 2 ? x2 : n == 3 ? x2 * x : x2 * x2;
+}
+
+// n x^(n-1)
+__device__ __forceinline__ double dipow(double x, int n) {
+    return n == 1 ? 1.0 : n == 2 ? 2.0 * x : n == 3 ? 3.0 * x * x : 4.0 * x * x * x;
+}
+
+__device__ __forceinline__ double sel4(const double (&v)[kMaxSlots], int i) {
+    return i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
+}
+
+struct StateScalars {
+    double T, invT, lnT, P, lnP, W, rho, Ctot;
+};
+
+// Thermodynamics of species k (Eqs. e:cpk, e:hk; B_k and dB_k/dT of Sections 2.3.1, 3.1).
+struct Thermo {
+    double cpR, HR, B, dB, dcpR;
+};
+
+template <bool JAC>
+__device__ __forceinline__ Thermo species_thermo(const DevModel &m, int k, double T, double invT, double lnT) {
+    const double *t = m.thermo + size_t(k) * kThermoStride + (T < __ldg(m.Tmid + k) ? 0 : 18);
+    const double a0 = __ldg(t + 0), a1 = __ldg(t + 1), a2 = __ldg(t + 2), a3 = __ldg(t + 3), a4 = __ldg(t + 4),
+                 a5 = __ldg(t + 5);
+    const double h1 = __ldg(t + 7), h2 = __ldg(t + 8), h3 = __ldg(t + 9), h4 = __ldg(t + 10);
+    const double g2 = __ldg(t + 11), g3 = __ldg(t + 12), g4 = __ldg(t + 13), b0 = __ldg(t + 17);
+    Thermo o;
+    o.cpR = fma(T, fma(T, fma(T, fma(T, a4, a3), a2), a1), a0);
+    o.HR = fma(T, fma(T, fma(T, fma(T, fma(T, h4, h3), h2), h1), a0), a5);
+    o.B = fma(a0 - 1.0, lnT, b0) + T * fma(T, fma(T, fma(T, g4, g3), g2), h1) - a5 * invT;
+    if constexpr (JAC) {
+        const double d2 = __ldg(t + 14), d3 = __ldg(t + 15), d4 = __ldg(t + 16);
+        o.dB = fma(a5, invT, a0 - 1.0) * invT + fma(T, fma(T, fma(T, h4, h3), h2), h1);
+        o.dcpR = fma(T, fma(T, fma(T, d4, d3), d2), a1);
+    } else {
+        o.dB = 0.0;
+        o.dcpR = 0.0;
+    }
+    return o;
+}
+
+// Third-body concentration [M]_i and E_i = [M]_i - u p/(RT) (u = 1 mixture, 0 single species).
+__device__ __forceinline__ void third_body(const DevModel &m, const RxnDev &d, const double *C, double Ctot,
+                                           double &M, double &E) {
+    if (d.tbmode == kTbSpecies) {
+        M = C[d.tbsp];
+        E = M;
+    } else {
+        double e = 0.0;
+        for (int x = 0; x < d.neff; ++x) e = fma(__ldg(m.eff_eps + d.eff_off + x), C[__ldg(m.eff_sp + d.eff_off + x)], e);
+        E = e;
+        M = Ctot + e;
+    }
+}
+
+// Reaction i: rate of progress q_i and, for the Jacobian, theta_i, a_i, dH_i and the b-slots.
+template <bool JAC>
+__device__ __forceinline__ void reaction(const DevModel &m, int i, const StateScalars &s, const double *C,
+                                         const double *B, const double *dB, const double *H, double *sq,
+                                         double *sth, double *sa, double *sdH, double *sb) {
+    RxnDev d;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(m.rx + i);
+        int4 *dst = reinterpret_cast<int4 *>(&d);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) dst[w] = __ldg(src + w);
+    }
+    const double *par = m.par + d.par_off;
+    const double T = s.T, invT = s.invT, lnT = s.lnT;
+    double lnkf = 0.0, dlnkf = 0.0, kf = 0.0;
+    double c = 1.0, dcdT = 0.0, psi = 0.0, E = 0.0;
+    int rev_off = 0;
+
+    if (d.kind == kElem || d.kind == kThird) {
+        const double lnA = __ldg(par + 0), beta = __ldg(par + 1), Ta = __ldg(par + 2);
+        lnkf = fma(beta, lnT, lnA) - Ta * invT;
+        dlnkf = fma(Ta, invT, beta) * invT;
+        if (d.kform == kKfConst) {
+            kf = __ldg(par + 3);
+        } else if (d.kform == kKfIntPow) {
+            double tp = 1.0, base = d.kpow >= 0 ? T : invT;
+            for (int x = 0; x < (d.kpow >= 0 ? d.kpow : -d.kpow); ++x) tp *= base;
+            kf = __ldg(par + 3) * tp;
+        } else {
+            kf = exp(lnkf);
+        }
+        rev_off = 4;
+        if (d.kind == kThird) {
+            double M;
+            third_body(m, d, C, s.Ctot, M, E);
+            c = M;
+            dcdT = -M * invT;
+            psi = 1.0;
+        }
+    } else if (d.kind == kFalloff || d.kind == kChem) {
+        const double lnk0 = fma(__ldg(par + 1), lnT, __ldg(par + 0)) - __ldg(par + 2) * invT;
+        const double lnki = fma(__ldg(par + 4), lnT, __ldg(par + 3)) - __ldg(par + 5) * invT;
+        const double dlnk0 = fma(__ldg(par + 2), invT, __ldg(par + 1)) * invT;
+        const double dlnki = fma(__ldg(par + 5), invT, __ldg(par + 4)) * invT;
+        double M;
+        third_body(m, d, C, s.Ctot, M, E);
+        const double ratio = exp(lnk0 - lnki);
+        const double Pr = ratio * M;
+        double F = 1.0, phiF = 0.0, tauF = 0.0;   // F, dlnF/dlnPr, dlnF/dT at fixed Pr
+        if (d.ftype == kTroe) {
+            const double a = __ldg(par + 6), iT3 = __ldg(par + 7), iT1 = __ldg(par + 8), T2 = __ldg(par + 9);
+            const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
+            double Fc = fma(1.0 - a, e3, a * e1);
+            double dFc = -(1.0 - a) * iT3 * e3 - a * iT1 * e1;
+            if (d.flags & 1) {
+                const double e2 = exp(-T2 * invT);
+                Fc += e2;
+                dFc = fma(T2 * invT * invT, e2, dFc);
+            }
+            const double lnFc = log(Fc), lFc = lnFc * kInvLn10;
+            const double lPr = log(fmax(Pr, 1e-300)) * kInvLn10;
+            const double At = lPr - 0.67 * lFc - 0.4;
+            const double Bt = 0.806 - 1.1762 * lFc - 0.14 * lPr;
+            const double iB = 1.0 / Bt, r = At * iB;
+            const double g = 1.0 / fma(r, r, 1.0);
+            F = exp(lnFc * g);
+            if constexpr (JAC) {
+                const double g2r = -2.0 * g * g * r * iB;
+                phiF = lnFc * g2r * fma(0.14, r, 1.0) * kInvLn10;
+                const double dg_dlFc = g2r * fma(1.1762, r, -0.67);
+                tauF = fma(lnFc * kInvLn10, dg_dlFc, g) * dFc / Fc;
+            }
+        } else if (d.ftype == kSri) {
+            const double a = __ldg(par + 6), b = __ldg(par + 7), ic = __ldg(par + 8), lnd = __ldg(par + 9),
+                         e = __ldg(par + 10);
+            const double lPr = log(fmax(Pr, 1e-300)) * kInvLn10;
+            const double X = 1.0 / fma(lPr, lPr, 1.0);
+            const double e1 = exp(-b * invT), e2 = exp(-T * ic);
+            const double base = fma(a, e1, e2);
+            const double lnb = log(base);
+            F = exp(fma(X, lnb, fma(e, lnT, lnd)));
+            if constexpr (JAC) {
+                phiF = -2.0 * X * X * lPr * lnb * kInvLn10;
+                tauF = fma(X * fma(a * b * invT * invT, e1, -ic * e2), 1.0 / base, e * invT);
+            }
+        }
+        const double iPr1 = 1.0 / (1.0 + Pr);
+        double phi;
+        if (d.kind == kFalloff) {
+            lnkf = lnki;
+            dlnkf = dlnki;
+            c = Pr * iPr1 * F;
+            phi = iPr1 + phiF;
+            psi = ratio * F * iPr1 * phi;
+        } else {
+            lnkf = lnk0;
+            dlnkf = dlnk0;
+            c = F * iPr1;
+            phi = phiF - Pr * iPr1;
+            const double Mg = M > 0.0 ? M : 1e-300;
+            psi = F * iPr1 * (phiF / Mg - ratio * iPr1);
+        }
+        kf = exp(lnkf);
+        dcdT = c * fma(phi, dlnk0 - dlnki - invT, tauF);
+        rev_off = 11;
+    } else if (d.kind == kPlog) {
+        const int n = int(__ldg(par + 0));
+        const double *t = par + 1;   // n x (p, ln p, ln A, beta, Ta)
+        int lo = 0, hi = 0;
+        double fr = 0.0;
+        if (s.P <= __ldg(t + 0)) {
+            lo = hi = 0;
+        } else if (s.P >= __ldg(t + 5 * (n - 1))) {
+            lo = hi = n - 1;
+        } else {
+            lo = 0;
+            while (lo < n - 2 && !(s.P < __ldg(t + 5 * (lo + 1)))) ++lo;   // bounded even for NaN P
+            hi = lo + 1;
+            const double l1 = __ldg(t + 5 * lo + 1), l2 = __ldg(t + 5 * hi + 1);
+            fr = (s.lnP - l1) / (l2 - l1);
+        }
+        const double *a = t + 5 * lo, *b = t + 5 * hi;
+        const double lk1 = fma(__ldg(a + 3), lnT, __ldg(a + 2)) - __ldg(a + 4) * invT;
+        const double lk2 = fma(__ldg(b + 3), lnT, __ldg(b + 2)) - __ldg(b + 4) * invT;
+        const double d1 = fma(__ldg(a + 4), invT, __ldg(a + 3)) * invT;
+        const double d2 = fma(__ldg(b + 4), invT, __ldg(b + 3)) * invT;
+        lnkf = fma(lk2 - lk1, fr, lk1);
+        dlnkf = fma(d2 - d1, fr, d1);
+        kf = exp(lnkf);
+        rev_off = 1 + 5 * n;
+    } else {   // Chebyshev, Eq. e:cheb; derivative via d T_n/dx = n U_{n-1}
+        const int nt = int(__ldg(par + 0)), npc = int(__ldg(par + 1));
+        const double Tt = (2.0 * invT - __ldg(par + 2)) * __ldg(par + 3);
+        const double pt = (2.0 * s.lnP * kInvLn10 - __ldg(par + 4)) * __ldg(par + 5);
+        const double *eta = par + 6;
+        double lk = 0.0, dlk = 0.0;
+        double Tm1 = 0.0, T0 = 1.0;        // T_{t-1}, T_t at Tt
+        double Um2 = 0.0, Um1 = 0.0;       // U_{t-2}, U_{t-1}
+        for (int x = 0; x < nt; ++x) {
+            double ct = 0.0, pm1 = 0.0, p0 = 1.0;
+            for (int y = 0; y < npc; ++y) {
+                ct = fma(__ldg(eta + x * npc + y), p0, ct);
+                const double pn = (y == 0) ? pt : 2.0 * pt * p0 - pm1;
+                pm1 = p0;
+                p0 = pn;
+            }
+            lk = fma(ct, T0, lk);
+            dlk = fma(ct * double(x), Um1, dlk);
+            const double Tn = (x == 0) ? Tt : 2.0 * Tt * T0 - Tm1;
+            Tm1 = T0;
+            T0 = Tn;
+            const double Un = (x == 0) ? 1.0 : (x == 1 ? 2.0 * Tt : 2.0 * Tt * Um1 - Um2);
+            Um2 = Um1;
+            Um1 = Un;
+        }
+        lnkf = lk * kLn10;
+        dlnkf = kLn10 * dlk * (-2.0 * invT * invT) * __ldg(par + 3);
+        kf = exp(lnkf);
+        rev_off = 6 + nt * npc;
+    }
+
+    // reverse rate coefficient (Section 2.3.1)
+    double kr = 0.0, dlnkr = 0.0;
+    double nf = 0.0, nb = 0.0;
+#pragma unroll
+    for (int x = 0; x < kMaxSlots; ++x) {
+        nf += x < d.nr ? double(d.rnu[x]) : 0.0;
+        nb += x < d.np ? double(d.pnu[x]) : 0.0;
+    }
+    if (d.rev == kRevKc) {
+        double sB = 0.0, sdB = 0.0;
+#pragma unroll
+        for (int x = 0; x < kMaxSlots; ++x) {
+            if (x < d.np) {
+                sB = fma(double(d.pnu[x]), B[d.psp[x]], sB);
+                if constexpr (JAC) sdB = fma(double(d.pnu[x]), dB[d.psp[x]], sdB);
+            }
+            if (x < d.nr) {
+                sB = fma(-double(d.rnu[x]), B[d.rsp[x]], sB);
+                if constexpr (JAC) sdB = fma(-double(d.rnu[x]), dB[d.rsp[x]], sdB);
+            }
+        }
+        const double lnKc = fma(nb - nf, m.lnPatmR, sB);
+        kr = exp(lnkf - lnKc);
+        dlnkr = dlnkf - sdB;
+    } else if (d.rev == kRevExplicit) {
+        const double *pr = par + rev_off;
+        kr = exp(fma(__ldg(pr + 1), lnT, __ldg(pr + 0)) - __ldg(pr + 2) * invT);
+        dlnkr = fma(__ldg(pr + 2), invT, __ldg(pr + 1)) * invT;
+    }
+
+    // concentration products and their partial derivatives (no division by [X])
+    double pwf[kMaxSlots], pwb[kMaxSlots];
+#pragma unroll
+    for (int x = 0; x < kMaxSlots; ++x) {
+        pwf[x] = x < d.nr ? ipow(C[d.rsp[x]], d.rnu[x]) : 1.0;
+        pwb[x] = x < d.np ? ipow(C[d.psp[x]], d.pnu[x]) : 1.0;
+    }
+    const double Pf = (pwf[0] * pwf[1]) * (pwf[2] * pwf[3]);
+    const double Pb = (pwb[0] * pwb[1]) * (pwb[2] * pwb[3]);
+    const double Rf = kf * Pf, Rr = kr * Pb, Rn = Rf - Rr;
+    const double q = c * Rn;
+    sq[i] = q;
+    if constexpr (!JAC) return;
+
+    const double dRdT = Rf * fma(-nf, invT, dlnkf) - Rr * fma(-nb, invT, dlnkr);
+    sth[i] = fma(dcdT, Rn, fma(c, dRdT, q * invT));
+    const double sigma = fma(nf, Rf, -nb * Rr);
+    sa[i] = -s.W * fma(c, sigma, psi * Rn * E);
+    double dH = 0.0;
+#pragma unroll
+    for (int x = 0; x < kMaxSlots; ++x) {
+        if (x < d.np) dH = fma(double(d.pnu[x]), H[d.psp[x]], dH);
+        if (x < d.nr) dH = fma(-double(d.rnu[x]), H[d.rsp[x]], dH);
+    }
+    sdH[i] = dH;
+    double Sf[kMaxSlots], Sb[kMaxSlots];
+#pragma unroll
+    for (int x = 0; x < kMaxSlots; ++x) {
+        double of = 1.0, ob = 1.0;
+#pragma unroll
+        for (int y = 0; y < kMaxSlots; ++y)
+            if (y != x) {
+                of *= pwf[y];
+                ob *= pwb[y];
+            }
+        Sf[x] = x < d.nr ? kf * dipow(C[d.rsp[x]], d.rnu[x]) * of : 0.0;
+        Sb[x] = x < d.np ? kr * dipow(C[d.psp[x]], d.pnu[x]) * ob : 0.0;
+    }
+    const double psiR = psi * Rn;
+    for (int x = 0; x < d.nslot; ++x) {
+        const int info = __ldg(m.slot_info + d.slot_off + x);
+        const int rs = ((info >> 16) & 0xff) - 1, ps = ((info >> 24) & 0xff) - 1;
+        double G = 0.0;
+        if (rs >= 0) G = sel4(Sf, rs);
+        if (ps >= 0) G -= sel4(Sb, ps);
+        sb[d.slot_off + x] = fma(c, G, psiR * __ldg(m.slot_eps + d.slot_off + x));
+    }
+}
+
+// Streams len doubles from shared memory to global memory with 16-byte streaming stores where the
+// global address allows it (head and tail peeled).
+__device__ __forceinline__ void store_segment(double *g, const double *sbuf, int len, int lane) {
+    const int head = (reinterpret_cast<uintptr_t>(g) & 15) ? 1 : 0;
+    if (head && lane == 0 && len > 0) __stcs(g, sbuf[0]);
+    const int rem = len - head;
+    const int npairs = rem > 0 ? rem >> 1 : 0;
+    double2 *g2 = reinterpret_cast<double2 *>(g + head);
+    for (int x = lane; x < npairs; x += 32) {
+        double2 v;
+        v.x = sbuf[head + 2 * x];
+        v.y = sbuf[head + 2 * x + 1];
+        __stcs(g2 + x, v);
+    }
+    if (rem > 0 && (rem & 1) && lane == 0) __stcs(g + len - 1, sbuf[len - 1]);
+}
+
+template <bool JAC, int WPS>
+__global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KParams p) {
+    extern __shared__ __align__(16) double smem[];
+    const DevModel &m = p.m;
+    const int N = m.N, R = m.R;
+    constexpr int G = WPS * 32;
+    const int grp = threadIdx.x / G, t = threadIdx.x - grp * G, lane = threadIdx.x & 31, wg = t >> 5;
+
+    // per-CTA constants
+    double *sDelta = smem, *sInvW = smem + N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        sDelta[k] = __ldg(m.Delta + k);
+        sInvW[k] = __ldg(m.invW + k);
+    }
+    __syncthreads();
+
+    const Scratch &sc = p.sc;
+    double *S = smem + p.shared_const + size_t(grp) * sc.total;
+    double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
+    double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
+    double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
+
+    for (long long st = (long long)blockIdx.x * p.groups + grp; st < p.n; st += (long long)gridDim.x * p.groups) {
+        // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
+        StateScalars s;
+        s.T = __ldg(p.T + st);
+        s.P = __ldg(p.P + st);
+        s.invT = 1.0 / s.T;
+        s.lnT = log(s.T);
+        const double *Ys = p.Y + st * p.ldy;
+        double *sY = sf;   // Y parks in the f array until the concentrations exist
+        for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
+        for (int k = t; k < N; k += G) {
+            const Thermo th = species_thermo<JAC>(m, k, s.T, s.invT, s.lnT);
+            scp[k] = kR * sInvW[k] * th.cpR;
+            sH[k] = kR * th.HR;
+            sB[k] = th.B;
+            if constexpr (JAC) {
+                sdB[k] = th.dB;
+                sJk0[k] = kR * sInvW[k] * th.dcpR;   // dcp_k/dT parks in the J_k0 array
+            }
+        }
+        group_sync<WPS>(grp);
+        double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        for (int k = lane; k < N; k += 32) {
+            const double y = sY[k];
+            r1 = fma(y, sInvW[k], r1);
+            r2 = fma(y, scp[k], r2);
+            if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
+        }
+        const double sYW = warp_sum(r1), cp = warp_sum(r2);
+        const double dcpdT = JAC ? warp_sum(r3) : 0.0;
+        s.W = 1.0 / sYW;
+        s.Ctot = s.P / (kR * s.T);
+        s.rho = s.Ctot * s.W;
+        s.lnP = log(s.P);
+        for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
+        group_sync<WPS>(grp);
+
+        // ---- reaction stage ----
+        for (int i = t; i < R; i += G) reaction<JAC>(m, i, s, sC, sB, sdB, sH, sq, sth, sa, sdH, sb);
+        group_sync<WPS>(grp);
+
+        const double invrho = 1.0 / s.rho;
+        if constexpr (!JAC) {
+            for (int k = t; k < N; k += G) {
+                double w = 0.0;
+                for (int e = __ldg(m.sp_ptr + k); e < __ldg(m.sp_ptr + k + 1); ++e)
+                    w = fma(__ldg(m.sp_nu + e), sq[__ldg(m.sp_rxn + e)], w);
+                sf[k] = __ldg(m.W + k) * invrho * w;
+            }
+            group_sync<WPS>(grp);
+            double hf = 0.0;
+            for (int k = lane; k < N; k += 32) hf = fma(sH[k] * sInvW[k], sf[k], hf);
+            hf = warp_sum(hf);
+            double *out = p.dydt + st * p.ldd;
+            const double invcp = 1.0 / cp;
+            for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -hf * invcp : sf[k - 1];
+            group_sync<WPS>(grp);
+            continue;
+        } else {
+            // ---- gather stage: species sums and energy-row column sums ----
+            for (int item = t; item < 2 * N; item += G) {
+                if (item < N) {
+                    const int k = item;
+                    double wq = 0.0, wt = 0.0, wa = 0.0;
+                    for (int e = __ldg(m.sp_ptr + k); e < __ldg(m.sp_ptr + k + 1); ++e) {
+                        const int i = __ldg(m.sp_rxn + e);
+                        const double nu = __ldg(m.sp_nu + e);
+                        wq = fma(nu, sq[i], wq);
+                        wt = fma(nu, sth[i], wt);
+                        wa = fma(nu, sa[i], wa);
+                    }
+                    const double pre = __ldg(m.W + k) * invrho;
+                    sf[k] = pre * wq;
+                    sJk0[k] = pre * wt;
+                    sA[k] = pre * fma(s.W, wq, wa);
+                    double ck = 0.0;
+                    const int en = __ldg(m.colN_nnz + k);
+                    if (en >= 0) {
+                        double acc = 0.0;
+                        for (int c = __ldg(m.nnz_cptr + en); c < __ldg(m.nnz_cptr + en + 1); ++c)
+                            acc = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], acc);
+                        ck = -__ldg(m.nnz_wr + en) * acc;
+                    }
+                    sCk[k] = ck;
+                } else {
+                    const int j = item - N;
+                    double hs = 0.0;
+                    for (int e = __ldg(m.col_ptr + j); e < __ldg(m.col_ptr + j + 1); ++e)
+                        hs = fma(sdH[__ldg(m.col_rxn + e)], sb[__ldg(m.col_slot + e)], hs);
+                    sHS[j] = hs * sInvW[j];
+                }
+            }
+            group_sync<WPS>(grp);
+            double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
+            for (int k = lane; k < N; k += 32) {
+                const double hk = sH[k] * sInvW[k];
+                x1 = fma(hk, sA[k], x1);
+                x2 = fma(hk, sf[k], x2);
+                x3 = fma(hk, sJk0[k], x3);
+                x4 = fma(scp[k], sf[k], x4);
+            }
+            const double HA = warp_sum(x1), Hf = warp_sum(x2), HJ0 = warp_sum(x3), CF = warp_sum(x4);
+            const double invcp = 1.0 / cp;
+            const double J00 = -invcp * (fma(-dcpdT * invcp, Hf, CF) + HJ0);
+            const double HSN = sHS[N - 1], cpN = scp[N - 1];
+            const double e0 = Hf * invcp * invcp;
+
+            // ---- row stage: dense FMA + sparse terms, staged per warp, streamed to HBM ----
+            const int ld = N + 1, RPC = sc.rows_per_chunk;
+            double *stage = S + sc.rows + wg * RPC * ld;
+            double *Jout = p.jac + st * p.ldj;
+            for (int chunk = wg; chunk * RPC < ld; chunk += WPS) {
+                const int r0 = chunk * RPC, r1e = min(r0 + RPC, ld);
+                for (int r = r0; r < r1e; ++r) {
+                    double *row = stage + (r - r0) * ld;
+                    if (r == 0) {
+                        for (int j = lane; j <= N; j += 32)
+                            row[j] = (j == 0) ? J00
+                                   : (j == N) ? 0.0
+                                              : fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN),
+                                                    (scp[j - 1] - cpN) * e0);
+                    } else {
+                        const int k = r - 1;
+                        const double Ak = sA[k], Ck = sCk[k];
+                        for (int j = lane; j <= N; j += 32)
+                            row[j] = (j == 0) ? sJk0[k] : (j == N) ? 0.0 : fma(Ak, sDelta[j - 1], Ck);
+                    }
+                }
+                __syncwarp();
+                for (int r = max(r0, 1); r < r1e; ++r) {
+                    const int k = r - 1;
+                    double *row = stage + (r - r0) * ld;
+                    for (int e = __ldg(m.row_ptr + k) + lane; e < __ldg(m.row_ptr + k + 1); e += 32) {
+                        const int j = __ldg(m.nnz_col + e);
+                        if (j == N - 1) continue;
+                        double acc = 0.0;
+                        for (int c = __ldg(m.nnz_cptr + e); c < __ldg(m.nnz_cptr + e + 1); ++c)
+                            acc = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], acc);
+                        row[1 + j] = fma(__ldg(m.nnz_wr + e), acc, row[1 + j]);
+                    }
+                }
+                __syncwarp();
+                store_segment(Jout + (long long)r0 * ld, stage, (r1e - r0) * ld, lane);
+                __syncwarp();
+            }
+            if (p.dydt) {
+                double *out = p.dydt + st * p.ldd;
+                for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -Hf * invcp : sf[k - 1];
+            }
+            group_sync<WPS>(grp);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// host-side launch helpers
+
+Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_chunk) {
+    Scratch sc{};
+    int o = 0;
+    auto take = [&](int n) {
+        int r = o;
+        o += (n + 1) & ~1;   // keep every array 16-byte aligned
+        return r;
+    };
+    sc.C = take(N);
+    sc.B = take(N);
+    sc.H = take(N);
+    sc.cpk = take(N);
+    sc.f = take(N);
+    sc.q = take(R);
+    if (jac) {
+        sc.dB = take(N);
+        sc.Jk0 = take(N);
+        sc.A = take(N);
+        sc.Ck = take(N);
+        sc.HS = take(N);
+        sc.th = take(R);
+        sc.a = take(R);
+        sc.dH = take(R);
+        sc.b = take(nslot);
+        sc.rows_per_chunk = rows_per_chunk;
+        sc.rows = take(wps * rows_per_chunk * (N + 1));
+    } else {
+        sc.dB = sc.Jk0 = sc.A = sc.Ck = sc.HS = sc.th = sc.a = sc.dH = sc.b = sc.rows = 0;
+        sc.rows_per_chunk = 0;
+    }
+    sc.total = o;
+    return sc;
+}
+
+int shared_const_doubles(int N) { return ((2 * N) + 1) & ~1; }
+
+template <bool JAC>
+static cudaError_t launch_t(const KParams &p, int wps, int blocks, size_t smem, cudaStream_t stream) {
+    const int threads = wps * 32 * p.groups;
+    cudaError_t e = cudaSuccess;
+#define PJ_CASE(W)                                                                                       \
+    case W:                                                                                              \
+        e = cudaFuncSetAttribute(pj_eval_kernel<JAC, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                 int(smem));                                                             \
+        if (e != cudaSuccess) return e;                                                                  \
+        pj_eval_kernel<JAC, W><<<blocks, threads, smem, stream>>>(p);                                   \
+        return cudaGetLastError();
+    switch (wps) {
+        PJ_CASE(1)
+        PJ_CASE(2)
+        PJ_CASE(4)
+        PJ_CASE(8)
+        PJ_CASE(16)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef PJ_CASE
+}
+
+cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream) {
+    return jac ? launch_t<true>(p, wps, blocks, smem, stream) : launch_t<false>(p, wps, blocks, smem, stream);
+}
+
+}  // namespace pj

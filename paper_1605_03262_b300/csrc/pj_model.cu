@@ -1,0 +1,410 @@
+// Host side: reader of the binary kinetic-model format and builder of the device image.
+//
+// The device image is organised for the kernels of pj_kernels.cu:
+//   * reactions are sorted by class (pressure dependence, falloff form, reversibility) so that the
+//     32 reactions a warp evaluates together take the same branches;
+//   * every reaction owns "b-slots", one per species l whose mass-fraction column the reaction
+//     touches directly (its reactants, products, non-unity third-body species, species m); the
+//     kernel writes b'_il = c_i dR_i/d[X_l] + (dc_i/d[M]) R_i eps_il into them;
+//   * static gather lists (CSR) turn the per-reaction terms into per-species sums without atomics:
+//     species -> (reaction, nu) for the production rates and the dense coefficients, column ->
+//     b-slots for the energy row, and (row k, column l) -> (b-slot, nu_ki) for the sparse block.
+// The derivation of these terms from the paper's Section 3 chain rule is given in pj_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "pj_internal.h"
+
+namespace pj {
+
+namespace {
+
+struct Reader {
+    const unsigned char *p, *end;
+    template <class T> T get() {
+        if (size_t(end - p) < sizeof(T)) throw FormatError("model buffer truncated");
+        T v;
+        std::memcpy(&v, p, sizeof(T));
+        p += sizeof(T);
+        return v;
+    }
+    int i32() { return get<int32_t>(); }
+    double f64() { return get<double>(); }
+};
+
+struct HRxn {
+    int kind = 0, rev = 0;
+    std::vector<std::pair<int, int>> reac, prod;
+    double A = 0, beta = 0, Ta = 0;
+    double Ar = 0, betar = 0, Tar = 0;
+    int tbmode = 0, tbsp = -1;
+    std::vector<std::pair<int, double>> eff;      // alpha for listed species
+    double k0[3] = {0, 0, 0}, ki[3] = {0, 0, 0};
+    int ftype = 0, hasT2 = 0;
+    double fp[5] = {0, 0, 0, 0, 0};
+    std::vector<double> plog;                     // n x (p, A, beta, Ta)
+    int nt = 0, npc = 0;
+    double crng[4] = {0, 0, 0, 0};
+    std::vector<double> eta;
+};
+
+struct HModel {
+    int NE = 0, N = 0, R = 0;
+    std::vector<double> W, Tmid, alo, ahi;
+    std::vector<HRxn> rx;
+};
+
+void check(bool ok, const char *msg) {
+    if (!ok) throw FormatError(msg);
+}
+
+HModel parse(const void *buf, size_t len) {
+    Reader r{static_cast<const unsigned char *>(buf), static_cast<const unsigned char *>(buf) + len};
+    char magic[8];
+    for (char &c : magic) c = r.get<char>();
+    check(std::memcmp(magic, "PYJACMEC", 8) == 0, "bad magic");
+    uint32_t ver = r.get<uint32_t>(), ne = r.get<uint32_t>(), ns = r.get<uint32_t>(), nr = r.get<uint32_t>();
+    check(ver == 1, "unsupported model format version");
+    check(ns >= 2 && ns <= 30000 && nr <= 2000000 && ne <= 64, "model sizes out of range");
+    HModel m;
+    m.NE = int(ne);
+    m.N = int(ns);
+    m.R = int(nr);
+    m.W.resize(ns);
+    m.Tmid.resize(ns);
+    m.alo.resize(7 * ns);
+    m.ahi.resize(7 * ns);
+    for (uint32_t k = 0; k < ns; ++k) {
+        m.W[k] = r.f64();
+        (void)r.f64();
+        m.Tmid[k] = r.f64();
+        (void)r.f64();
+        for (int c = 0; c < 7; ++c) m.alo[7 * k + c] = r.f64();
+        for (int c = 0; c < 7; ++c) m.ahi[7 * k + c] = r.f64();
+        for (uint32_t e = 0; e < ne; ++e) (void)r.i32();
+        check(m.W[k] > 0.0 && std::isfinite(m.W[k]), "species molecular weight must be positive");
+    }
+    m.rx.resize(nr);
+    for (uint32_t i = 0; i < nr; ++i) {
+        HRxn &x = m.rx[i];
+        x.kind = r.i32();
+        x.rev = r.i32();
+        check(x.kind >= 0 && x.kind <= 5 && x.rev >= 0 && x.rev <= 2, "bad reaction kind or reversibility");
+        for (int side = 0; side < 2; ++side) {
+            int n = r.i32();
+            check(n >= 0 && n <= 8, "too many species on one side of a reaction");
+            auto &v = side ? x.prod : x.reac;
+            for (int s = 0; s < n; ++s) {
+                int sp = r.i32(), nu = r.i32();
+                check(sp >= 0 && sp < int(ns) && nu >= 1 && nu <= 8, "bad stoichiometry entry");
+                v.emplace_back(sp, nu);
+            }
+        }
+        x.A = r.f64();
+        x.beta = r.f64();
+        x.Ta = r.f64();
+        if (x.rev == kRevExplicit) {
+            x.Ar = r.f64();
+            x.betar = r.f64();
+            x.Tar = r.f64();
+        }
+        if (x.kind == kThird || x.kind == kFalloff || x.kind == kChem) {
+            x.tbmode = r.i32();
+            x.tbsp = r.i32();
+            int neff = r.i32();
+            check(x.tbmode == kTbMix || x.tbmode == kTbSpecies, "bad third-body mode");
+            check(x.tbmode != kTbSpecies || (x.tbsp >= 0 && x.tbsp < int(ns)), "bad third-body species");
+            check(neff >= 0 && neff <= int(ns) && (neff == 0 || x.tbmode == kTbMix), "bad efficiency list");
+            for (int e = 0; e < neff; ++e) {
+                int sp = r.i32();
+                double a = r.f64();
+                check(sp >= 0 && sp < int(ns), "bad efficiency species");
+                x.eff.emplace_back(sp, a);
+            }
+        }
+        if (x.kind == kFalloff || x.kind == kChem) {
+            for (double &v : x.k0) v = r.f64();
+            for (double &v : x.ki) v = r.f64();
+            x.ftype = r.i32();
+            for (double &v : x.fp) v = r.f64();
+            x.hasT2 = r.i32();
+            check(x.ftype >= 0 && x.ftype <= 2, "bad falloff form");
+        }
+        if (x.kind == kPlog) {
+            int n = r.i32();
+            check(n >= 1 && n <= 64, "bad PLOG table size");
+            x.plog.resize(4 * n);
+            for (double &v : x.plog) v = r.f64();
+            for (int c = 1; c < n; ++c) check(x.plog[4 * c] > x.plog[4 * (c - 1)], "PLOG pressures must increase");
+            for (int c = 0; c < n; ++c) check(x.plog[4 * c] > 0 && x.plog[4 * c + 1] > 0, "PLOG p and A must be positive");
+        }
+        if (x.kind == kCheb) {
+            x.nt = r.i32();
+            x.npc = r.i32();
+            check(x.nt >= 1 && x.npc >= 1 && x.nt <= 16 && x.npc <= 16, "bad Chebyshev shape");
+            for (double &v : x.crng) v = r.f64();
+            check(x.crng[0] > 0 && x.crng[1] > x.crng[0] && x.crng[2] > 0 && x.crng[3] > x.crng[2],
+                  "bad Chebyshev range");
+            x.eta.resize(size_t(x.nt) * x.npc);
+            for (double &v : x.eta) v = r.f64();
+        }
+    }
+    check(r.p == r.end, "trailing bytes after the last reaction");
+    return m;
+}
+
+// Merge repeated species of one side into distinct (species, nu) slots.
+std::vector<std::pair<int, int>> distinct(const std::vector<std::pair<int, int>> &v) {
+    std::vector<std::pair<int, int>> out;
+    for (auto &e : v) {
+        bool found = false;
+        for (auto &o : out)
+            if (o.first == e.first) {
+                o.second += e.second;
+                found = true;
+            }
+        if (!found) out.push_back(e);
+    }
+    return out;
+}
+
+int class_key(const HRxn &x) {
+    // kind first, then falloff form, third-body mode and reversibility: warp-uniform branches
+    int k = x.kind * 64 + x.ftype * 16 + x.tbmode * 4 + x.rev;
+    return k;
+}
+
+}  // namespace
+
+// Builds the host copy of the device image. Device pointers are patched by the caller.
+HostImage build_image(const void *buf, size_t len) {
+    HModel m = parse(buf, len);
+    HostImage im;
+    const int N = m.N, R = m.R;
+    im.N = N;
+    im.R = R;
+    im.NE = m.NE;
+    if (N > 32000) throw Unsupported("more than 32000 species");
+
+    // species tables
+    im.W = m.W;
+    im.Tmid = m.Tmid;
+    im.invW.resize(N);
+    im.Delta.resize(N);
+    for (int k = 0; k < N; ++k) im.invW[k] = 1.0 / m.W[k];
+    for (int k = 0; k < N; ++k) im.Delta[k] = (k == N - 1) ? 0.0 : (1.0 / m.W[k] - 1.0 / m.W[N - 1]);
+    im.thermo.assign(size_t(N) * kThermoStride, 0.0);
+    for (int k = 0; k < N; ++k)
+        for (int rng = 0; rng < 2; ++rng) {
+            const double *a = rng ? &m.ahi[7 * k] : &m.alo[7 * k];
+            double *t = &im.thermo[size_t(k) * kThermoStride + 18 * rng];
+            for (int c = 0; c < 7; ++c) t[c] = a[c];
+            t[7] = a[1] / 2.0;   // enthalpy and B_k / dB_k/dT coefficients
+            t[8] = a[2] / 3.0;
+            t[9] = a[3] / 4.0;
+            t[10] = a[4] / 5.0;
+            t[11] = a[2] / 6.0;
+            t[12] = a[3] / 12.0;
+            t[13] = a[4] / 20.0;
+            t[14] = 2.0 * a[2];  // d(cp/R)/dT coefficients
+            t[15] = 3.0 * a[3];
+            t[16] = 4.0 * a[4];
+            t[17] = a[6] - a[0];
+        }
+
+    // reaction order
+    im.perm.resize(R);
+    std::iota(im.perm.begin(), im.perm.end(), 0);
+    std::stable_sort(im.perm.begin(), im.perm.end(),
+                     [&](int a, int b) { return class_key(m.rx[a]) < class_key(m.rx[b]); });
+
+    // per-reaction records, parameter pool, b-slots
+    std::vector<std::vector<std::pair<int, double>>> net(R);   // sorted index -> (species, nu)
+    std::vector<std::vector<int>> slot_species(R);
+    im.rx.resize(R);
+    int slot_total = 0;
+    for (int si = 0; si < R; ++si) {
+        const HRxn &x = m.rx[im.perm[si]];
+        RxnDev d{};
+        d.kind = uint8_t(x.kind);
+        d.rev = uint8_t(x.rev);
+        d.ftype = uint8_t(x.ftype);
+        d.tbmode = uint8_t(x.kind == kThird || x.kind == kFalloff || x.kind == kChem ? x.tbmode : kTbNone);
+        auto reac = distinct(x.reac), prod = distinct(x.prod);
+        if (reac.size() > size_t(kMaxSlots) || prod.size() > size_t(kMaxSlots))
+            throw Unsupported("more than 4 distinct species on one side of a reaction");
+        d.nr = uint8_t(reac.size());
+        d.np = uint8_t(prod.size());
+        for (int s = 0; s < kMaxSlots; ++s) {
+            d.rsp[s] = int16_t(s < d.nr ? reac[s].first : 0);
+            d.rnu[s] = int8_t(s < d.nr ? reac[s].second : 0);
+            d.psp[s] = int16_t(s < d.np ? prod[s].first : 0);
+            d.pnu[s] = int8_t(s < d.np ? prod[s].second : 0);
+        }
+        for (auto &e : reac)
+            if (e.second > kMaxNu) throw Unsupported("stoichiometric coefficient above 4");
+        for (auto &e : prod)
+            if (e.second > kMaxNu) throw Unsupported("stoichiometric coefficient above 4");
+        d.flags = uint8_t(x.hasT2 ? 1 : 0);
+        d.tbsp = int16_t(d.tbmode == kTbSpecies ? x.tbsp : 0);
+        d.kform = kKfGeneral;
+        d.kpow = 0;
+        // parameter pool
+        d.par_off = int(im.par.size());
+        auto lnA = [](double A) {
+            if (!(A > 0.0)) throw FormatError("Arrhenius prefactors must be positive");
+            return std::log(A);
+        };
+        if (x.kind == kElem || x.kind == kThird) {
+            im.par.insert(im.par.end(), {lnA(x.A), x.beta, x.Ta, x.A});
+            if (x.beta == 0.0 && x.Ta == 0.0) d.kform = kKfConst;
+            else if (x.Ta == 0.0 && x.beta == std::floor(x.beta) && std::fabs(x.beta) <= 4.0) {
+                d.kform = kKfIntPow;
+                d.kpow = int(x.beta);
+            }
+        } else if (x.kind == kFalloff || x.kind == kChem) {
+            im.par.insert(im.par.end(), {lnA(x.k0[0]), x.k0[1], x.k0[2], lnA(x.ki[0]), x.ki[1], x.ki[2]});
+            if (x.ftype == kTroe) {
+                if (!(x.fp[1] > 0 && x.fp[2] > 0)) throw FormatError("Troe T*** and T* must be positive");
+                im.par.insert(im.par.end(), {x.fp[0], 1.0 / x.fp[1], 1.0 / x.fp[2], x.fp[3], 0.0});
+            } else if (x.ftype == kSri) {
+                if (!(x.fp[2] > 0 && x.fp[3] > 0)) throw FormatError("SRI c and d must be positive");
+                im.par.insert(im.par.end(), {x.fp[0], x.fp[1], 1.0 / x.fp[2], std::log(x.fp[3]), x.fp[4]});
+            } else {
+                im.par.insert(im.par.end(), {0.0, 0.0, 0.0, 0.0, 0.0});
+            }
+        } else if (x.kind == kPlog) {
+            int n = int(x.plog.size() / 4);
+            im.par.push_back(double(n));
+            for (int c = 0; c < n; ++c)
+                im.par.insert(im.par.end(), {x.plog[4 * c], std::log(x.plog[4 * c]), lnA(x.plog[4 * c + 1]),
+                                             x.plog[4 * c + 2], x.plog[4 * c + 3]});
+        } else {   // Chebyshev
+            double Tsum = 1.0 / x.crng[0] + 1.0 / x.crng[1];
+            double Tscale = 1.0 / (1.0 / x.crng[1] - 1.0 / x.crng[0]);
+            double lPsum = std::log10(x.crng[2]) + std::log10(x.crng[3]);
+            double lPscale = 1.0 / (std::log10(x.crng[3]) - std::log10(x.crng[2]));
+            im.par.insert(im.par.end(), {double(x.nt), double(x.npc), Tsum, Tscale, lPsum, lPscale});
+            im.par.insert(im.par.end(), x.eta.begin(), x.eta.end());
+        }
+        if (x.rev == kRevExplicit) im.par.insert(im.par.end(), {lnA(x.Ar), x.betar, x.Tar});
+
+        // third-body efficiencies (mixture): epsilon = alpha - 1 for listed species, merged
+        std::map<int, double> eps;
+        if (d.tbmode == kTbMix)
+            for (auto &e : x.eff) eps[e.first] = e.second - 1.0;
+        d.eff_off = int(im.eff_sp.size());
+        int neff = 0;
+        for (auto &e : eps)
+            if (e.second != 0.0) {
+                im.eff_sp.push_back(e.first);
+                im.eff_eps.push_back(e.second);
+                ++neff;
+            }
+        d.neff = int16_t(neff);
+
+        // b-slots: reactants, products, non-unity efficiency species, species m
+        std::vector<int> sl;
+        auto add = [&](int sp) {
+            if (std::find(sl.begin(), sl.end(), sp) == sl.end()) sl.push_back(sp);
+        };
+        for (auto &e : reac) add(e.first);
+        for (auto &e : prod) add(e.first);
+        if (d.tbmode == kTbMix && (x.kind == kThird || x.kind == kFalloff || x.kind == kChem))
+            for (auto &e : eps)
+                if (e.second != 0.0) add(e.first);
+        if (d.tbmode == kTbSpecies) add(x.tbsp);
+        d.slot_off = slot_total;
+        d.nslot = int(sl.size());
+        for (int sp : sl) {
+            int rs = -1, ps = -1;
+            for (int s = 0; s < d.nr; ++s)
+                if (reac[s].first == sp) rs = s;
+            for (int s = 0; s < d.np; ++s)
+                if (prod[s].first == sp) ps = s;
+            double e = 0.0;
+            if (d.tbmode == kTbMix) {
+                auto it = eps.find(sp);
+                if (it != eps.end()) e = it->second;
+            } else if (d.tbmode == kTbSpecies) {
+                e = (sp == x.tbsp) ? 1.0 : 0.0;
+            }
+            im.slot_info.push_back(sp | ((rs + 1) << 16) | ((ps + 1) << 24));
+            im.slot_eps.push_back(e);
+        }
+        slot_species[si] = sl;
+        slot_total += d.nslot;
+        // net stoichiometry
+        std::map<int, int> nn;
+        for (auto &e : reac) nn[e.first] -= e.second;
+        for (auto &e : prod) nn[e.first] += e.second;
+        for (auto &e : nn)
+            if (e.second != 0) net[si].emplace_back(e.first, double(e.second));
+        im.rx[si] = d;
+    }
+
+    // species gather CSR: species k -> (reaction, nu_ki), reactions ascending
+    {
+        std::vector<std::vector<std::pair<int, double>>> lists(N);
+        for (int i = 0; i < R; ++i)
+            for (auto &e : net[i]) lists[e.first].emplace_back(i, e.second);
+        im.sp_ptr.assign(N + 1, 0);
+        for (int k = 0; k < N; ++k) {
+            im.sp_ptr[k + 1] = im.sp_ptr[k] + int(lists[k].size());
+            for (auto &e : lists[k]) {
+                im.sp_rxn.push_back(e.first);
+                im.sp_nu.push_back(e.second);
+            }
+        }
+    }
+    // energy-row column CSR: column l -> b-slots (reaction ascending)
+    {
+        std::vector<std::vector<std::pair<int, int>>> lists(N);
+        for (int i = 0; i < R; ++i)
+            for (int s = 0; s < int(slot_species[i].size()); ++s)
+                lists[slot_species[i][s]].emplace_back(im.rx[i].slot_off + s, i);
+        im.col_ptr.assign(N + 1, 0);
+        for (int l = 0; l < N; ++l) {
+            im.col_ptr[l + 1] = im.col_ptr[l] + int(lists[l].size());
+            for (auto &e : lists[l]) {
+                im.col_slot.push_back(e.first);
+                im.col_rxn.push_back(e.second);
+            }
+        }
+    }
+    // sparse block: (row k, column l) -> contributions (b-slot of reaction i for l, nu_ki)
+    {
+        std::map<std::pair<int, int>, std::vector<std::pair<int, double>>> pairs;
+        for (int i = 0; i < R; ++i)
+            for (auto &e : net[i])
+                for (int s = 0; s < int(slot_species[i].size()); ++s)
+                    pairs[{e.first, slot_species[i][s]}].emplace_back(im.rx[i].slot_off + s, e.second);
+        im.row_ptr.assign(N + 1, 0);
+        im.colN_nnz.assign(N, -1);
+        im.nnz_cptr.push_back(0);
+        for (auto &kv : pairs) {
+            int k = kv.first.first, l = kv.first.second;
+            int e = int(im.nnz_col.size());
+            im.nnz_col.push_back(l);
+            im.nnz_wr.push_back(m.W[k] / m.W[l]);
+            for (auto &c : kv.second) {
+                im.con_slot.push_back(c.first);
+                im.con_nu.push_back(c.second);
+            }
+            im.nnz_cptr.push_back(int(im.con_slot.size()));
+            im.row_ptr[k + 1]++;
+            if (l == N - 1) im.colN_nnz[k] = e;
+        }
+        for (int k = 0; k < N; ++k) im.row_ptr[k + 1] += im.row_ptr[k];
+    }
+    return im;
+}
+
+}  // namespace pj

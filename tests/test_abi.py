@@ -1,0 +1,73 @@
+"""The C-ABI library: it builds, loads and exports every symbol the public header declares; host-side
+argument and model-format checks that need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1605_03262_b300 import build as pjbuild
+from paper_1605_03262_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(HEADER_DIR):
+        if fn.endswith(".h"):
+            text = open(os.path.join(HEADER_DIR, fn)).read()
+            names |= set(re.findall(r"PJ_API\s+[\w\s\*]*?\b(pj_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = pjbuild.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for must in ("pj_mech_load", "pj_mech_load_file", "pj_mech_free", "pj_mech_info", "pj_eval_dydt",
+                 "pj_eval_jacobian", "pj_eval_jacobian_host", "pj_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared_symbols()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_model_format_errors_are_reported_without_a_gpu(lib):
+    lib.pj_mech_load.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]
+    lib.pj_mech_load.restype = ctypes.c_int
+    lib.pj_last_error.restype = ctypes.c_char_p
+    blob = synth.to_bytes(synth.config_model(0))
+    h = ctypes.c_void_p()
+    for bad in (blob[:-5], b"XXXXXXXX" + blob[8:], blob + b"\0\0"):
+        buf = ctypes.create_string_buffer(bad, len(bad))
+        assert lib.pj_mech_load(buf, len(bad), ctypes.byref(h)) == -2       # PJ_EFORMAT
+        assert lib.pj_last_error()
+    assert lib.pj_mech_load(None, 0, ctypes.byref(h)) == -1                # PJ_EINVAL
+
+
+def test_null_model_arguments_are_rejected(lib):
+    lib.pj_eval_jacobian.restype = ctypes.c_int
+    lib.pj_eval_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 3 + \
+        [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.pj_eval_jacobian(None, 4, None, None, None, 13, None, 196, None, 0, None) == -1
+    lib.pj_mech_info.restype = ctypes.c_int
+    assert lib.pj_mech_info(None, None, None, None) == -1
+
+
+def test_oversized_stoichiometry_is_unsupported(lib):
+    from paper_1605_03262_b300.synth import KIND_ELEMENTARY, REV_IRREVERSIBLE, Reaction
+    from tests import mechs
+    r = Reaction(kind=KIND_ELEMENTARY, rev_mode=REV_IRREVERSIBLE, reac=[(0, 5)], prod=[(1, 1)], arr=(1.0, 0.0, 0.0))
+    model = mechs.one_reaction_model(r, [(1, 0), (5, 0)])
+    blob = synth.to_bytes(model)
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    h = ctypes.c_void_p()
+    assert lib.pj_mech_load(buf, len(blob), ctypes.byref(h)) == -6          # PJ_EUNSUPPORTED

@@ -1,0 +1,158 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case copies the oracle's C sources to a temporary directory, plants one mistake (a dropped
+term, a flipped sign, a wrong index or operand), compiles the copy with gcc and runs a quick set of
+pins against it: the analytical Jacobian against the complex-step derivative of the source terms,
+mass / element / enthalpy conservation, thermodynamics against quadrature of c_p, and closed-form
+rates. Every mutant must fail at least one pin; the unmodified copy must pass them all.
+"""
+import math
+import os
+import shutil
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_1605_03262_b300 import synth
+from paper_1605_03262_b300.synth import P_ATM, R_GAS
+from tests import mechs
+
+SRC = os.path.dirname(oracle.__file__)
+FILES = ("pyjac_oracle.c", "source_terms.inc", "oracle_model.h")
+
+# (file, text to replace, replacement)
+MUTANTS = [
+    ("pyjac_oracle.c", "dB[k] = (a[0] - 1.0 + a[5] / T) / T", "dB[k] = (a[0] - 1.0 - a[5] / T) / T"),
+    ("pyjac_oracle.c", "(dAdPr * Bt - At * dBdPr)", "(dAdPr * Bt + At * dBdPr)"),
+    ("pyjac_oracle.c", "dcdY = -Wm * c * Dl[j] + t2;", "dcdY = -Wm * c * Dl[j] - t2;"),
+    ("pyjac_oracle.c", "(r->k0[2] - r->kinf[2]) / T - 1.0)", "(r->k0[2] - r->kinf[2]) / T + 1.0)"),
+    ("source_terms.inc", "f[0] = -(hs + hsc) / (rho * cp);", "f[0] = (hs + hsc) / (rho * cp);"),
+    ("source_terms.inc", "a[2] / 6.0", "a[2] / 3.0"),
+    ("source_terms.inc", "(log(P) - log(a[0])) / (log(b[0]) - log(a[0]))",
+     "(log(P) - log(b[0])) / (log(b[0]) - log(a[0]))"),
+    ("source_terms.inc", "FN(chebT)(i, Tt) * FN(chebT)(j, (SCALAR)pt)", "FN(chebT)(j, Tt) * FN(chebT)(i, (SCALAR)pt)"),
+    ("pyjac_oracle.c", "-(cpk[j] - cpk[L]) / (rho * cp) * HWO", "-(cpk[j] - cpk[0]) / (rho * cp) * HWO"),
+    ("pyjac_oracle.c", "dkr = (dkf * Kc - dKc * kf) / (Kc * Kc);", "dkr = (dkf * Kc + dKc * kf) / (Kc * Kc);"),
+    ("pyjac_oracle.c", "acc_d(&row[1 + j], &cmp[1 + j], om[k] * Wm * Dl[j]);",
+     "acc_d(&row[1 + j], &cmp[1 + j], -om[k] * Wm * Dl[j]);"),
+    ("pyjac_oracle.c", "double dl = (k == j ? 1.0 : 0.0) - (k == L ? 1.0 : 0.0);",
+     "double dl = (k == j ? 1.0 : 0.0);"),
+    ("pyjac_oracle.c", "*dFdT_Pr = Fv * (e / T + X", "*dFdT_Pr = Fv * (e * T + X"),
+    ("pyjac_oracle.c", "else                        dcdY = c * (-1.0 / (1.0 + Pr) * dPrdY + dFdY / Fv);",
+     "else                        dcdY = c * (1.0 / (1.0 + Pr) * dPrdY + dFdY / Fv);"),
+    ("source_terms.inc", "f[1 + k] = m->W[k] * w / rho;", "f[1 + k] = w / rho;"),
+    ("source_terms.inc", "pow(PJO_PATM / PJO_R, (double)dn)", "pow(PJO_R / PJO_PATM, (double)dn)"),
+    ("source_terms.inc", "for (int s = 0; s < r->np; ++s) Prr *= FN(ipow)(C[r->psp[s]], r->pnu[s]);",
+     "for (int s = 0; s < r->np; ++s) Prr *= C[r->psp[s]];"),
+    ("pyjac_oracle.c", "cs_add(&s, hk[k] * J[(size_t)(1 + k) * ld + 0]);", "cs_add(&s, hk[k] * J[(size_t)(1 + k) * ld + 1]);"),
+    ("source_terms.inc", "c = Pr / (1.0 + Pr) * F; kf = ki;", "c = Pr / (1.0 + Pr) * F; kf = k0;"),
+    ("pyjac_oracle.c", "return kf / T * (r->kinf[1] + r->kinf[2] / T);", "return kf / T * (r->k0[1] + r->k0[2] / T);"),
+]
+
+EPS = 2.0 ** -52
+
+
+def _H_quad(a, T):
+    v, _ = integrate.quad(lambda t: np.polynomial.polynomial.polyval(t, a[:5]), 0.0, T, epsabs=0.0, epsrel=1e-13)
+    return a[5] + v
+
+
+def _pins(lib) -> list:
+    """Quick pins; returns the names of those that failed."""
+    failed = []
+    # 1. analytical Jacobian vs complex step, every reaction type (explicit and K_c reverse, chem.-act.)
+    for seed in (3, 4):
+        model = mechs.mixed_model(seed=seed, n_species=9, n_reactions=30)
+        om = oracle.load_model(synth.to_bytes(model), lib=lib)
+        T, P, Y = synth.generate_states(model.n_species, 6, seed=seed + 10)
+        J, f, Js, fs = om.jacobian(T, P, Y, with_scale=True)
+        Jc = om.jacobian_complex_step(T, P, Y)
+        bad = ~(np.abs(J - Jc) <= 1e-10 * np.maximum(np.abs(Jc), 1e-20) + 64 * EPS * Js)
+        if bad.any() or not np.all(np.isfinite(J)):
+            failed.append("complex-step")
+            break
+    # 2. conservation: mass, elements, enthalpy
+    model = synth.config_model(0)
+    om = oracle.load_model(synth.to_bytes(model), lib=lib)
+    T, P, Y = synth.config_states(0, 6)
+    J, f, Js, fs = om.jacobian(T, P, Y, with_scale=True)
+    W = np.array([s.W for s in model.species])
+    E = np.array([s.elem for s in model.species], dtype=np.float64)
+    if not np.all(np.abs(f[:, 1:].sum(1)) <= 1e-13 * fs[:, 1:].sum(1)):
+        failed.append("mass")
+    if not np.all(np.abs((f[:, 1:] / W) @ E) <= 1e-13 * ((fs[:, 1:] / W) @ E)):
+        failed.append("elements")
+    for s in range(2):
+        a = [(sp.a_low if T[s] < sp.T_mid else sp.a_high) for sp in model.species]
+        h = np.array([R_GAS / sp.W * _H_quad(a[i], T[s]) for i, sp in enumerate(model.species)])
+        cpk = np.array([R_GAS / sp.W * np.polynomial.polynomial.polyval(T[s], a[i][:5])
+                        for i, sp in enumerate(model.species)])
+        if abs(np.sum(h * f[s, 1:]) + (Y[s] @ cpk) * f[s, 0]) > 1e-11 * np.abs(h * f[s, 1:]).sum():
+            failed.append("enthalpy")
+            break
+    # 3. thermodynamics: B_k against quadrature-based S/R - H/(RT) - ln T
+    th = om.species_thermo(1500.0)
+    for k, sp in enumerate(model.species):
+        a = sp.a_high
+        S, _ = integrate.quad(lambda t: np.polynomial.polynomial.polyval(t, a[1:5]), 0.0, 1500.0, epsabs=0.0,
+                              epsrel=1e-13)
+        B = a[0] * math.log(1500.0) + a[6] + S - _H_quad(a, 1500.0) / 1500.0 - math.log(1500.0)
+        if abs(th["B"][k] - B) > 1e-9 * max(1.0, abs(B)):
+            failed.append("thermo")
+            break
+    # 4. rates at a PLOG interior pressure and a Chebyshev point against numpy
+    grid = [(1.0 * P_ATM, 1.0e5, 0.5, 1000.0), (3.0 * P_ATM, 3.0e5, 0.2, 1500.0), (20.0 * P_ATM, 2.0e6, -0.4, 800.0)]
+    r = synth.Reaction(kind=synth.KIND_PLOG, rev_mode=synth.REV_IRREVERSIBLE, reac=[(0, 1), (1, 1)], prod=[(2, 1)],
+                       plog=grid)
+    TWO = [(1, 0, 0), (0, 1, 0), (1, 1, 0)]
+    om1 = oracle.load_model(synth.to_bytes(mechs.one_reaction_model(r, TWO)), lib=lib)
+    Tq = 1300.0
+    lk = [math.log(A * Tq ** b * math.exp(-Ta / Tq)) for _, A, b, Ta in grid]
+    kf = om1.reaction_rates(Tq, 7.0 * P_ATM, np.array([0.3, 0.3, 0.4]))["kf"][0]
+    if abs(kf - math.exp(np.interp(math.log(7.0 * P_ATM), [math.log(g[0]) for g in grid], lk))) > 1e-12 * kf:
+        failed.append("plog")
+    eta = np.arange(21, dtype=float).reshape(7, 3) * 0.05
+    eta[0, 0] = 8.0
+    rngs = (300.0, 3000.0, 0.1 * P_ATM, 100.0 * P_ATM)
+    r = synth.Reaction(kind=synth.KIND_CHEB, rev_mode=synth.REV_IRREVERSIBLE, reac=[(0, 1), (1, 1)], prod=[(2, 1)],
+                       cheb_shape=(7, 3), cheb_range=rngs, cheb_eta=eta)
+    om2 = oracle.load_model(synth.to_bytes(mechs.one_reaction_model(r, TWO)), lib=lib)
+    Pq = 5.0 * P_ATM
+    Tt = (2 / Tq - 1 / rngs[0] - 1 / rngs[1]) / (1 / rngs[1] - 1 / rngs[0])
+    pt = (2 * math.log10(Pq) - math.log10(rngs[2]) - math.log10(rngs[3])) / (math.log10(rngs[3]) - math.log10(rngs[2]))
+    kf = om2.reaction_rates(Tq, Pq, np.array([0.3, 0.3, 0.4]))["kf"][0]
+    if abs(math.log10(kf) - np.polynomial.chebyshev.chebval2d(Tt, pt, eta)) > 1e-12:
+        failed.append("chebyshev")
+    return failed
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+def _variant(workdir, tag, mutation=None):
+    d = os.path.join(str(workdir), tag)
+    os.makedirs(d, exist_ok=True)
+    for fn in FILES:
+        shutil.copy(os.path.join(SRC, fn), os.path.join(d, fn))
+    if mutation is not None:
+        fn, old, new = mutation
+        p = os.path.join(d, fn)
+        text = open(p).read()
+        assert text.count(old) == 1, ("mutation anchor not found exactly once", fn, old)
+        open(p, "w").write(text.replace(old, new))
+    so = oracle.compile_variant(d, os.path.join(d, "liboracle_%s.so" % tag))
+    return oracle.load_variant(so)
+
+
+def test_unmodified_copy_passes_the_quick_pins(workdir):
+    assert _pins(_variant(workdir, "clean")) == []
+
+
+@pytest.mark.parametrize("idx", range(len(MUTANTS)))
+def test_planted_mistake_is_caught(workdir, idx):
+    failed = _pins(_variant(workdir, "m%02d" % idx, MUTANTS[idx]))
+    assert failed, "mutation %d survived every pin: %r" % (idx, MUTANTS[idx])
