@@ -43,10 +43,9 @@ DeviceProps device_props(int dev) {
     return cache[dev];
 }
 
-int rows_per_chunk(int N) { return std::max(1, std::min(4, 256 / (N + 1))); }
 
 size_t smem_bytes(const pj_mech *m, bool jac, const pj::LaunchCfg &c) {
-    pj::Scratch sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, rows_per_chunk(m->N));
+    pj::Scratch sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, m->dev.rpc);
     return (size_t(pj::shared_const_doubles(m->N)) + size_t(sc.total) * c.groups) * sizeof(double);
 }
 
@@ -122,7 +121,7 @@ int launch(const pj_mech *m, bool jac, int64_t n, const double *T, const double 
         return fail(PJ_EUNSUPPORTED, "one state's working set does not fit in shared memory for this model");
     pj::KParams p{};
     p.m = m->dev;
-    p.sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, rows_per_chunk(m->N));
+    p.sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, m->dev.rpc);
     p.n = n;
     p.T = T;
     p.P = P;
@@ -183,6 +182,15 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
            o_cs = push(blob, im.col_slot), o_cr = push(blob, im.col_rxn), o_rp = push(blob, im.row_ptr),
            o_nc = push(blob, im.nnz_col), o_ncp = push(blob, im.nnz_cptr), o_nw = push(blob, im.nnz_wr),
            o_cns = push(blob, im.con_slot), o_cnn = push(blob, im.con_nu), o_cN = push(blob, im.colN_nnz);
+    size_t o_si = push(blob, im.s_items), o_gi = push(blob, im.g_items), o_hi = push(blob, im.h_items),
+           o_ci = push(blob, im.c_items), o_ha = push(blob, im.h_aux), o_sc = push(blob, im.s_chunk),
+           o_gc = push(blob, im.g_chunk), o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk),
+           o_sd = push(blob, im.s_dst), o_gd = push(blob, im.g_dst), o_hd = push(blob, im.h_dst),
+           o_cd = push(blob, im.c_dst), o_ss = push(blob, im.s_scale), o_cs2 = push(blob, im.c_scale);
+    pj::MathTables tables;
+    pj::build_math_tables(tables);
+    std::vector<pj::MathTables> tvec(1, tables);
+    size_t o_mt = push(blob, tvec);
     pj_mech *m = new (std::nothrow) pj_mech();
     if (!m) return fail(PJ_ENOMEM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&m->device);
@@ -236,6 +244,27 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.con_nu = reinterpret_cast<const double *>(b + o_cnn);
     d.colN_nnz = reinterpret_cast<const int *>(b + o_cN);
     d.lnPatmR = std::log(pj::kPatm / pj::kR);
+    d.rpc = im.rpc;
+    d.n_row_chunks = im.n_row_chunks;
+    d.ng = im.ng;
+    d.nh = im.nh;
+    d.ncc = im.ncc;
+    d.s_items = reinterpret_cast<const unsigned *>(b + o_si);
+    d.g_items = reinterpret_cast<const unsigned *>(b + o_gi);
+    d.h_items = reinterpret_cast<const unsigned *>(b + o_hi);
+    d.c_items = reinterpret_cast<const unsigned *>(b + o_ci);
+    d.h_aux = reinterpret_cast<const int *>(b + o_ha);
+    d.s_chunk = reinterpret_cast<const int *>(b + o_sc);
+    d.g_chunk = reinterpret_cast<const int *>(b + o_gc);
+    d.h_chunk = reinterpret_cast<const int *>(b + o_hc);
+    d.c_chunk = reinterpret_cast<const int *>(b + o_cc);
+    d.s_dst = reinterpret_cast<const int *>(b + o_sd);
+    d.g_dst = reinterpret_cast<const int *>(b + o_gd);
+    d.h_dst = reinterpret_cast<const int *>(b + o_hd);
+    d.c_dst = reinterpret_cast<const int *>(b + o_cd);
+    d.s_scale = reinterpret_cast<const double *>(b + o_ss);
+    d.c_scale = reinterpret_cast<const double *>(b + o_cs2);
+    d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
     m->N = im.N;
     m->R = im.R;
     m->NE = im.NE;

@@ -10,6 +10,8 @@
 
 #include <cuda_runtime.h>
 
+#include "pj_fastmath.cuh"
+
 namespace pj {
 
 constexpr double kR = 8.31446261815324;   // J/(mol K)
@@ -71,6 +73,17 @@ struct DevModel {
     const double *con_nu;
     const int *colN_nnz;      // per row k: nnz index of column N-1, or -1
     double lnPatmR;           // ln(p_atm / R)
+    // Lane-balanced schedules (see pj_model.cu): items are lane-interleaved (chunk offset +
+    // t*32 + lane); an item packs an index (24 bits), a coefficient code (7 bits) and an
+    // end-of-sum flag (bit 31); entries (one per finished sum) are lane-interleaved too.
+    int rpc, n_row_chunks;    // rows per staged chunk, chunks covering the N+1 rows
+    int ng, nh, ncc;          // chunks of the species-gather, column-sum and C_k schedules
+    const unsigned *s_items, *g_items, *h_items, *c_items;
+    const int *h_aux;         // reaction of each column-sum item
+    const int *s_chunk, *g_chunk, *h_chunk, *c_chunk;   // per chunk: item offset, length, entry offset
+    const int *s_dst, *g_dst, *h_dst, *c_dst;
+    const double *s_scale, *c_scale;
+    const MathTables *tables;  // exp/log tables (pj_fastmath.cuh)
 };
 
 // Offsets (in doubles) of one state's scratch in shared memory.
@@ -114,7 +127,14 @@ struct HostImage {
         con_slot, colN_nnz;
     std::vector<int> perm;
     int N = 0, R = 0, NE = 0;
+    // lane-balanced schedules
+    int rpc = 1, n_row_chunks = 0, ng = 0, nh = 0, ncc = 0;
+    std::vector<unsigned> s_items, g_items, h_items, c_items;
+    std::vector<int> h_aux, s_chunk, g_chunk, h_chunk, c_chunk, s_dst, g_dst, h_dst, c_dst;
+    std::vector<double> s_scale, c_scale;
 };
+
+constexpr int kNuBias = 64;          // coefficient code = nu + kNuBias (7 bits)
 
 HostImage build_image(const void *buf, size_t len);                 // throws FormatError / Unsupported
 Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_chunk);

@@ -377,19 +377,29 @@ __global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KP
     constexpr int G = WPS * 32;
     const int grp = threadIdx.x / G, t = threadIdx.x - grp * G, lane = threadIdx.x & 31, wg = t >> 5;
 
-    // per-CTA constants
-    double *sDelta = smem, *sInvW = smem + N;
+    // per-CTA constants: Delta_j, 1/W_j and the stoichiometric-coefficient table nu = code - kNuBias
+    double *sNu = smem, *sDelta = smem + 128, *sInvW = smem + 128 + N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         sDelta[k] = __ldg(m.Delta + k);
         sInvW[k] = __ldg(m.invW + k);
     }
-    __syncthreads();
+    for (int c = threadIdx.x; c < 128; c += blockDim.x) sNu[c] = double(c - kNuBias);
 
     const Scratch &sc = p.sc;
     double *S = smem + p.shared_const + size_t(grp) * sc.total;
     double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
     double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
     double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
+    if (t == 0) {   // neutral elements read by padded schedule items; never overwritten
+        sq[R] = 0.0;
+        if (JAC) {
+            sth[R] = 0.0;
+            sa[R] = 0.0;
+            sdH[R] = 0.0;
+            sb[m.nslot] = 0.0;
+        }
+    }
+    __syncthreads();
 
     for (long long st = (long long)blockIdx.x * p.groups + grp; st < p.n; st += (long long)gridDim.x * p.groups) {
         // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
@@ -434,11 +444,21 @@ __global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KP
 
         const double invrho = 1.0 / s.rho;
         if constexpr (!JAC) {
-            for (int k = t; k < N; k += G) {
+            for (int c = wg; c < m.ng; c += WPS) {       // omega_k through the species-gather schedule
+                const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
+                const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
+                const unsigned *it = m.g_items + ioff + lane;
                 double w = 0.0;
-                for (int e = __ldg(m.sp_ptr + k); e < __ldg(m.sp_ptr + k + 1); ++e)
-                    w = fma(__ldg(m.sp_nu + e), sq[__ldg(m.sp_rxn + e)], w);
-                sf[k] = __ldg(m.W + k) * invrho * w;
+                for (int x = 0; x < len; ++x) {
+                    const unsigned v = __ldg(it + 32 * x);
+                    w = fma(sNu[(v >> 24) & 127], sq[v & 0xffffff], w);
+                    if (v >> 31) {
+                        const int k = __ldg(dst);
+                        dst += 32;
+                        sf[k] = __ldg(m.W + k) * invrho * w;
+                        w = 0.0;
+                    }
+                }
             }
             group_sync<WPS>(grp);
             double hf = 0.0;
@@ -450,37 +470,63 @@ __global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KP
             group_sync<WPS>(grp);
             continue;
         } else {
-            // ---- gather stage: species sums and energy-row column sums ----
-            for (int item = t; item < 2 * N; item += G) {
-                if (item < N) {
-                    const int k = item;
-                    double wq = 0.0, wt = 0.0, wa = 0.0;
-                    for (int e = __ldg(m.sp_ptr + k); e < __ldg(m.sp_ptr + k + 1); ++e) {
-                        const int i = __ldg(m.sp_rxn + e);
-                        const double nu = __ldg(m.sp_nu + e);
-                        wq = fma(nu, sq[i], wq);
-                        wt = fma(nu, sth[i], wt);
-                        wa = fma(nu, sa[i], wa);
+            // ---- gather stage: lane-balanced schedules (each sum is one lane's, in list order) ----
+            for (int c = wg; c < m.ng; c += WPS) {       // omega_k, J_k0, A_k
+                const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
+                const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
+                const unsigned *it = m.g_items + ioff + lane;
+                double wq = 0.0, wt = 0.0, wa = 0.0;
+                for (int x = 0; x < len; ++x) {
+                    const unsigned v = __ldg(it + 32 * x);
+                    const int i = v & 0xffffff;
+                    const double nu = sNu[(v >> 24) & 127];
+                    wq = fma(nu, sq[i], wq);
+                    wt = fma(nu, sth[i], wt);
+                    wa = fma(nu, sa[i], wa);
+                    if (v >> 31) {
+                        const int k = __ldg(dst);
+                        dst += 32;
+                        const double pre = __ldg(m.W + k) * invrho;
+                        sf[k] = pre * wq;
+                        sJk0[k] = pre * wt;
+                        sA[k] = pre * fma(s.W, wq, wa);
+                        wq = wt = wa = 0.0;
                     }
-                    const double pre = __ldg(m.W + k) * invrho;
-                    sf[k] = pre * wq;
-                    sJk0[k] = pre * wt;
-                    sA[k] = pre * fma(s.W, wq, wa);
-                    double ck = 0.0;
-                    const int en = __ldg(m.colN_nnz + k);
-                    if (en >= 0) {
-                        double acc = 0.0;
-                        for (int c = __ldg(m.nnz_cptr + en); c < __ldg(m.nnz_cptr + en + 1); ++c)
-                            acc = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], acc);
-                        ck = -__ldg(m.nnz_wr + en) * acc;
+                }
+            }
+            for (int c = wg; c < m.nh; c += WPS) {       // HS_j = (1/W_j) sum_i dH_i b'_ij
+                const int ioff = __ldg(m.h_chunk + 3 * c), len = __ldg(m.h_chunk + 3 * c + 1);
+                const int *dst = m.h_dst + __ldg(m.h_chunk + 3 * c + 2) + lane;
+                const unsigned *it = m.h_items + ioff + lane;
+                const int *ax = m.h_aux + ioff + lane;
+                double acc = 0.0;
+                for (int x = 0; x < len; ++x) {
+                    const unsigned v = __ldg(it + 32 * x);
+                    acc = fma(sdH[__ldg(ax + 32 * x)], sb[v & 0xffffff], acc);
+                    if (v >> 31) {
+                        const int j = __ldg(dst);
+                        dst += 32;
+                        sHS[j] = acc * sInvW[j];
+                        acc = 0.0;
                     }
-                    sCk[k] = ck;
-                } else {
-                    const int j = item - N;
-                    double hs = 0.0;
-                    for (int e = __ldg(m.col_ptr + j); e < __ldg(m.col_ptr + j + 1); ++e)
-                        hs = fma(sdH[__ldg(m.col_rxn + e)], sb[__ldg(m.col_slot + e)], hs);
-                    sHS[j] = hs * sInvW[j];
+                }
+            }
+            for (int c = wg; c < m.ncc; c += WPS) {      // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
+                const int ioff = __ldg(m.c_chunk + 3 * c), len = __ldg(m.c_chunk + 3 * c + 1);
+                const int eoff = __ldg(m.c_chunk + 3 * c + 2) + lane;
+                const int *dst = m.c_dst + eoff;
+                const double *scl = m.c_scale + eoff;
+                const unsigned *it = m.c_items + ioff + lane;
+                double acc = 0.0;
+                for (int x = 0; x < len; ++x) {
+                    const unsigned v = __ldg(it + 32 * x);
+                    acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
+                    if (v >> 31) {
+                        sCk[__ldg(dst)] = -__ldg(scl) * acc;
+                        dst += 32;
+                        scl += 32;
+                        acc = 0.0;
+                    }
                 }
             }
             group_sync<WPS>(grp);
@@ -498,42 +544,44 @@ __global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KP
             const double HSN = sHS[N - 1], cpN = scp[N - 1];
             const double e0 = Hf * invcp * invcp;
 
-            // ---- row stage: dense FMA + sparse terms, staged per warp, streamed to HBM ----
-            const int ld = N + 1, RPC = sc.rows_per_chunk;
+            // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
+            //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
+            const int ld = N + 1, RPC = m.rpc;
             double *stage = S + sc.rows + wg * RPC * ld;
             double *Jout = p.jac + st * p.ldj;
-            for (int chunk = wg; chunk * RPC < ld; chunk += WPS) {
-                const int r0 = chunk * RPC, r1e = min(r0 + RPC, ld);
-                for (int r = r0; r < r1e; ++r) {
-                    double *row = stage + (r - r0) * ld;
-                    if (r == 0) {
-                        for (int j = lane; j <= N; j += 32)
-                            row[j] = (j == 0) ? J00
-                                   : (j == N) ? 0.0
-                                              : fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN),
-                                                    (scp[j - 1] - cpN) * e0);
-                    } else {
-                        const int k = r - 1;
-                        const double Ak = sA[k], Ck = sCk[k];
-                        for (int j = lane; j <= N; j += 32)
-                            row[j] = (j == 0) ? sJk0[k] : (j == N) ? 0.0 : fma(Ak, sDelta[j - 1], Ck);
+            for (int c = wg; c < m.n_row_chunks; c += WPS) {
+                const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+                for (int x = lane; x < nel; x += 32) {
+                    const int rr = x / ld, j = x - rr * ld, r = r0 + rr;
+                    double v;
+                    if (j == 0) v = (r == 0) ? J00 : sJk0[r - 1];
+                    else if (j == N) v = 0.0;
+                    else if (r == 0) v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
+                    else v = fma(sA[r - 1], sDelta[j - 1], sCk[r - 1]);
+                    stage[x] = v;
+                }
+                __syncwarp();
+                {
+                    const int ioff = __ldg(m.s_chunk + 3 * c), len = __ldg(m.s_chunk + 3 * c + 1);
+                    const int eoff = __ldg(m.s_chunk + 3 * c + 2) + lane;
+                    const int *dst = m.s_dst + eoff;
+                    const double *scl = m.s_scale + eoff;
+                    const unsigned *it = m.s_items + ioff + lane;
+                    double acc = 0.0;
+                    for (int x = 0; x < len; ++x) {
+                        const unsigned v = __ldg(it + 32 * x);
+                        acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
+                        if (v >> 31) {
+                            const int d = __ldg(dst);
+                            stage[d] = fma(__ldg(scl), acc, stage[d]);
+                            dst += 32;
+                            scl += 32;
+                            acc = 0.0;
+                        }
                     }
                 }
                 __syncwarp();
-                for (int r = max(r0, 1); r < r1e; ++r) {
-                    const int k = r - 1;
-                    double *row = stage + (r - r0) * ld;
-                    for (int e = __ldg(m.row_ptr + k) + lane; e < __ldg(m.row_ptr + k + 1); e += 32) {
-                        const int j = __ldg(m.nnz_col + e);
-                        if (j == N - 1) continue;
-                        double acc = 0.0;
-                        for (int c = __ldg(m.nnz_cptr + e); c < __ldg(m.nnz_cptr + e + 1); ++c)
-                            acc = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], acc);
-                        row[1 + j] = fma(__ldg(m.nnz_wr + e), acc, row[1 + j]);
-                    }
-                }
-                __syncwarp();
-                store_segment(Jout + (long long)r0 * ld, stage, (r1e - r0) * ld, lane);
+                store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
                 __syncwarp();
             }
             if (p.dydt) {
@@ -561,17 +609,17 @@ Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_ch
     sc.H = take(N);
     sc.cpk = take(N);
     sc.f = take(N);
-    sc.q = take(R);
+    sc.q = take(R + 1);
     if (jac) {
         sc.dB = take(N);
         sc.Jk0 = take(N);
         sc.A = take(N);
         sc.Ck = take(N);
         sc.HS = take(N);
-        sc.th = take(R);
-        sc.a = take(R);
-        sc.dH = take(R);
-        sc.b = take(nslot);
+        sc.th = take(R + 1);
+        sc.a = take(R + 1);
+        sc.dH = take(R + 1);
+        sc.b = take(nslot + 1);
         sc.rows_per_chunk = rows_per_chunk;
         sc.rows = take(wps * rows_per_chunk * (N + 1));
     } else {
@@ -582,7 +630,7 @@ Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_ch
     return sc;
 }
 
-int shared_const_doubles(int N) { return ((2 * N) + 1) & ~1; }
+int shared_const_doubles(int N) { return 128 + (((2 * N) + 1) & ~1); }
 
 template <bool JAC>
 static cudaError_t launch_t(const KParams &p, int wps, int blocks, size_t smem, cudaStream_t stream) {

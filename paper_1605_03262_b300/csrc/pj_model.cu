@@ -183,6 +183,108 @@ int class_key(const HRxn &x) {
 
 }  // namespace
 
+namespace {
+
+// One finished sum of a schedule: items (index, coefficient code, optional aux) summed in order
+// by a single lane, then written to dst (with scale).
+struct Task {
+    std::vector<unsigned> idx;
+    std::vector<int> code;
+    std::vector<int> aux;
+    int dst = 0;
+    double scale = 0.0;
+};
+
+// Lays out one chunk of tasks over the 32 lanes of a warp. Tasks are packed largest first onto
+// the least-loaded lane (longest-processing-time rule); each lane's items run back to back with an
+// end flag on the last item of every task; shorter lanes are padded with neutral items. Which lane
+// evaluates a task does not change its value: a task is always summed by one lane, in item order.
+void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code, int pad_aux,
+                std::vector<unsigned> &items, std::vector<int> *aux, std::vector<int> &dst,
+                std::vector<double> *scale, std::vector<int> &chunk) {
+    std::stable_sort(tasks.begin(), tasks.end(),
+                     [](const Task *a, const Task *b) { return a->idx.size() > b->idx.size(); });
+    std::vector<std::vector<const Task *>> lane(32);
+    std::vector<size_t> load(32, 0);
+    for (const Task *t : tasks) {
+        int best = 0;
+        for (int l = 1; l < 32; ++l)
+            if (load[l] < load[best]) best = l;
+        lane[best].push_back(t);
+        load[best] += t->idx.size();
+    }
+    size_t len = 0, ents = 0;
+    for (int l = 0; l < 32; ++l) {
+        len = std::max(len, load[l]);
+        ents = std::max(ents, lane[l].size());
+    }
+    const size_t ioff = items.size(), eoff = dst.size();
+    items.resize(ioff + len * 32, pad_idx | (unsigned(pad_code) << 24));
+    if (aux) aux->resize(ioff + len * 32, pad_aux);
+    dst.resize(eoff + ents * 32, 0);
+    if (scale) scale->resize(eoff + ents * 32, 0.0);
+    for (int l = 0; l < 32; ++l) {
+        size_t pos = 0, m = 0;
+        for (const Task *t : lane[l]) {
+            for (size_t q = 0; q < t->idx.size(); ++q, ++pos) {
+                unsigned v = t->idx[q] | (unsigned(t->code[q]) << 24);
+                if (q + 1 == t->idx.size()) v |= 0x80000000u;
+                items[ioff + pos * 32 + l] = v;
+                if (aux) (*aux)[ioff + pos * 32 + l] = t->aux[q];
+            }
+            dst[eoff + m * 32 + l] = t->dst;
+            if (scale) (*scale)[eoff + m * 32 + l] = t->scale;
+            ++m;
+        }
+    }
+    chunk.push_back(int(ioff));
+    chunk.push_back(int(len));
+    chunk.push_back(int(eoff));
+}
+
+// A task with no items still has to write its (zero) result: give it one neutral item.
+void ensure_nonempty(Task &t, unsigned pad_idx, int pad_code, int pad_aux) {
+    if (t.idx.empty()) {
+        t.idx.push_back(pad_idx);
+        t.code.push_back(pad_code);
+        t.aux.push_back(pad_aux);
+    }
+}
+
+// Splits tasks into chunks with at least 32 x (longest task) items each, so that the longest
+// task does not dominate its chunk; returns the chunks' task lists (balanced by item count).
+std::vector<std::vector<const Task *>> split_chunks(const std::vector<Task> &tasks) {
+    size_t total = 0, longest = 1;
+    for (auto &t : tasks) {
+        total += t.idx.size();
+        longest = std::max(longest, t.idx.size());
+    }
+    int n = int(std::max<size_t>(1, total / (32 * longest)));
+    n = std::min(n, 16);
+    std::vector<std::vector<const Task *>> out(n);
+    std::vector<size_t> load(n, 0);
+    std::vector<const Task *> order;
+    for (auto &t : tasks) order.push_back(&t);
+    std::stable_sort(order.begin(), order.end(),
+                     [](const Task *a, const Task *b) { return a->idx.size() > b->idx.size(); });
+    for (const Task *t : order) {
+        int best = 0;
+        for (int c = 1; c < n; ++c)
+            if (load[c] < load[best]) best = c;
+        out[best].push_back(t);
+        load[best] += t->idx.size();
+    }
+    return out;
+}
+
+int nu_code(double nu) {
+    const int v = int(nu);
+    if (double(v) != nu || v < -kNuBias || v >= kNuBias) throw Unsupported("net stoichiometric coefficient out of range");
+    return v + kNuBias;
+}
+
+}  // namespace
+
 // Builds the host copy of the device image. Device pointers are patched by the caller.
 HostImage build_image(const void *buf, size_t len) {
     HModel m = parse(buf, len);
@@ -403,6 +505,93 @@ HostImage build_image(const void *buf, size_t len) {
             if (l == N - 1) im.colN_nnz[k] = e;
         }
         for (int k = 0; k < N; ++k) im.row_ptr[k + 1] += im.row_ptr[k];
+    }
+
+    // lane-balanced schedules; neutral items read the zero element appended to each array
+    const unsigned zero_slot = unsigned(slot_total), zero_rxn = unsigned(R);
+    const int zero_code = kNuBias;   // nu = 0
+    if (slot_total >= (1 << 24) || R >= (1 << 24)) throw Unsupported("more than 2^24 reactions or b-slots");
+    // species gather: omega_k, J_k0, A_k from (reaction, nu_ki)
+    {
+        std::vector<Task> tasks(N);
+        for (int k = 0; k < N; ++k) {
+            tasks[k].dst = k;
+            for (int e = im.sp_ptr[k]; e < im.sp_ptr[k + 1]; ++e) {
+                tasks[k].idx.push_back(unsigned(im.sp_rxn[e]));
+                tasks[k].code.push_back(nu_code(im.sp_nu[e]));
+                tasks[k].aux.push_back(0);
+            }
+            ensure_nonempty(tasks[k], zero_rxn, zero_code, 0);
+        }
+        auto chunks = split_chunks(tasks);
+        for (auto &c : chunks) emit_chunk(c, zero_rxn, zero_code, 0, im.g_items, nullptr, im.g_dst, nullptr, im.g_chunk);
+        im.ng = int(chunks.size());
+    }
+    // energy-row column sums HS_j from (b-slot, reaction)
+    {
+        std::vector<Task> tasks(N);
+        for (int l = 0; l < N; ++l) {
+            tasks[l].dst = l;
+            for (int e = im.col_ptr[l]; e < im.col_ptr[l + 1]; ++e) {
+                tasks[l].idx.push_back(unsigned(im.col_slot[e]));
+                tasks[l].code.push_back(zero_code);
+                tasks[l].aux.push_back(im.col_rxn[e]);
+            }
+            ensure_nonempty(tasks[l], zero_slot, zero_code, R);
+        }
+        auto chunks = split_chunks(tasks);
+        for (auto &c : chunks)
+            emit_chunk(c, zero_slot, zero_code, R, im.h_items, &im.h_aux, im.h_dst, nullptr, im.h_chunk);
+        im.nh = int(chunks.size());
+    }
+    // C_k = -(W_k/W_N) sum nu_ki b'_iN, from the sparse entries of column N-1
+    {
+        std::vector<Task> tasks(N);
+        for (int k = 0; k < N; ++k) {
+            tasks[k].dst = k;
+            const int e = im.colN_nnz[k];
+            if (e >= 0) {
+                tasks[k].scale = im.nnz_wr[e];
+                for (int c = im.nnz_cptr[e]; c < im.nnz_cptr[e + 1]; ++c) {
+                    tasks[k].idx.push_back(unsigned(im.con_slot[c]));
+                    tasks[k].code.push_back(nu_code(im.con_nu[c]));
+                    tasks[k].aux.push_back(0);
+                }
+            }
+            ensure_nonempty(tasks[k], zero_slot, zero_code, 0);
+        }
+        auto chunks = split_chunks(tasks);
+        for (auto &c : chunks)
+            emit_chunk(c, zero_slot, zero_code, 0, im.c_items, nullptr, im.c_dst, &im.c_scale, im.c_chunk);
+        im.ncc = int(chunks.size());
+    }
+    // sparse block, per chunk of rpc staged rows (row r = species r-1, row 0 = energy row)
+    {
+        im.rpc = std::max(1, std::min(4, 256 / (N + 1)));
+        im.n_row_chunks = (N + 1 + im.rpc - 1) / im.rpc;
+        for (int c = 0; c < im.n_row_chunks; ++c) {
+            const int r0 = c * im.rpc, r1 = std::min(r0 + im.rpc, N + 1);
+            std::vector<Task> tasks;
+            for (int r = std::max(r0, 1); r < r1; ++r) {
+                const int k = r - 1;
+                for (int e = im.row_ptr[k]; e < im.row_ptr[k + 1]; ++e) {
+                    const int j = im.nnz_col[e];
+                    if (j == N - 1) continue;
+                    Task t;
+                    t.dst = (r - r0) * (N + 1) + 1 + j;
+                    t.scale = im.nnz_wr[e];
+                    for (int q = im.nnz_cptr[e]; q < im.nnz_cptr[e + 1]; ++q) {
+                        t.idx.push_back(unsigned(im.con_slot[q]));
+                        t.code.push_back(nu_code(im.con_nu[q]));
+                        t.aux.push_back(0);
+                    }
+                    tasks.push_back(std::move(t));
+                }
+            }
+            std::vector<const Task *> ptrs;
+            for (auto &t : tasks) ptrs.push_back(&t);
+            emit_chunk(ptrs, zero_slot, zero_code, 0, im.s_items, nullptr, im.s_dst, &im.s_scale, im.s_chunk);
+        }
     }
     return im;
 }
