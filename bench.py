@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from paper_1605_03262_b300 import synth  # noqa: E402
+from paper_1605_03262_b300 import autotune, synth  # noqa: E402
 
 METRIC = "Jacobians/sec (FP64, 1 B300) per mechanism size vs roofline; p50/p99 serving latency"
 UNIT = "Jacobians/s"
@@ -291,7 +291,9 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     model = synth.config_model(cfg)
     T, P, Y = synth.config_states(cfg, n_states, seed_offset=1000 + rank)
     n, N = Y.shape
-    g = pj.Model(synth.to_bytes(model))
+    blob = synth.to_bytes(model)
+    g = pj.Model(blob)
+    tune = autotune.autotune(g, blob, use_cache=False)
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
     J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
@@ -308,7 +310,8 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": cal["fp64_tflops"], "unit": "TFLOP/s",
                      "frac": achieved / cal["fp64_tflops"] if cal["fp64_tflops"] else None},
         "hbm_write_gbs": n * (N + 1) ** 2 * 8 / (ms_mean * 1e-3) / 1e9,
-        "launch": {"warps_per_state": launch[0], "states_per_cta": launch[1], "ctas_per_sm": launch[2]},
+        "launch": {"warps_per_state": launch[0], "states_per_cta": launch[1], "ctas_per_sm": launch[2],
+                   "chosen_by": "autotuner (%d probe states)" % tune.get("n_probe", 0)},
     }
     del J, flush
     return res, (g, model, T, P, Y, Td, Pd, Yd)
@@ -475,7 +478,9 @@ def run_profile_case(spec: str, warmup: int):
     torch.cuda.set_device(0)
     model = synth.config_model(cfg)
     T, P, Y = synth.config_states(cfg, n, seed_offset=1000)
-    g = pj.Model(synth.to_bytes(model))
+    blob = synth.to_bytes(model)
+    g = pj.Model(blob)
+    autotune.autotune(g, blob, use_cache=False)
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
     J = torch.empty((n, model.n_species + 1, model.n_species + 1), dtype=torch.float64, device="cuda")
     for _ in range(warmup + 1):

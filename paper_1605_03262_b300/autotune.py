@@ -1,0 +1,127 @@
+"""Launch-shape autotuner for the evaluation kernels.
+
+A launch shape is (warps per state, states per CTA, CTAs per SM). Results are bitwise identical
+for every shape (fixed-order reductions and per-lane schedules), so the tuner only times: it
+evaluates a probe batch with each feasible shape and keeps the fastest. Choices are cached per
+(model bytes, device name, kernel) in a JSON file (``$PYJAC_B300_CACHE`` or
+``~/.cache/pyjac_b300/autotune.json``).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import threading
+from typing import Dict, List, Optional, Sequence, Tuple
+
+__all__ = ["candidate_shapes", "autotune", "cache_path"]
+
+_lock = threading.Lock()
+
+Shape = Tuple[int, int, int]
+
+
+def cache_path() -> str:
+    return os.environ.get("PYJAC_B300_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "pyjac_b300", "autotune.json"))
+
+
+def _load_cache() -> Dict[str, list]:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(cache: Dict[str, list]) -> None:
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + ".tmp.%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def candidate_shapes(model, which: str = "jacobian") -> List[Shape]:
+    """Every (warps per state, states per CTA, 1) the library accepts for this model."""
+    out = []
+    for wps in (1, 2, 4, 8, 16):
+        for groups in range(1, 17):
+            if wps * 32 * groups > 512 or (wps > 1 and groups > 15):
+                continue
+            try:
+                model.launch_smem_bytes(wps, groups, 1, which=which)
+                model.set_launch(wps, groups, 1, which=which)
+            except Exception:
+                continue
+            out.append((wps, groups, 1))
+    return out
+
+
+def _key(model, blob_digest: str, which: str) -> str:
+    import torch
+    name = torch.cuda.get_device_name(model.device)
+    return "%s|%s|%s" % (blob_digest, name, which)
+
+
+def autotune(model, blob: bytes, which: str = "jacobian", probe: Optional[Sequence] = None,
+             n_probe: int = 0, reps: int = 2, use_cache: bool = True, shapes: Optional[List[Shape]] = None
+             ) -> Dict[str, object]:
+    """Time the candidate shapes on a probe batch, set the fastest on ``model`` and return a report.
+
+    probe: optional (T, P, Y) device tensors; else a synthetic batch of n_probe states (default:
+    enough states to fill every SM several times over) is drawn."""
+    import torch
+    from . import synth
+    digest = hashlib.sha1(blob).hexdigest()
+    key = _key(model, digest, which)
+    if use_cache and shapes is None:
+        with _lock:
+            hit = _load_cache().get(key)
+        if hit:
+            try:
+                model.set_launch(*hit, which=which)
+                return {"shape": tuple(hit), "cached": True}
+            except Exception:
+                pass
+    cands = shapes if shapes is not None else candidate_shapes(model, which)
+    if not cands:
+        raise RuntimeError("no feasible launch shape for this model")
+    if probe is None:
+        sms = torch.cuda.get_device_properties(model.device).multi_processor_count
+        n = n_probe or max(4096, sms * 16 * 8)
+        N = model.n_species
+        budget = 2 << 30                                          # keep the probe output under 2 GB
+        n = max(sms, min(n, budget // (8 * (N + 1) ** 2)))
+        T, P, Y = synth.generate_states(N, n, seed=12345)
+        probe = tuple(torch.as_tensor(a, dtype=torch.float64, device=model.device) for a in (T, P, Y))
+    T, P, Y = probe
+    n, N = Y.shape[0], model.n_species
+    out = (torch.empty((n, N + 1, N + 1), dtype=torch.float64, device=model.device) if which == "jacobian"
+           else torch.empty((n, N + 1), dtype=torch.float64, device=model.device))
+    fn = model.eval_jacobian if which == "jacobian" else model.eval_dydt
+    timings = {}
+    for shape in cands:
+        model.set_launch(*shape, which=which)
+        fn(T, P, Y, out=out)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn(T, P, Y, out=out)
+        e.record()
+        torch.cuda.synchronize()
+        timings[shape] = s.elapsed_time(e) / reps
+    best = min(timings, key=timings.get)
+    model.set_launch(*best, which=which)
+    if use_cache:
+        with _lock:
+            cache = _load_cache()
+            cache[key] = list(best)
+            _store_cache(cache)
+    return {"shape": best, "cached": False, "ms": timings[best], "n_probe": n,
+            "timings": {"%d,%d,%d" % k: v for k, v in sorted(timings.items(), key=lambda kv: kv[1])[:8]}}

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 SOURCES = ["pj_model.cu", "pj_kernels.cu", "pj_api.cu", "pj_host.cu"]
-HEADERS = ["pj_internal.h"]
+HEADERS = ["pj_internal.h", "pj_fastmath.cuh"]
 LIB = os.path.join(HERE, "libpyjacb300.so")
 CALIB_SRC = "pj_calib.cu"
 CALIB_LIB = os.path.join(HERE, "libpjcalib.so")
@@ -34,7 +34,8 @@ def needs_build() -> bool:
 def build_calib(force: bool = False) -> str:
     """Measurement kernels for the benchmark's roofline denominators (libpjcalib.so)."""
     src = os.path.join(SRC_DIR, CALIB_SRC)
-    if not force and os.path.exists(CALIB_LIB) and os.path.getmtime(CALIB_LIB) >= os.path.getmtime(src):
+    deps = [src, os.path.join(SRC_DIR, "pj_fastmath.cuh")]
+    if not force and os.path.exists(CALIB_LIB) and os.path.getmtime(CALIB_LIB) >= max(map(os.path.getmtime, deps)):
         return CALIB_LIB
     tmp = CALIB_LIB + ".tmp.%d" % os.getpid()
     cmd = [os.environ.get("NVCC", "nvcc")] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",

@@ -79,7 +79,8 @@ pj::LaunchCfg default_cfg(const pj_mech *m, bool jac, int wps) {
 
 pj::LaunchCfg pick_default(const pj_mech *m, bool jac) {
     const int N = m->N;
-    int wps = jac ? (N <= 64 ? 1 : N <= 160 ? 2 : N <= 320 ? 4 : 8) : (N <= 128 ? 1 : 2);
+    // measured on B300: two warps per state up to ~100 species, then wider groups
+    int wps = jac ? (N <= 24 ? 1 : N <= 96 ? 2 : N <= 200 ? 4 : 16) : (N <= 128 ? 1 : 2);
     pj::LaunchCfg c = default_cfg(m, jac, wps);
     while (c.groups == 0 && wps < 16) {   // grow the group until one state fits
         wps *= 2;

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "pj_fastmath.cuh"
+
 namespace {
 
 constexpr int kChains = 8;
@@ -49,6 +51,17 @@ __global__ void store_only(double2 *p, size_t n2) {
     z.x = 0.0;
     z.y = 0.0;
     for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n2; i += stride) __stcs(p + i, z);
+}
+
+__global__ void fastmath_check(const double *x, int n, const pj::MathTables *tb, double *e_fast, double *e_lib,
+                               double *l_fast, double *l_lib) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = x[i];
+        e_fast[i] = pj::fast_exp(v, tb);
+        e_lib[i] = exp(v);
+        l_fast[i] = pj::fast_log(v, tb);
+        l_lib[i] = log(v);
+    }
 }
 
 int sms() {
@@ -107,6 +120,21 @@ __attribute__((visibility("default"))) int pjc_fp64_func_rate(int op, int iters,
     if (e != cudaSuccess || ms <= 0.f) return -1;
     *calls_per_s = 4.0 * double(iters) * threads * blocks / (ms * 1e-3);
     return 0;
+}
+
+// The table-driven exp/log of the Jacobian kernels next to CUDA's exp/log on device array x[n]
+// (all pointers device pointers), for the accuracy test.
+__attribute__((visibility("default"))) int pjc_fastmath_check(const double *x, int n, double *e_fast, double *e_lib,
+                                                              double *l_fast, double *l_lib) {
+    pj::MathTables h;
+    pj::build_math_tables(h);
+    pj::MathTables *d = nullptr;
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) return -1;
+    cudaMemcpy(d, &h, sizeof(h), cudaMemcpyHostToDevice);
+    fastmath_check<<<sms() * 4, 256>>>(x, n, d, e_fast, e_lib, l_fast, l_lib);
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(d);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 // Store-only bandwidth (GB/s, bytes written) over a buffer of the given size.

@@ -112,11 +112,86 @@ __device__ __forceinline__ void third_body(const DevModel &m, const RxnDev &d, c
     }
 }
 
+// One side of a reaction: the concentration product P = prod [X]^nu, its partial derivatives
+// S_x = dP/d[X_x] (formed from the other factors, never by dividing by [X], Section 3.1), and the
+// side's sums of nu B_k, nu dB_k/dT (equilibrium constant, Section 2.3.1) and nu H_k (energy row).
+struct Side {
+    double P, S[kMaxSlots], sB, sdB, sH;
+};
+
+template <int NS, bool JAC>
+__device__ __forceinline__ void side(const int16_t *sp, const int8_t *nu, const double *C, const double *B,
+                                     const double *dB, const double *H, const double *sNu, bool kc, Side &o) {
+    double p[NS], d[NS];
+    o.sB = 0.0;
+    o.sdB = 0.0;
+    o.sH = 0.0;
+#pragma unroll
+    for (int x = 0; x < NS; ++x) {
+        const int k = sp[x], v = nu[x];
+        const double c = C[k];
+        if (v == 1) {
+            p[x] = c;
+            d[x] = 1.0;
+        } else {
+            const double c2 = c * c;
+            if (v == 2) {
+                p[x] = c2;
+                d[x] = 2.0 * c;
+            } else if (v == 3) {
+                p[x] = c2 * c;
+                d[x] = 3.0 * c2;
+            } else {
+                p[x] = c2 * c2;
+                d[x] = 4.0 * c2 * c;
+            }
+        }
+        const double vd = sNu[v + kNuBias];
+        if (kc) {
+            o.sB = fma(vd, B[k], o.sB);
+            if constexpr (JAC) o.sdB = fma(vd, dB[k], o.sdB);
+        }
+        if constexpr (JAC) o.sH = fma(vd, H[k], o.sH);
+    }
+    if constexpr (NS == 1) {
+        o.P = p[0];
+        o.S[0] = d[0];
+    } else if constexpr (NS == 2) {
+        o.P = p[0] * p[1];
+        o.S[0] = d[0] * p[1];
+        o.S[1] = d[1] * p[0];
+    } else if constexpr (NS == 3) {
+        const double p01 = p[0] * p[1];
+        o.P = p01 * p[2];
+        o.S[0] = d[0] * (p[1] * p[2]);
+        o.S[1] = d[1] * (p[0] * p[2]);
+        o.S[2] = d[2] * p01;
+    } else {
+        const double p01 = p[0] * p[1], p23 = p[2] * p[3];
+        o.P = p01 * p23;
+        o.S[0] = d[0] * (p[1] * p23);
+        o.S[1] = d[1] * (p[0] * p23);
+        o.S[2] = d[2] * (p[3] * p01);
+        o.S[3] = d[3] * (p[2] * p01);
+    }
+}
+
+template <bool JAC>
+__device__ __forceinline__ void side_n(int n, const int16_t *sp, const int8_t *nu, const double *C, const double *B,
+                                       const double *dB, const double *H, const double *sNu, bool kc, Side &o) {
+    switch (n) {
+    case 1: side<1, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    case 2: side<2, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    case 3: side<3, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    default: side<4, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    }
+}
+
 // Reaction i: rate of progress q_i and, for the Jacobian, theta_i, a_i, dH_i and the b-slots.
 template <bool JAC>
 __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateScalars &s, const double *C,
-                                         const double *B, const double *dB, const double *H, double *sq,
-                                         double *sth, double *sa, double *sdH, double *sb) {
+                                         const double *B, const double *dB, const double *H, const double *sNu,
+                                         double *sq, double *sth, double *sa, double *sdH, double *sb) {
     RxnDev d;
     {
         const int4 *src = reinterpret_cast<const int4 *>(m.rx + i);
@@ -124,6 +199,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
 #pragma unroll
         for (int w = 0; w < 4; ++w) dst[w] = __ldg(src + w);
     }
+    const MathTables *tb = m.tables;
     const double *par = m.par + d.par_off;
     const double T = s.T, invT = s.invT, lnT = s.lnT;
     double lnkf = 0.0, dlnkf = 0.0, kf = 0.0;
@@ -141,7 +217,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             for (int x = 0; x < (d.kpow >= 0 ? d.kpow : -d.kpow); ++x) tp *= base;
             kf = __ldg(par + 3) * tp;
         } else {
-            kf = exp(lnkf);
+            kf = fast_exp(lnkf, tb);
         }
         rev_off = 4;
         if (d.kind == kThird) {
@@ -158,26 +234,26 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         const double dlnki = fma(__ldg(par + 5), invT, __ldg(par + 4)) * invT;
         double M;
         third_body(m, d, C, s.Ctot, M, E);
-        const double ratio = exp(lnk0 - lnki);
+        const double ratio = fast_exp(lnk0 - lnki, tb);
         const double Pr = ratio * M;
         double F = 1.0, phiF = 0.0, tauF = 0.0;   // F, dlnF/dlnPr, dlnF/dT at fixed Pr
         if (d.ftype == kTroe) {
             const double a = __ldg(par + 6), iT3 = __ldg(par + 7), iT1 = __ldg(par + 8), T2 = __ldg(par + 9);
-            const double e3 = exp(-T * iT3), e1 = exp(-T * iT1);
+            const double e3 = fast_exp(-T * iT3, tb), e1 = fast_exp(-T * iT1, tb);
             double Fc = fma(1.0 - a, e3, a * e1);
             double dFc = -(1.0 - a) * iT3 * e3 - a * iT1 * e1;
             if (d.flags & 1) {
-                const double e2 = exp(-T2 * invT);
+                const double e2 = fast_exp(-T2 * invT, tb);
                 Fc += e2;
                 dFc = fma(T2 * invT * invT, e2, dFc);
             }
-            const double lnFc = log(Fc), lFc = lnFc * kInvLn10;
-            const double lPr = log(fmax(Pr, 1e-300)) * kInvLn10;
+            const double lnFc = fast_log(Fc, tb), lFc = lnFc * kInvLn10;
+            const double lPr = fast_log(fmax(Pr, 1e-300), tb) * kInvLn10;
             const double At = lPr - 0.67 * lFc - 0.4;
             const double Bt = 0.806 - 1.1762 * lFc - 0.14 * lPr;
             const double iB = 1.0 / Bt, r = At * iB;
             const double g = 1.0 / fma(r, r, 1.0);
-            F = exp(lnFc * g);
+            F = fast_exp(lnFc * g, tb);
             if constexpr (JAC) {
                 const double g2r = -2.0 * g * g * r * iB;
                 phiF = lnFc * g2r * fma(0.14, r, 1.0) * kInvLn10;
@@ -187,12 +263,12 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         } else if (d.ftype == kSri) {
             const double a = __ldg(par + 6), b = __ldg(par + 7), ic = __ldg(par + 8), lnd = __ldg(par + 9),
                          e = __ldg(par + 10);
-            const double lPr = log(fmax(Pr, 1e-300)) * kInvLn10;
+            const double lPr = fast_log(fmax(Pr, 1e-300), tb) * kInvLn10;
             const double X = 1.0 / fma(lPr, lPr, 1.0);
-            const double e1 = exp(-b * invT), e2 = exp(-T * ic);
+            const double e1 = fast_exp(-b * invT, tb), e2 = fast_exp(-T * ic, tb);
             const double base = fma(a, e1, e2);
-            const double lnb = log(base);
-            F = exp(fma(X, lnb, fma(e, lnT, lnd)));
+            const double lnb = fast_log(base, tb);
+            F = fast_exp(fma(X, lnb, fma(e, lnT, lnd)), tb);
             if constexpr (JAC) {
                 phiF = -2.0 * X * X * lPr * lnb * kInvLn10;
                 tauF = fma(X * fma(a * b * invT * invT, e1, -ic * e2), 1.0 / base, e * invT);
@@ -214,7 +290,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             const double Mg = M > 0.0 ? M : 1e-300;
             psi = F * iPr1 * (phiF / Mg - ratio * iPr1);
         }
-        kf = exp(lnkf);
+        kf = fast_exp(lnkf, tb);
         dcdT = c * fma(phi, dlnk0 - dlnki - invT, tauF);
         rev_off = 11;
     } else if (d.kind == kPlog) {
@@ -240,7 +316,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         const double d2 = fma(__ldg(b + 4), invT, __ldg(b + 3)) * invT;
         lnkf = fma(lk2 - lk1, fr, lk1);
         dlnkf = fma(d2 - d1, fr, d1);
-        kf = exp(lnkf);
+        kf = fast_exp(lnkf, tb);
         rev_off = 1 + 5 * n;
     } else {   // Chebyshev, Eq. e:cheb; derivative via d T_n/dx = n U_{n-1}
         const int nt = int(__ldg(par + 0)), npc = int(__ldg(par + 1));
@@ -259,7 +335,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
                 p0 = pn;
             }
             lk = fma(ct, T0, lk);
-            dlk = fma(ct * double(x), Um1, dlk);
+            dlk = fma(ct * sNu[x + kNuBias], Um1, dlk);
             const double Tn = (x == 0) ? Tt : 2.0 * Tt * T0 - Tm1;
             Tm1 = T0;
             T0 = Tn;
@@ -269,50 +345,36 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         }
         lnkf = lk * kLn10;
         dlnkf = kLn10 * dlk * (-2.0 * invT * invT) * __ldg(par + 3);
-        kf = exp(lnkf);
+        kf = fast_exp(lnkf, tb);
         rev_off = 6 + nt * npc;
     }
 
-    // reverse rate coefficient (Section 2.3.1)
-    double kr = 0.0, dlnkr = 0.0;
-    double nf = 0.0, nb = 0.0;
+    // concentration products, their partial derivatives, and the equilibrium-constant sums
+    const bool kc = d.rev == kRevKc;
+    Side sf, sr;
+    side_n<JAC>(d.nr, d.rsp, d.rnu, C, B, dB, H, sNu, kc, sf);
+    side_n<JAC>(d.np, d.psp, d.pnu, C, B, dB, H, sNu, kc, sr);
+    int inf = 0, inb = 0;
 #pragma unroll
     for (int x = 0; x < kMaxSlots; ++x) {
-        nf += x < d.nr ? double(d.rnu[x]) : 0.0;
-        nb += x < d.np ? double(d.pnu[x]) : 0.0;
+        inf += x < d.nr ? d.rnu[x] : 0;
+        inb += x < d.np ? d.pnu[x] : 0;
     }
-    if (d.rev == kRevKc) {
-        double sB = 0.0, sdB = 0.0;
-#pragma unroll
-        for (int x = 0; x < kMaxSlots; ++x) {
-            if (x < d.np) {
-                sB = fma(double(d.pnu[x]), B[d.psp[x]], sB);
-                if constexpr (JAC) sdB = fma(double(d.pnu[x]), dB[d.psp[x]], sdB);
-            }
-            if (x < d.nr) {
-                sB = fma(-double(d.rnu[x]), B[d.rsp[x]], sB);
-                if constexpr (JAC) sdB = fma(-double(d.rnu[x]), dB[d.rsp[x]], sdB);
-            }
-        }
-        const double lnKc = fma(nb - nf, m.lnPatmR, sB);
-        kr = exp(lnkf - lnKc);
-        dlnkr = dlnkf - sdB;
+    const double nf = sNu[inf + kNuBias], nb = sNu[inb + kNuBias];
+
+    // reverse rate coefficient (Section 2.3.1)
+    double kr = 0.0, dlnkr = 0.0;
+    if (kc) {
+        const double lnKc = fma(sNu[inb - inf + kNuBias], m.lnPatmR, sr.sB - sf.sB);
+        kr = fast_exp(lnkf - lnKc, tb);
+        dlnkr = dlnkf - (sr.sdB - sf.sdB);
     } else if (d.rev == kRevExplicit) {
         const double *pr = par + rev_off;
-        kr = exp(fma(__ldg(pr + 1), lnT, __ldg(pr + 0)) - __ldg(pr + 2) * invT);
+        kr = fast_exp(fma(__ldg(pr + 1), lnT, __ldg(pr + 0)) - __ldg(pr + 2) * invT, tb);
         dlnkr = fma(__ldg(pr + 2), invT, __ldg(pr + 1)) * invT;
     }
 
-    // concentration products and their partial derivatives (no division by [X])
-    double pwf[kMaxSlots], pwb[kMaxSlots];
-#pragma unroll
-    for (int x = 0; x < kMaxSlots; ++x) {
-        pwf[x] = x < d.nr ? ipow(C[d.rsp[x]], d.rnu[x]) : 1.0;
-        pwb[x] = x < d.np ? ipow(C[d.psp[x]], d.pnu[x]) : 1.0;
-    }
-    const double Pf = (pwf[0] * pwf[1]) * (pwf[2] * pwf[3]);
-    const double Pb = (pwb[0] * pwb[1]) * (pwb[2] * pwb[3]);
-    const double Rf = kf * Pf, Rr = kr * Pb, Rn = Rf - Rr;
+    const double Rf = kf * sf.P, Rr = kr * sr.P, Rn = Rf - Rr;
     const double q = c * Rn;
     sq[i] = q;
     if constexpr (!JAC) return;
@@ -321,34 +383,16 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
     sth[i] = fma(dcdT, Rn, fma(c, dRdT, q * invT));
     const double sigma = fma(nf, Rf, -nb * Rr);
     sa[i] = -s.W * fma(c, sigma, psi * Rn * E);
-    double dH = 0.0;
-#pragma unroll
-    for (int x = 0; x < kMaxSlots; ++x) {
-        if (x < d.np) dH = fma(double(d.pnu[x]), H[d.psp[x]], dH);
-        if (x < d.nr) dH = fma(-double(d.rnu[x]), H[d.rsp[x]], dH);
-    }
-    sdH[i] = dH;
-    double Sf[kMaxSlots], Sb[kMaxSlots];
-#pragma unroll
-    for (int x = 0; x < kMaxSlots; ++x) {
-        double of = 1.0, ob = 1.0;
-#pragma unroll
-        for (int y = 0; y < kMaxSlots; ++y)
-            if (y != x) {
-                of *= pwf[y];
-                ob *= pwb[y];
-            }
-        Sf[x] = x < d.nr ? kf * dipow(C[d.rsp[x]], d.rnu[x]) * of : 0.0;
-        Sb[x] = x < d.np ? kr * dipow(C[d.psp[x]], d.pnu[x]) * ob : 0.0;
-    }
-    const double psiR = psi * Rn;
+    sdH[i] = sr.sH - sf.sH;
+    // b'_il = c (k_f dP'/d[X_l] - k_r dP''/d[X_l]) + psi R eps_il
+    const double ckf = c * kf, ckr = c * kr, psiR = psi * Rn;
     for (int x = 0; x < d.nslot; ++x) {
         const int info = __ldg(m.slot_info + d.slot_off + x);
         const int rs = ((info >> 16) & 0xff) - 1, ps = ((info >> 24) & 0xff) - 1;
         double G = 0.0;
-        if (rs >= 0) G = sel4(Sf, rs);
-        if (ps >= 0) G -= sel4(Sb, ps);
-        sb[d.slot_off + x] = fma(c, G, psiR * __ldg(m.slot_eps + d.slot_off + x));
+        if (rs >= 0) G = ckf * sel4(sf.S, rs);
+        if (ps >= 0) G = fma(-ckr, sel4(sr.S, ps), G);
+        sb[d.slot_off + x] = fma(psiR, __ldg(m.slot_eps + d.slot_off + x), G);
     }
 }
 
@@ -370,7 +414,7 @@ __device__ __forceinline__ void store_segment(double *g, const double *sbuf, int
 }
 
 template <bool JAC, int WPS>
-__global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__ KParams p) {
     extern __shared__ __align__(16) double smem[];
     const DevModel &m = p.m;
     const int N = m.N, R = m.R;
@@ -407,7 +451,7 @@ __global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KP
         s.T = __ldg(p.T + st);
         s.P = __ldg(p.P + st);
         s.invT = 1.0 / s.T;
-        s.lnT = log(s.T);
+        s.lnT = fast_log(s.T, m.tables);
         const double *Ys = p.Y + st * p.ldy;
         double *sY = sf;   // Y parks in the f array until the concentrations exist
         for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
@@ -434,12 +478,12 @@ __global__ void __launch_bounds__(512) pj_eval_kernel(const __grid_constant__ KP
         s.W = 1.0 / sYW;
         s.Ctot = s.P / (kR * s.T);
         s.rho = s.Ctot * s.W;
-        s.lnP = log(s.P);
+        s.lnP = fast_log(s.P, m.tables);
         for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
         group_sync<WPS>(grp);
 
         // ---- reaction stage ----
-        for (int i = t; i < R; i += G) reaction<JAC>(m, i, s, sC, sB, sdB, sH, sq, sth, sa, sdH, sb);
+        for (int i = t; i < R; i += G) reaction<JAC>(m, i, s, sC, sB, sdB, sH, sNu, sq, sth, sa, sdH, sb);
         group_sync<WPS>(grp);
 
         const double invrho = 1.0 / s.rho;

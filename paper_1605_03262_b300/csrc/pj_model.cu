@@ -176,9 +176,15 @@ std::vector<std::pair<int, int>> distinct(const std::vector<std::pair<int, int>>
 }
 
 int class_key(const HRxn &x) {
-    // kind first, then falloff form, third-body mode and reversibility: warp-uniform branches
-    int k = x.kind * 64 + x.ftype * 16 + x.tbmode * 4 + x.rev;
-    return k;
+    // kind first, then falloff form, third-body mode, reversibility and the number of distinct
+    // species on each side: the 32 reactions of a warp mostly take the same branches
+    auto ndist = [](const std::vector<std::pair<int, int>> &v) {
+        std::vector<int> s;
+        for (auto &e : v)
+            if (std::find(s.begin(), s.end(), e.first) == s.end()) s.push_back(e.first);
+        return int(s.size());
+    };
+    return ((((x.kind * 4 + x.ftype) * 4 + x.tbmode) * 4 + x.rev) * 8 + ndist(x.reac)) * 8 + ndist(x.prod);
 }
 
 }  // namespace
