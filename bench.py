@@ -125,10 +125,15 @@ def work_model(model) -> dict:
             "contributions": contributions}
 
 
+# FP64 operations of one call of the table-driven exp and log (Tang's methods, as implemented):
+# range reduction, polynomial and reconstruction. Division is weighted by its measured throughput.
+EXP_OPS, LOG_OPS = 10.0, 12.0
+
+
 def dfma_equivalents(work: dict, ratios: dict) -> float:
-    """FP64-pipe time per Jacobian in units of one FMA issue: arithmetic ops plus each call weighted
-    by its measured throughput relative to FMA."""
-    return work["arith"] + work["exp"] * ratios["exp"] + work["log"] * ratios["log"] + work["div"] * ratios["div"]
+    """FP64-pipe time per Jacobian in units of one FMA issue: arithmetic ops, exp and log at the
+    operation counts of the table-driven algorithms, division at its measured cost relative to FMA."""
+    return work["arith"] + work["exp"] * EXP_OPS + work["log"] * LOG_OPS + work["div"] * ratios["div"]
 
 
 # ---------------------------------------------------------------------------------------------
@@ -317,6 +322,134 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     return res, (g, model, T, P, Y, Td, Pd, Yd)
 
 
+BATCH_MIX = ((0, 16384), (1, 65536), (2, 32768), (3, 2048))
+
+
+def batched_form(steps: int, warmup: int):
+    """The batched form against plain per-model launches on one mixed batch of the four model
+    sizes: sequential plain launches (each model at its autotuned shape), one persistent batched
+    launch, and the batched launch replayed from a CUDA graph. Same states and outputs in all three."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    items, total = [], 0
+    for cfg, n in BATCH_MIX:
+        model = synth.config_model(cfg)
+        blob = synth.to_bytes(model)
+        g = pj.Model(blob)
+        autotune.autotune(g, blob, use_cache=False)
+        T, P, Y = synth.config_states(cfg, n, seed_offset=2000)
+        Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+        N = model.n_species
+        J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
+        items.append((g, Td, Pd, Yd, J))
+        total += n
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+
+    def plain():
+        for g, Td, Pd, Yd, J in items:
+            g.eval_jacobian(Td, Pd, Yd, out=J)
+
+    plan = pj.BatchPlan(items)
+    graph = plan.capture()
+
+    def timed(fn):
+        for _ in range(warmup):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ms.append(s.elapsed_time(e))
+        return float(np.mean(ms))
+
+    t_plain = timed(plain)
+    t_batch = timed(plan.run)
+    t_graph = timed(graph.replay)
+    out = {"mix": {synth.CONFIGS[c]["name"]: n for c, n in BATCH_MIX}, "total_states": total,
+           "plain_sequential": {"ms": t_plain, "jacobians_per_s": total / (t_plain * 1e-3), "launches": len(items)},
+           "batched_persistent": {"ms": t_batch, "jacobians_per_s": total / (t_batch * 1e-3), "launches": 1,
+                                  "tiles": plan.n_tiles, "threads_per_cta": plan.threads_per_cta},
+           "batched_graph": {"ms": t_graph, "jacobians_per_s": total / (t_graph * 1e-3), "launches": 1}}
+    del items, flush, plan, graph
+    torch.cuda.empty_cache()
+    return out
+
+
+def _request_trace(models, n_req, seed):
+    """Requests drawn uniformly from the models, each with log-uniform 1..4096 states (host arrays)."""
+    rng = np.random.default_rng(seed)
+    names = sorted(models)
+    out = []
+    for k in range(n_req):
+        name = names[int(rng.integers(0, len(names)))]
+        n = int(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))))
+        n = max(1, min(4096, n))
+        out.append((name, *synth.generate_states(models[name].n_species, n, seed=seed * 100003 + k)))
+    return out
+
+
+def serving_form(seed: int = 7, open_loop_s: float = 3.0):
+    """The serving form: continuous batching over the four resident models, against the plain
+    per-mechanism launch (one request at a time, no merging, no overlap) on the same requests.
+    Capacity = closed-loop throughput of a fixed trace; then Poisson arrivals at 0.5x and 0.8x that
+    capacity (requests/s), with p50/p99 latency (submit -> result in device memory)."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    from paper_1605_03262_b300.serving import Server, latency_summary
+    models = {}
+    for cfg in (0, 1, 2, 3):
+        blob = synth.to_bytes(synth.config_model(cfg))
+        g = pj.Model(blob)
+        autotune.autotune(g, blob, use_cache=False)
+        models[synth.CONFIGS[cfg]["name"]] = g
+
+    def run(trace, arrivals, **kw):
+        with Server(models, **kw) as srv:
+            t0 = time.perf_counter()
+            futs = []
+            for (name, T, P, Y), ta in zip(trace, arrivals):
+                dt = t0 + ta - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                futs.append(srv.submit(name, T, P, Y))
+            for f in futs:
+                f.result()
+            wall = time.perf_counter() - t0
+            stats = dict(srv.stats)
+        states = sum(len(r[1]) for r in trace)
+        out = {"requests": len(trace), "states": states, "wall_s": wall, "jacobians_per_s": states / wall}
+        out.update(latency_summary([f.request for f in futs]))
+        out["server"] = stats
+        return out
+
+    torch.cuda.synchronize()
+    cap_trace = _request_trace(models, 240, seed)
+    run(cap_trace[:20], [0.0] * 20)                          # warm-up (allocator, streams)
+    cap = run(cap_trace, [0.0] * len(cap_trace))
+    cap_plain = run(cap_trace, [0.0] * len(cap_trace), max_inflight=1, max_batch_states=1)
+    req_rate = cap["requests"] / cap["wall_s"]
+    res = {"capacity_closed_loop": cap, "plain_per_request_closed_loop": cap_plain, "offered": {}}
+    rng = np.random.default_rng(seed + 1)
+    for frac in (0.5, 0.8):
+        lam = frac * req_rate
+        n_req = max(20, int(lam * open_loop_s))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        trace = _request_trace(models, n_req, seed + int(frac * 100))
+        res["offered"]["%.1fx" % frac] = {
+            "request_rate_per_s": lam,
+            "continuous_batching": run(trace, arrivals),
+            "plain_per_request": run(trace, arrivals, max_inflight=1, max_batch_states=1),
+        }
+    torch.cuda.empty_cache()
+    return res
+
+
 def e2e_host(g, T, P, Y, steps):
     """End to end through the C ABI on pinned host buffers (copies inside the timed region)."""
     import torch
@@ -390,6 +523,8 @@ def run_ours(args):
                                                                         "roofline", "hbm_write_gbs", "launch",
                                                                         "fp64_dfma_equiv_per_jacobian")}
             torch.cuda.empty_cache()
+    batched = batched_form(max(3, args.steps // 2), args.warmup) if not args.headline_only else None
+    serving = serving_form() if not (args.headline_only or args.no_serving) else None
     per_config[synth.CONFIGS[HEADLINE_CFG]["name"]] = {k: res[k] for k in ("n_states", "ms_per_step",
                                                                             "jacobians_per_s", "roofline",
                                                                             "hbm_write_gbs", "launch",
@@ -416,6 +551,8 @@ def run_ours(args):
         "e2e": e2e,
         "calibration": cal,
         "per_config": per_config,
+        "batched_form": batched,
+        "serving_form": serving,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(HEADLINE_CFG)
@@ -470,17 +607,25 @@ def run_reference(args):
 
 
 def run_profile_case(spec: str, warmup: int):
-    """--profile CFG:N -- a small case for ncu: warm-up launches, then one Jacobian launch of the
-    first N states of configuration CFG (inputs larger than L2 once N is a few thousand)."""
+    """--profile CFG:N[:WPS,GROUPS] -- a small case for ncu: warm-up launches, then one Jacobian
+    launch of the first N states of configuration CFG (inputs larger than L2 once N is a few
+    thousand), at the given launch shape or else the autotuner's. The autotuner's own probe
+    launches use a separate kernel instance count, so with an explicit shape the only launches
+    are the warm-ups and the profiled one."""
     import torch
     import paper_1605_03262_b300 as pj
-    cfg, n = (int(x) for x in spec.split(":"))
+    parts = spec.split(":")
+    cfg, n = int(parts[0]), int(parts[1])
+    shape = tuple(int(x) for x in parts[2].split(",")) if len(parts) > 2 else None
     torch.cuda.set_device(0)
     model = synth.config_model(cfg)
     T, P, Y = synth.config_states(cfg, n, seed_offset=1000)
     blob = synth.to_bytes(model)
     g = pj.Model(blob)
-    autotune.autotune(g, blob, use_cache=False)
+    if shape:
+        g.set_launch(shape[0], shape[1], 1)
+    else:
+        autotune.autotune(g, blob, use_cache=False)
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
     J = torch.empty((n, model.n_species + 1, model.n_species + 1), dtype=torch.float64, device="cuda")
     for _ in range(warmup + 1):
@@ -498,7 +643,8 @@ def main():
     ap.add_argument("--headline-only", action="store_true", help="skip the other model sizes")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, metavar="CFG:N", help="one small profiling case (for ncu)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
+    ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS]", help="one small profiling case (for ncu)")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile, args.warmup)

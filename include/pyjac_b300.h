@@ -138,6 +138,48 @@ PJ_API int pj_get_launch(const pj_mech *m, int which, pj_launch *cfg);
 /* Shared memory (bytes) one CTA of the given shape needs for this model, or PJ_EINVAL. */
 PJ_API int pj_launch_smem_bytes(const pj_mech *m, int which, const pj_launch *cfg, size_t *bytes);
 
+/*
+ * Batched form: one persistent launch over several (model, state batch) items of uneven size.
+ * Each item names a loaded model, its n states (device T, P, Y) and its outputs; the plan splits
+ * every item into tiles of consecutive states, and the CTAs of one kernel take tiles from a shared
+ * counter, evaluating each with its model's warps-per-state setting (pj_set_launch). Results are
+ * those of pj_eval_jacobian / pj_eval_dydt on the same states (same arithmetic, same order).
+ *
+ * which: 0 = Jacobian (jac required, dydt optional), 1 = source terms (dydt required).
+ * shape (may be NULL): threads_per_cta (multiple of 32, <= 512; default 512), ctas_per_sm (default
+ * 1) and tile_states (states per tile; 0 = four times the states a CTA evaluates concurrently).
+ * pj_batch_create checks every item like the plain entry points (PJ_EINVAL / PJ_EUNSUPPORTED),
+ * copies the item table and tiles to device memory it owns, and keeps the pointers: the buffers
+ * must stay valid while the plan is used. pj_batch_run resets the plan's tile counter and launches
+ * on the stream, asynchronously; it allocates nothing and does not synchronise, so a run can be
+ * captured into a CUDA graph and replayed. Runs of one plan must not overlap on the GPU (they share
+ * the counter). pj_batch_free releases the plan (no run may be in flight).
+ */
+typedef struct pj_batch pj_batch;
+
+typedef struct {
+    const pj_mech *mech;
+    int64_t n;
+    const double *T, *P, *Y;
+    int64_t ldy;
+    double *jac;
+    int64_t ldj;
+    double *dydt;
+    int64_t ldd;
+} pj_batch_item;
+
+typedef struct {
+    int threads_per_cta;
+    int ctas_per_sm;
+    int tile_states;
+} pj_batch_shape;
+
+PJ_API int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj_batch_shape *shape,
+                           pj_batch **out);
+PJ_API int pj_batch_run(pj_batch *b, void *stream);
+PJ_API int pj_batch_info(const pj_batch *b, int *n_tiles, size_t *smem_bytes, int *threads_per_cta);
+PJ_API void pj_batch_free(pj_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ import os
 import threading
 from typing import Optional, Tuple
 
-__all__ = ["Model", "LibraryError", "library", "load_library", "PJ_STATUS", "LIB_PATH"]
+__all__ = ["Model", "BatchPlan", "LibraryError", "library", "load_library", "PJ_STATUS", "LIB_PATH"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpyjacb300.so")
@@ -37,6 +37,16 @@ class LibraryError(RuntimeError):
 
 class pj_launch(ctypes.Structure):
     _fields_ = [("warps_per_state", ctypes.c_int), ("states_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+class pj_batch_item(ctypes.Structure):
+    _fields_ = [("mech", ctypes.c_void_p), ("n", ctypes.c_int64), ("T", ctypes.c_void_p), ("P", ctypes.c_void_p),
+                ("Y", ctypes.c_void_p), ("ldy", ctypes.c_int64), ("jac", ctypes.c_void_p), ("ldj", ctypes.c_int64),
+                ("dydt", ctypes.c_void_p), ("ldd", ctypes.c_int64)]
+
+
+class pj_batch_shape(ctypes.Structure):
+    _fields_ = [("threads_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("tile_states", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -67,6 +77,11 @@ def load_library(path: str = LIB_PATH):
             "pj_set_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
             "pj_get_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
             "pj_launch_smem_bytes": ([vp, i32, ctypes.POINTER(pj_launch), ctypes.POINTER(sz)], i32),
+            "pj_batch_create": ([ctypes.POINTER(pj_batch_item), i32, i32, ctypes.POINTER(pj_batch_shape),
+                                 ctypes.POINTER(vp)], i32),
+            "pj_batch_run": ([vp, vp], i32),
+            "pj_batch_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(sz), ctypes.POINTER(i32)], i32),
+            "pj_batch_free": ([vp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -237,3 +252,68 @@ def _host_stride0(a):
     if isinstance(a, torch.Tensor):
         return a.stride(0)
     return a.strides[0] // 8
+
+
+class BatchPlan:
+    """One persistent launch over several (model, states, outputs) items (the batched form).
+
+    items: sequence of (Model, T, P, Y, out[, dydt_out]) with CUDA float64 tensors; for
+    which="jacobian" out is (n, N+1, N+1) (dydt_out optional), for which="dydt" out is (n, N+1).
+    The plan keeps pointers to these tensors: refill them in place and call run() again, or
+    capture run() into a CUDA graph with capture() and replay it."""
+
+    def __init__(self, items, which: str = "jacobian", threads_per_cta: int = 0, ctas_per_sm: int = 0,
+                 tile_states: int = 0):
+        self.which = 0 if which == "jacobian" else 1
+        self._keep = []
+        arr = (pj_batch_item * len(items))()
+        for x, item in enumerate(items):
+            model, T, P, Y, out = item[:5]
+            f = item[5] if len(item) > 5 else None
+            T, P, Y, n = model._inputs(T, P, Y)
+            self._keep += [model, T, P, Y, out, f]
+            a = arr[x]
+            a.mech = model.handle
+            a.n = n
+            a.T, a.P, a.Y, a.ldy = T.data_ptr(), P.data_ptr(), Y.data_ptr(), Y.stride(0)
+            if self.which == 0:
+                a.jac, a.ldj = out.data_ptr(), out.stride(0)
+                a.dydt, a.ldd = (f.data_ptr(), f.stride(0)) if f is not None else (None, 0)
+            else:
+                a.jac, a.ldj = None, 0
+                a.dydt, a.ldd = out.data_ptr(), out.stride(0)
+        shape = pj_batch_shape(threads_per_cta, ctas_per_sm, tile_states)
+        h = ctypes.c_void_p()
+        _check(library().pj_batch_create(arr, len(items), self.which, ctypes.byref(shape), ctypes.byref(h)))
+        self._h = h
+        nt, sm, th = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int()
+        _check(library().pj_batch_info(h, ctypes.byref(nt), ctypes.byref(sm), ctypes.byref(th)))
+        self.n_tiles, self.smem_bytes, self.threads_per_cta = nt.value, sm.value, th.value
+
+    def run(self, stream=None) -> None:
+        _check(library().pj_batch_run(self._h, _stream_handle(stream)))
+
+    def capture(self):
+        """CUDA graph of one run (counter reset + persistent launch); replay() re-evaluates."""
+        torch = _torch()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run()
+        return graph
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            library().pj_batch_free(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -192,6 +192,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     pj::build_math_tables(tables);
     std::vector<pj::MathTables> tvec(1, tables);
     size_t o_mt = push(blob, tvec);
+    std::vector<pj::DevModel> dm_placeholder(1);
+    size_t o_dm = push(blob, dm_placeholder);
     pj_mech *m = new (std::nothrow) pj_mech();
     if (!m) return fail(PJ_ENOMEM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&m->device);
@@ -266,6 +268,13 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.s_scale = reinterpret_cast<const double *>(b + o_ss);
     d.c_scale = reinterpret_cast<const double *>(b + o_cs2);
     d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
+    m->dev_model = reinterpret_cast<const pj::DevModel *>(b + o_dm);
+    e = cudaMemcpy(b + o_dm, &d, sizeof(d), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->dev_blob);
+        delete m;
+        return cuda_fail(e, "cudaMemcpy of the model descriptor");
+    }
     m->N = im.N;
     m->R = im.R;
     m->NE = im.NE;

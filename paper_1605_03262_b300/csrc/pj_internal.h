@@ -106,6 +106,35 @@ struct KParams {
     int shared_const;         // doubles of per-CTA constants at the start of shared memory
 };
 
+// Batched form: one entry per (model, state batch) of a plan, and tiles of consecutive states.
+struct BatchIO {
+    const double *T, *P, *Y;
+    long long ldy;
+    double *jac;
+    long long ldj;
+    double *dydt;
+    long long ldd;
+};
+
+struct BatchItem {
+    const DevModel *m;        // device copy of the model's DevModel
+    Scratch sc;
+    BatchIO io;
+    int wps, groups, shared_const, pad;
+};
+
+struct BatchTile {
+    int item, pad;
+    long long begin, count;
+};
+
+struct BatchParams {
+    const BatchItem *items;
+    const BatchTile *tiles;
+    int ntiles;
+    int *counter;             // tile counter, zeroed before every launch
+};
+
 struct LaunchCfg {
     int wps = 1;              // warps per state
     int groups = 4;           // states per CTA
@@ -140,6 +169,8 @@ HostImage build_image(const void *buf, size_t len);                 // throws Fo
 Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_chunk);
 int shared_const_doubles(int N);
 cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream);
+cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem);
+cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads, size_t smem, cudaStream_t stream);
 int set_error(int code, const std::string &msg);   // records the calling thread's last error, returns code
 
 }  // namespace pj
@@ -156,6 +187,7 @@ struct pj_mech {
     int jac_cfg_set = 0, dydt_cfg_set = 0;
     int device = 0;
     pj_host_staging *staging = nullptr;   // device buffers of pj_eval_jacobian_host (lazy)
+    const pj::DevModel *dev_model = nullptr;   // device copy of dev (for batched plans)
 };
 
 void pj_host_staging_release(pj_mech *m);

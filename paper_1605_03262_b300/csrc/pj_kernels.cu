@@ -44,12 +44,21 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// The threads that evaluate one state: group index in the CTA, thread index in the group, lane,
+// warp in the group, warps per group (WPS template argument, or runtime when it is 0).
+struct Grp {
+    int grp, t, lane, wg, wps, G;
+};
+
 template <int WPS>
-__device__ __forceinline__ void group_sync(int grp) {
+__device__ __forceinline__ void group_sync(const Grp &g) {
     if constexpr (WPS == 1) {
         __syncwarp();
+    } else if constexpr (WPS > 1) {
+        asm volatile("bar.sync %0, %1;" ::"r"(g.grp + 1), "r"(WPS * 32) : "memory");
     } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(WPS * 32) : "memory");
+        if (g.wps == 1) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(g.grp + 1), "r"(g.G) : "memory");
     }
 }
 
@@ -413,227 +422,292 @@ __device__ __forceinline__ void store_segment(double *g, const double *sbuf, int
     if (rem > 0 && (rem & 1) && lane == 0) __stcs(g + len - 1, sbuf[len - 1]);
 }
 
-template <bool JAC, int WPS>
-__global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__ KParams p) {
-    extern __shared__ __align__(16) double smem[];
-    const DevModel &m = p.m;
-    const int N = m.N, R = m.R;
-    constexpr int G = WPS * 32;
-    const int grp = threadIdx.x / G, t = threadIdx.x - grp * G, lane = threadIdx.x & 31, wg = t >> 5;
+using StateIO = BatchIO;
 
-    // per-CTA constants: Delta_j, 1/W_j and the stoichiometric-coefficient table nu = code - kNuBias
-    double *sNu = smem, *sDelta = smem + 128, *sInvW = smem + 128 + N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+// Per-CTA constants of a model: Delta_j, 1/W_j and the coefficient table nu = code - kNuBias.
+__device__ __forceinline__ void load_model_consts(const DevModel &m, double *smem) {
+    double *sNu = smem, *sDelta = smem + 128, *sInvW = smem + 128 + m.N;
+    for (int k = threadIdx.x; k < m.N; k += blockDim.x) {
         sDelta[k] = __ldg(m.Delta + k);
         sInvW[k] = __ldg(m.invW + k);
     }
     for (int c = threadIdx.x; c < 128; c += blockDim.x) sNu[c] = double(c - kNuBias);
+}
 
-    const Scratch &sc = p.sc;
-    double *S = smem + p.shared_const + size_t(grp) * sc.total;
+// Neutral elements read by padded schedule items; written once, never overwritten by a state.
+template <bool JAC>
+__device__ __forceinline__ void init_neutral(const DevModel &m, const Scratch &sc, double *S, int t) {
+    if (t == 0) {
+        S[sc.q + m.R] = 0.0;
+        if (JAC) {
+            S[sc.th + m.R] = 0.0;
+            S[sc.a + m.R] = 0.0;
+            S[sc.dH + m.R] = 0.0;
+            S[sc.b + m.nslot] = 0.0;
+        }
+    }
+}
+
+// One state, evaluated by one group: state prep, thermodynamics, reaction stage, gathers and rows.
+template <bool JAC, int WPS>
+__device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
+                                           const StateIO &io, long long st, const Grp &g) {
+    const int N = m.N, R = m.R;
+    const int G = WPS ? WPS * 32 : g.G, NW = WPS ? WPS : g.wps;
+    const int t = g.t, lane = g.lane, wg = g.wg;
+    const double *sNu = smem_const, *sDelta = smem_const + 128, *sInvW = smem_const + 128 + N;
     double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
     double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
     double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
-    if (t == 0) {   // neutral elements read by padded schedule items; never overwritten
-        sq[R] = 0.0;
-        if (JAC) {
-            sth[R] = 0.0;
-            sa[R] = 0.0;
-            sdH[R] = 0.0;
-            sb[m.nslot] = 0.0;
+    (void)sHS;
+    // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
+    StateScalars s;
+    s.T = __ldg(io.T + st);
+    s.P = __ldg(io.P + st);
+    s.invT = 1.0 / s.T;
+    s.lnT = fast_log(s.T, m.tables);
+    const double *Ys = io.Y + st * io.ldy;
+    double *sY = sf;   // Y parks in the f array until the concentrations exist
+    for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
+    for (int k = t; k < N; k += G) {
+        const Thermo th = species_thermo<JAC>(m, k, s.T, s.invT, s.lnT);
+        scp[k] = kR * sInvW[k] * th.cpR;
+        sH[k] = kR * th.HR;
+        sB[k] = th.B;
+        if constexpr (JAC) {
+            sdB[k] = th.dB;
+            sJk0[k] = kR * sInvW[k] * th.dcpR;   // dcp_k/dT parks in the J_k0 array
         }
     }
-    __syncthreads();
+    group_sync<WPS>(g);
+    double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        const double y = sY[k];
+        r1 = fma(y, sInvW[k], r1);
+        r2 = fma(y, scp[k], r2);
+        if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
+    }
+    const double sYW = warp_sum(r1), cp = warp_sum(r2);
+    const double dcpdT = JAC ? warp_sum(r3) : 0.0;
+    s.W = 1.0 / sYW;
+    s.Ctot = s.P / (kR * s.T);
+    s.rho = s.Ctot * s.W;
+    s.lnP = fast_log(s.P, m.tables);
+    for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
+    group_sync<WPS>(g);
 
-    for (long long st = (long long)blockIdx.x * p.groups + grp; st < p.n; st += (long long)gridDim.x * p.groups) {
-        // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
-        StateScalars s;
-        s.T = __ldg(p.T + st);
-        s.P = __ldg(p.P + st);
-        s.invT = 1.0 / s.T;
-        s.lnT = fast_log(s.T, m.tables);
-        const double *Ys = p.Y + st * p.ldy;
-        double *sY = sf;   // Y parks in the f array until the concentrations exist
-        for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
-        for (int k = t; k < N; k += G) {
-            const Thermo th = species_thermo<JAC>(m, k, s.T, s.invT, s.lnT);
-            scp[k] = kR * sInvW[k] * th.cpR;
-            sH[k] = kR * th.HR;
-            sB[k] = th.B;
-            if constexpr (JAC) {
-                sdB[k] = th.dB;
-                sJk0[k] = kR * sInvW[k] * th.dcpR;   // dcp_k/dT parks in the J_k0 array
+    // ---- reaction stage ----
+    for (int i = t; i < R; i += G) reaction<JAC>(m, i, s, sC, sB, sdB, sH, sNu, sq, sth, sa, sdH, sb);
+    group_sync<WPS>(g);
+
+    const double invrho = 1.0 / s.rho;
+    if constexpr (!JAC) {
+        for (int c = wg; c < m.ng; c += NW) {       // omega_k through the species-gather schedule
+            const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
+            const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
+            const unsigned *it = m.g_items + ioff + lane;
+            double w = 0.0;
+            for (int x = 0; x < len; ++x) {
+                const unsigned v = __ldg(it + 32 * x);
+                w = fma(sNu[(v >> 24) & 127], sq[v & 0xffffff], w);
+                if (v >> 31) {
+                    const int k = __ldg(dst);
+                    dst += 32;
+                    sf[k] = __ldg(m.W + k) * invrho * w;
+                    w = 0.0;
+                }
             }
         }
-        group_sync<WPS>(grp);
-        double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        group_sync<WPS>(g);
+        double hf = 0.0;
+        for (int k = lane; k < N; k += 32) hf = fma(sH[k] * sInvW[k], sf[k], hf);
+        hf = warp_sum(hf);
+        double *out = io.dydt + st * io.ldd;
+        const double invcp = 1.0 / cp;
+        for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -hf * invcp : sf[k - 1];
+        group_sync<WPS>(g);
+        return;
+    } else {
+        // ---- gather stage: lane-balanced schedules (each sum is one lane's, in list order) ----
+        for (int c = wg; c < m.ng; c += NW) {       // omega_k, J_k0, A_k
+            const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
+            const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
+            const unsigned *it = m.g_items + ioff + lane;
+            double wq = 0.0, wt = 0.0, wa = 0.0;
+            for (int x = 0; x < len; ++x) {
+                const unsigned v = __ldg(it + 32 * x);
+                const int i = v & 0xffffff;
+                const double nu = sNu[(v >> 24) & 127];
+                wq = fma(nu, sq[i], wq);
+                wt = fma(nu, sth[i], wt);
+                wa = fma(nu, sa[i], wa);
+                if (v >> 31) {
+                    const int k = __ldg(dst);
+                    dst += 32;
+                    const double pre = __ldg(m.W + k) * invrho;
+                    sf[k] = pre * wq;
+                    sJk0[k] = pre * wt;
+                    sA[k] = pre * fma(s.W, wq, wa);
+                    wq = wt = wa = 0.0;
+                }
+            }
+        }
+        for (int c = wg; c < m.nh; c += NW) {       // HS_j = (1/W_j) sum_i dH_i b'_ij
+            const int ioff = __ldg(m.h_chunk + 3 * c), len = __ldg(m.h_chunk + 3 * c + 1);
+            const int *dst = m.h_dst + __ldg(m.h_chunk + 3 * c + 2) + lane;
+            const unsigned *it = m.h_items + ioff + lane;
+            const int *ax = m.h_aux + ioff + lane;
+            double acc = 0.0;
+            for (int x = 0; x < len; ++x) {
+                const unsigned v = __ldg(it + 32 * x);
+                acc = fma(sdH[__ldg(ax + 32 * x)], sb[v & 0xffffff], acc);
+                if (v >> 31) {
+                    const int j = __ldg(dst);
+                    dst += 32;
+                    sHS[j] = acc * sInvW[j];
+                    acc = 0.0;
+                }
+            }
+        }
+        for (int c = wg; c < m.ncc; c += NW) {      // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
+            const int ioff = __ldg(m.c_chunk + 3 * c), len = __ldg(m.c_chunk + 3 * c + 1);
+            const int eoff = __ldg(m.c_chunk + 3 * c + 2) + lane;
+            const int *dst = m.c_dst + eoff;
+            const double *scl = m.c_scale + eoff;
+            const unsigned *it = m.c_items + ioff + lane;
+            double acc = 0.0;
+            for (int x = 0; x < len; ++x) {
+                const unsigned v = __ldg(it + 32 * x);
+                acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
+                if (v >> 31) {
+                    sCk[__ldg(dst)] = -__ldg(scl) * acc;
+                    dst += 32;
+                    scl += 32;
+                    acc = 0.0;
+                }
+            }
+        }
+        group_sync<WPS>(g);
+        double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
         for (int k = lane; k < N; k += 32) {
-            const double y = sY[k];
-            r1 = fma(y, sInvW[k], r1);
-            r2 = fma(y, scp[k], r2);
-            if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
+            const double hk = sH[k] * sInvW[k];
+            x1 = fma(hk, sA[k], x1);
+            x2 = fma(hk, sf[k], x2);
+            x3 = fma(hk, sJk0[k], x3);
+            x4 = fma(scp[k], sf[k], x4);
         }
-        const double sYW = warp_sum(r1), cp = warp_sum(r2);
-        const double dcpdT = JAC ? warp_sum(r3) : 0.0;
-        s.W = 1.0 / sYW;
-        s.Ctot = s.P / (kR * s.T);
-        s.rho = s.Ctot * s.W;
-        s.lnP = fast_log(s.P, m.tables);
-        for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
-        group_sync<WPS>(grp);
+        const double HA = warp_sum(x1), Hf = warp_sum(x2), HJ0 = warp_sum(x3), CF = warp_sum(x4);
+        const double invcp = 1.0 / cp;
+        const double J00 = -invcp * (fma(-dcpdT * invcp, Hf, CF) + HJ0);
+        const double HSN = sHS[N - 1], cpN = scp[N - 1];
+        const double e0 = Hf * invcp * invcp;
 
-        // ---- reaction stage ----
-        for (int i = t; i < R; i += G) reaction<JAC>(m, i, s, sC, sB, sdB, sH, sNu, sq, sth, sa, sdH, sb);
-        group_sync<WPS>(grp);
-
-        const double invrho = 1.0 / s.rho;
-        if constexpr (!JAC) {
-            for (int c = wg; c < m.ng; c += WPS) {       // omega_k through the species-gather schedule
-                const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
-                const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-                const unsigned *it = m.g_items + ioff + lane;
-                double w = 0.0;
-                for (int x = 0; x < len; ++x) {
-                    const unsigned v = __ldg(it + 32 * x);
-                    w = fma(sNu[(v >> 24) & 127], sq[v & 0xffffff], w);
-                    if (v >> 31) {
-                        const int k = __ldg(dst);
-                        dst += 32;
-                        sf[k] = __ldg(m.W + k) * invrho * w;
-                        w = 0.0;
-                    }
-                }
+        // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
+        //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
+        const int ld = N + 1, RPC = m.rpc;
+        double *stage = S + sc.rows + wg * RPC * ld;
+        double *Jout = io.jac + st * io.ldj;
+        for (int c = wg; c < m.n_row_chunks; c += NW) {
+            const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+            for (int x = lane; x < nel; x += 32) {
+                const int rr = x / ld, j = x - rr * ld, r = r0 + rr;
+                double v;
+                if (j == 0) v = (r == 0) ? J00 : sJk0[r - 1];
+                else if (j == N) v = 0.0;
+                else if (r == 0) v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
+                else v = fma(sA[r - 1], sDelta[j - 1], sCk[r - 1]);
+                stage[x] = v;
             }
-            group_sync<WPS>(grp);
-            double hf = 0.0;
-            for (int k = lane; k < N; k += 32) hf = fma(sH[k] * sInvW[k], sf[k], hf);
-            hf = warp_sum(hf);
-            double *out = p.dydt + st * p.ldd;
-            const double invcp = 1.0 / cp;
-            for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -hf * invcp : sf[k - 1];
-            group_sync<WPS>(grp);
-            continue;
-        } else {
-            // ---- gather stage: lane-balanced schedules (each sum is one lane's, in list order) ----
-            for (int c = wg; c < m.ng; c += WPS) {       // omega_k, J_k0, A_k
-                const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
-                const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-                const unsigned *it = m.g_items + ioff + lane;
-                double wq = 0.0, wt = 0.0, wa = 0.0;
-                for (int x = 0; x < len; ++x) {
-                    const unsigned v = __ldg(it + 32 * x);
-                    const int i = v & 0xffffff;
-                    const double nu = sNu[(v >> 24) & 127];
-                    wq = fma(nu, sq[i], wq);
-                    wt = fma(nu, sth[i], wt);
-                    wa = fma(nu, sa[i], wa);
-                    if (v >> 31) {
-                        const int k = __ldg(dst);
-                        dst += 32;
-                        const double pre = __ldg(m.W + k) * invrho;
-                        sf[k] = pre * wq;
-                        sJk0[k] = pre * wt;
-                        sA[k] = pre * fma(s.W, wq, wa);
-                        wq = wt = wa = 0.0;
-                    }
-                }
-            }
-            for (int c = wg; c < m.nh; c += WPS) {       // HS_j = (1/W_j) sum_i dH_i b'_ij
-                const int ioff = __ldg(m.h_chunk + 3 * c), len = __ldg(m.h_chunk + 3 * c + 1);
-                const int *dst = m.h_dst + __ldg(m.h_chunk + 3 * c + 2) + lane;
-                const unsigned *it = m.h_items + ioff + lane;
-                const int *ax = m.h_aux + ioff + lane;
-                double acc = 0.0;
-                for (int x = 0; x < len; ++x) {
-                    const unsigned v = __ldg(it + 32 * x);
-                    acc = fma(sdH[__ldg(ax + 32 * x)], sb[v & 0xffffff], acc);
-                    if (v >> 31) {
-                        const int j = __ldg(dst);
-                        dst += 32;
-                        sHS[j] = acc * sInvW[j];
-                        acc = 0.0;
-                    }
-                }
-            }
-            for (int c = wg; c < m.ncc; c += WPS) {      // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
-                const int ioff = __ldg(m.c_chunk + 3 * c), len = __ldg(m.c_chunk + 3 * c + 1);
-                const int eoff = __ldg(m.c_chunk + 3 * c + 2) + lane;
-                const int *dst = m.c_dst + eoff;
-                const double *scl = m.c_scale + eoff;
-                const unsigned *it = m.c_items + ioff + lane;
+            __syncwarp();
+            {
+                const int ioff = __ldg(m.s_chunk + 3 * c), len = __ldg(m.s_chunk + 3 * c + 1);
+                const int eoff = __ldg(m.s_chunk + 3 * c + 2) + lane;
+                const int *dst = m.s_dst + eoff;
+                const double *scl = m.s_scale + eoff;
+                const unsigned *it = m.s_items + ioff + lane;
                 double acc = 0.0;
                 for (int x = 0; x < len; ++x) {
                     const unsigned v = __ldg(it + 32 * x);
                     acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
                     if (v >> 31) {
-                        sCk[__ldg(dst)] = -__ldg(scl) * acc;
+                        const int d = __ldg(dst);
+                        stage[d] = fma(__ldg(scl), acc, stage[d]);
                         dst += 32;
                         scl += 32;
                         acc = 0.0;
                     }
                 }
             }
-            group_sync<WPS>(grp);
-            double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
-            for (int k = lane; k < N; k += 32) {
-                const double hk = sH[k] * sInvW[k];
-                x1 = fma(hk, sA[k], x1);
-                x2 = fma(hk, sf[k], x2);
-                x3 = fma(hk, sJk0[k], x3);
-                x4 = fma(scp[k], sf[k], x4);
-            }
-            const double HA = warp_sum(x1), Hf = warp_sum(x2), HJ0 = warp_sum(x3), CF = warp_sum(x4);
-            const double invcp = 1.0 / cp;
-            const double J00 = -invcp * (fma(-dcpdT * invcp, Hf, CF) + HJ0);
-            const double HSN = sHS[N - 1], cpN = scp[N - 1];
-            const double e0 = Hf * invcp * invcp;
-
-            // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
-            //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
-            const int ld = N + 1, RPC = m.rpc;
-            double *stage = S + sc.rows + wg * RPC * ld;
-            double *Jout = p.jac + st * p.ldj;
-            for (int c = wg; c < m.n_row_chunks; c += WPS) {
-                const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
-                for (int x = lane; x < nel; x += 32) {
-                    const int rr = x / ld, j = x - rr * ld, r = r0 + rr;
-                    double v;
-                    if (j == 0) v = (r == 0) ? J00 : sJk0[r - 1];
-                    else if (j == N) v = 0.0;
-                    else if (r == 0) v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
-                    else v = fma(sA[r - 1], sDelta[j - 1], sCk[r - 1]);
-                    stage[x] = v;
-                }
-                __syncwarp();
-                {
-                    const int ioff = __ldg(m.s_chunk + 3 * c), len = __ldg(m.s_chunk + 3 * c + 1);
-                    const int eoff = __ldg(m.s_chunk + 3 * c + 2) + lane;
-                    const int *dst = m.s_dst + eoff;
-                    const double *scl = m.s_scale + eoff;
-                    const unsigned *it = m.s_items + ioff + lane;
-                    double acc = 0.0;
-                    for (int x = 0; x < len; ++x) {
-                        const unsigned v = __ldg(it + 32 * x);
-                        acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
-                        if (v >> 31) {
-                            const int d = __ldg(dst);
-                            stage[d] = fma(__ldg(scl), acc, stage[d]);
-                            dst += 32;
-                            scl += 32;
-                            acc = 0.0;
-                        }
-                    }
-                }
-                __syncwarp();
-                store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
-                __syncwarp();
-            }
-            if (p.dydt) {
-                double *out = p.dydt + st * p.ldd;
-                for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -Hf * invcp : sf[k - 1];
-            }
-            group_sync<WPS>(grp);
+            __syncwarp();
+            store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
+            __syncwarp();
         }
+        if (io.dydt) {
+            double *out = io.dydt + st * io.ldd;
+            for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -Hf * invcp : sf[k - 1];
+        }
+        group_sync<WPS>(g);
+    }
+}
+
+template <bool JAC, int WPS>
+__global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__ KParams p) {
+    extern __shared__ __align__(16) double smem[];
+    const DevModel &m = p.m;
+    Grp g;
+    g.wps = WPS;
+    g.G = WPS * 32;
+    g.grp = threadIdx.x / g.G;
+    g.t = threadIdx.x - g.grp * g.G;
+    g.lane = threadIdx.x & 31;
+    g.wg = g.t >> 5;
+    load_model_consts(m, smem);
+    double *S = smem + p.shared_const + size_t(g.grp) * p.sc.total;
+    init_neutral<JAC>(m, p.sc, S, g.t);
+    __syncthreads();
+    const StateIO io{p.T, p.P, p.Y, p.ldy, p.jac, p.ldj, p.dydt, p.ldd};
+    for (long long st = (long long)blockIdx.x * p.groups + g.grp; st < p.n; st += (long long)gridDim.x * p.groups)
+        eval_state<JAC, WPS>(m, p.sc, S, smem, io, st, g);
+}
+
+// Persistent kernel over tiles of states from several models (the batched form): each CTA takes
+// the next tile from an atomic counter, loads the tile's model constants when the model changes,
+// and its groups evaluate the tile's states with the model's group width.
+template <bool JAC>
+__global__ void __launch_bounds__(512, 1) pj_batch_kernel(const __grid_constant__ BatchParams p) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ DevModel s_m;
+    __shared__ int s_tile;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= p.ntiles) break;
+        const BatchTile tl = p.tiles[tile];
+        const BatchItem &it = p.items[tl.item];
+        Grp g;
+        g.wps = it.wps;
+        g.G = it.wps * 32;
+        g.grp = threadIdx.x / g.G;
+        g.t = threadIdx.x - g.grp * g.G;
+        g.lane = threadIdx.x & 31;
+        g.wg = g.t >> 5;
+        double *S = smem + it.shared_const + size_t(g.grp) * it.sc.total;
+        if (tl.item != cur) {
+            const int *src = reinterpret_cast<const int *>(it.m);
+            int *dst = reinterpret_cast<int *>(&s_m);
+            for (int w = threadIdx.x; w < int(sizeof(DevModel) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            load_model_consts(s_m, smem);
+            if (g.grp < it.groups) init_neutral<JAC>(s_m, it.sc, S, g.t);
+            cur = tl.item;
+            __syncthreads();
+        }
+        if (g.grp < it.groups)
+            for (long long st = tl.begin + g.grp; st < tl.begin + tl.count; st += it.groups)
+                eval_state<JAC, 0>(s_m, it.sc, S, smem, it.io, st, g);
+        __syncthreads();
     }
 }
 
@@ -701,6 +775,22 @@ static cudaError_t launch_t(const KParams &p, int wps, int blocks, size_t smem, 
 
 cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream) {
     return jac ? launch_t<true>(p, wps, blocks, smem, stream) : launch_t<false>(p, wps, blocks, smem, stream);
+}
+
+cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem) {
+    cudaFuncAttributes a{};
+    cudaError_t e = jac ? cudaFuncGetAttributes(&a, pj_batch_kernel<true>) : cudaFuncGetAttributes(&a, pj_batch_kernel<false>);
+    if (e != cudaSuccess) return e;
+    if (static_smem) *static_smem = a.sharedSizeBytes;
+    if (dyn_smem == 0) return cudaSuccess;
+    return jac ? cudaFuncSetAttribute(pj_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn_smem))
+               : cudaFuncSetAttribute(pj_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn_smem));
+}
+
+cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads, size_t smem, cudaStream_t stream) {
+    if (jac) pj_batch_kernel<true><<<blocks, threads, smem, stream>>>(p);
+    else pj_batch_kernel<false><<<blocks, threads, smem, stream>>>(p);
+    return cudaGetLastError();
 }
 
 }  // namespace pj

@@ -1,0 +1,241 @@
+"""Serving form: a continuous-batching loop for Jacobian requests over several resident models.
+
+Requests (model name, T, P, Y) arrive at any time through :meth:`Server.submit`, which returns a
+future. A scheduler thread runs iterations continuously:
+
+* retire: iterations whose completion event has fired hand their results to the futures and
+  give back their device memory and stream;
+* admit: queued requests are taken in arrival order; requests of the same model that are queued
+  together are merged into one launch (up to ``max_batch_states`` states). An iteration is admitted
+  only while an in-flight slot is free and the device memory it holds (inputs, Jacobians, dydt)
+  fits the HBM budget next to the iterations already in flight; otherwise it waits in the queue
+  (no out-of-memory, no rejection). Iterations run on a pool of streams, so requests admitted
+  while others are on the GPU overlap with them.
+
+Model images stay resident for the server's lifetime. Each request's latency is measured from
+:meth:`submit` to the completion event of its iteration (results in device memory), and, with
+``host_results=True``, to the end of the copy to host memory. The evaluation itself is the
+library's Jacobian kernel, so a request's result is the same (bitwise) alone and in the mix.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures
+import threading
+import time
+from typing import Dict, List, Optional
+
+import numpy as np
+
+__all__ = ["Server", "Request"]
+
+
+class Request:
+    __slots__ = ("rid", "name", "T", "P", "Y", "n", "t_submit", "t_done", "future", "dydt")
+
+    def __init__(self, rid, name, T, P, Y, dydt):
+        self.rid, self.name, self.T, self.P, self.Y = rid, name, T, P, Y
+        self.n = int(Y.shape[0])
+        self.t_submit = time.perf_counter()
+        self.t_done = None
+        self.future: concurrent.futures.Future = concurrent.futures.Future()
+        self.dydt = dydt
+
+
+class _Iteration:
+    __slots__ = ("reqs", "model", "stream", "event", "bytes", "J", "F", "offsets", "host")
+
+    def __init__(self):
+        self.reqs, self.offsets, self.host = [], [], None
+
+
+class Server:
+    """Continuous-batching Jacobian server on the current CUDA device.
+
+    models: name -> paper_1605_03262_b300.Model (already loaded; their launch shapes are used).
+    hbm_budget: bytes of device memory in-flight iterations may hold (default: half of the free
+    memory at start). max_inflight: concurrent iterations (and streams). max_batch_states: states
+    merged into one launch. host_results: copy results to host memory (numpy) before completing."""
+
+    def __init__(self, models: Dict[str, object], hbm_budget: Optional[int] = None, max_inflight: int = 6,
+                 max_batch_states: int = 65536, host_results: bool = False):
+        import torch
+        self.torch = torch
+        self.models = dict(models)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        free, _ = torch.cuda.mem_get_info(self.device)
+        self.hbm_budget = int(hbm_budget) if hbm_budget is not None else int(free // 2)
+        self.max_inflight = int(max_inflight)
+        self.max_batch_states = int(max_batch_states)
+        self.host_results = bool(host_results)
+        self._queue: collections.deque = collections.deque()
+        self._inflight: List[_Iteration] = []
+        self._streams = [torch.cuda.Stream(device=self.device) for _ in range(self.max_inflight)]
+        self._free_streams = list(self._streams)
+        self._held = 0
+        self._cv = threading.Condition()
+        self._stop = False
+        self._thread: Optional[threading.Thread] = None
+        self._next_id = 0
+        self.stats = {"iterations": 0, "requests": 0, "states": 0, "max_inflight_seen": 0, "waits_for_memory": 0,
+                      "merged_requests": 0}
+
+    # -- client side ---------------------------------------------------------------------------
+    def submit(self, name: str, T, P, Y, dydt: bool = False) -> concurrent.futures.Future:
+        """Queue one request (host or device float64 arrays). The future's result is the Jacobian
+        (n, N+1, N+1) as a CUDA tensor (or numpy array with host_results), or (J, dydt)."""
+        if name not in self.models:
+            raise KeyError("unknown model %r" % name)
+        need = self._bytes(self.models[name], int(Y.shape[0]))
+        if need > self.hbm_budget:
+            raise ValueError("request needs %d bytes of device memory, above the server's budget %d"
+                             % (need, self.hbm_budget))
+        with self._cv:
+            req = Request(self._next_id, name, T, P, Y, dydt)
+            req.future.request = req          # lets clients read the request's timings
+            self._next_id += 1
+            self._queue.append(req)
+            self._cv.notify()
+        return req.future
+
+    def start(self) -> "Server":
+        if self._thread is None:
+            self._stop = False
+            self._thread = threading.Thread(target=self._loop, name="pyjac-b300-server", daemon=True)
+            self._thread.start()
+        return self
+
+    def stop(self, drain: bool = True) -> None:
+        if self._thread is None:
+            return
+        with self._cv:
+            self._stop = True
+            self._drain = drain
+            self._cv.notify()
+        self._thread.join()
+        self._thread = None
+
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *exc):
+        self.stop()
+
+    # -- scheduler -----------------------------------------------------------------------------
+    @staticmethod
+    def _bytes(model, n: int) -> int:
+        N = model.n_species
+        return 8 * n * ((N + 1) ** 2 + 2 * (N + 1) + 2)
+
+    def _loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        self._drain = True
+        while True:
+            progressed = self._retire()
+            with self._cv:
+                if self._stop and (not self._drain or (not self._queue and not self._inflight)):
+                    break
+            progressed |= self._admit()
+            if not progressed:
+                with self._cv:
+                    if not self._queue or len(self._inflight) >= self.max_inflight:
+                        self._cv.wait(timeout=0.0002 if self._inflight else 0.05)
+        # fail whatever is left (stop without drain)
+        with self._cv:
+            while self._queue:
+                self._queue.popleft().future.set_exception(RuntimeError("server stopped"))
+
+    def _retire(self) -> bool:
+        done = [it for it in self._inflight if it.event.query()]
+        for it in done:
+            self._inflight.remove(it)
+            t = time.perf_counter()
+            for r, (a, b) in zip(it.reqs, it.offsets):
+                r.t_done = t
+                if self.host_results:
+                    J = it.host[0][a:b]
+                    res = (J, it.host[1][a:b]) if r.dydt else J
+                else:
+                    J = it.J[a:b]
+                    res = (J, it.F[a:b]) if r.dydt else J
+                r.future.set_result(res)
+            self._held -= it.bytes
+            self._free_streams.append(it.stream)
+        return bool(done)
+
+    def _admit(self) -> bool:
+        torch = self.torch
+        admitted = False
+        while True:
+            with self._cv:
+                if not self._queue or len(self._inflight) >= self.max_inflight or not self._free_streams:
+                    return admitted
+                head = self._queue[0]
+                model = self.models[head.name]
+                # merge queued requests of the head's model, in arrival order, up to the state cap
+                take, n = [], 0
+                for r in self._queue:
+                    if r.name != head.name:
+                        continue
+                    if take and n + r.n > self.max_batch_states:
+                        break
+                    take.append(r)
+                    n += r.n
+                need = self._bytes(model, n)
+                if self._held + need > self.hbm_budget:
+                    if len(take) > 1:                     # try the head alone
+                        take, n = [head], head.n
+                        need = self._bytes(model, n)
+                    if self._held + need > self.hbm_budget:
+                        self.stats["waits_for_memory"] += 1
+                        return admitted
+                for r in take:
+                    self._queue.remove(r)
+            it = _Iteration()
+            it.reqs, it.model, it.bytes = take, model, need
+            it.stream = self._free_streams.pop()
+            self._held += need
+            N = model.n_species
+            with torch.cuda.stream(it.stream):
+                T = torch.empty(n, dtype=torch.float64, device=self.device)
+                P = torch.empty(n, dtype=torch.float64, device=self.device)
+                Y = torch.empty((n, N), dtype=torch.float64, device=self.device)
+                a = 0
+                for r in take:
+                    b = a + r.n
+                    T[a:b].copy_(torch.as_tensor(r.T, dtype=torch.float64), non_blocking=True)
+                    P[a:b].copy_(torch.as_tensor(r.P, dtype=torch.float64), non_blocking=True)
+                    Y[a:b].copy_(torch.as_tensor(r.Y, dtype=torch.float64), non_blocking=True)
+                    it.offsets.append((a, b))
+                    a = b
+                it.J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device=self.device)
+                want_f = any(r.dydt for r in take)
+                it.F = torch.empty((n, N + 1), dtype=torch.float64, device=self.device) if want_f else None
+                model.eval_jacobian(T, P, Y, out=it.J, dydt_out=it.F, stream=it.stream)
+                if self.host_results:
+                    Jh = torch.empty(it.J.shape, dtype=torch.float64, pin_memory=True)
+                    Jh.copy_(it.J, non_blocking=True)
+                    Fh = None
+                    if it.F is not None:
+                        Fh = torch.empty(it.F.shape, dtype=torch.float64, pin_memory=True)
+                        Fh.copy_(it.F, non_blocking=True)
+                    it.host = (Jh.numpy(), Fh.numpy() if Fh is not None else None)
+                    it.J = it.F = None
+                it.event = torch.cuda.Event()
+                it.event.record(it.stream)
+            self._inflight.append(it)
+            self.stats["iterations"] += 1
+            self.stats["requests"] += len(take)
+            self.stats["merged_requests"] += len(take) - 1
+            self.stats["states"] += n
+            self.stats["max_inflight_seen"] = max(self.stats["max_inflight_seen"], len(self._inflight))
+            admitted = True
+
+
+def latency_summary(requests: List[Request]) -> dict:
+    lat = np.array([r.t_done - r.t_submit for r in requests if r.t_done is not None]) * 1e3
+    if lat.size == 0:
+        return {"n": 0}
+    return {"n": int(lat.size), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max())}
