@@ -242,24 +242,37 @@ def _barrier(ws):
         dist.barrier()
 
 
+def _reduce_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def _max_over_ranks(ws, x: float) -> float:
+    """Largest value over the ranks (the step time that counts for the whole job)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def _sum_over_ranks(ws, x: float) -> float:
+    """Sum over the ranks (states processed by the whole job)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def shard_states(cfg: int, rank: int, n_states=None):
+    """The batch a rank evaluates: the configuration's state count, its own seeded draw (weak
+    scaling: every rank owns a full-size batch, no data is exchanged)."""
+    return synth.config_states(cfg, n_states, seed_offset=1000 + rank)
 
 
 def workload_name(cfg: int) -> str:
@@ -294,7 +307,7 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     import torch
     import paper_1605_03262_b300 as pj
     model = synth.config_model(cfg)
-    T, P, Y = synth.config_states(cfg, n_states, seed_offset=1000 + rank)
+    T, P, Y = shard_states(cfg, rank, n_states)
     n, N = Y.shape
     blob = synth.to_bytes(model)
     g = pj.Model(blob)
