@@ -180,6 +180,32 @@ PJ_API int pj_batch_run(pj_batch *b, void *stream);
 PJ_API int pj_batch_info(const pj_batch *b, int *n_tiles, size_t *smem_bytes, int *threads_per_cta);
 PJ_API void pj_batch_free(pj_batch *b);
 
+/*
+ * Batched launch that allocates nothing (the paper has no counterpart; it serves callers, not the
+ * method). Some callers cannot allocate device memory where they call us: a reacting-flow solver
+ * that owns a fixed device memory pool and forbids cudaMalloc/cudaFree inside its time step
+ * (those calls can synchronise the device and fragment the pool), or code that must not meet an
+ * allocation failure in the middle of a run. pj_batch_run_noalloc evaluates the same items as
+ * pj_batch_create + pj_batch_run would (same arithmetic, same results), but keeps the launch's
+ * working data -- the item table, the tile bounds and the tile counter -- in one fixed static
+ * device array of the library (about 16 KB, held by every GPU that loads the library until the
+ * process exits) instead of device memory it would allocate. It calls no cudaMalloc, cudaFree or
+ * other allocating routine; the caller still provides every input and output buffer.
+ *
+ * Limits and rules:
+ *   - at most 64 items per call; more are rejected with PJ_EINVAL and a message naming the limit;
+ *   - which: 0 = Jacobian (jac required, dydt optional), 1 = source terms (dydt required);
+ *     tile_states: states per tile, 0 = four times the states a CTA evaluates concurrently;
+ *   - every call uses the same array, which keeps the last call's contents; each call re-writes
+ *     the table and zeroes the tile counter (copied from the host on the given stream) before its
+ *     kernel starts. Calls that overlap on the GPU race on the array: order them on one stream, or
+ *     wait for one to finish before issuing the next;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ *     that first call before any stream capture;
+ *   - asynchronous on the stream; argument errors as pj_batch_create.
+ */
+PJ_API int pj_batch_run_noalloc(const pj_batch_item *items, int n_items, int which, int tile_states, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,8 +28,13 @@
 // groups and loops persistently over states. All of a state's intermediates live in shared
 // memory. Reductions over species use a fixed 32-lane order that every warp repeats, so the
 // result of a state is bitwise independent of the launch shape.
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
 
+#include "../../include/pyjac_b300.h"
 #include "pj_internal.h"
 
 namespace pj {
@@ -794,3 +799,187 @@ cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads
 }
 
 }  // namespace pj
+
+// ---------------------------------------------------------------------------------------------
+// Batched launch without any allocation (pj_batch_run_noalloc).
+//
+// Some callers cannot allocate device memory in their call path: a solver or CFD code that owns a
+// fixed memory pool and forbids cudaMalloc/cudaFree inside its time step (both can synchronise the
+// device and fragment the pool), or code that must not meet an allocation failure mid-run. For
+// them the batched launch keeps its working data -- the item table, the tile bounds of every item
+// and the tile counter -- in the fixed static device array below instead of a cudaMalloc'd plan.
+// The caller still passes the state inputs and the outputs.
+
+namespace pj {
+
+constexpr int kNoAllocMaxItems = 64;   // largest number of items one call accepts
+
+struct NoAllocScratch {
+    int counter;                       // tile counter, zeroed at the start of every call
+    int n_items;
+    int pad[62];
+    int tile_first[kNoAllocMaxItems + 1];   // first tile of each item; tile_first[n_items] = tiles
+    long long tile_states[kNoAllocMaxItems];
+    long long n_states[kNoAllocMaxItems];
+    BatchItem items[kNoAllocMaxItems];
+};
+
+// The array (about 16 KB): held by every device that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+template <bool JAC>
+__global__ void __launch_bounds__(512, 1) pj_batch_noalloc_kernel(NoAllocScratch *scr, int ntiles) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ DevModel s_m;
+    __shared__ int s_tile, s_item;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int tile = atomicAdd(&scr->counter, 1);
+            int it = 0;
+            if (tile < ntiles)
+                while (it + 1 < scr->n_items && tile >= scr->tile_first[it + 1]) ++it;
+            s_tile = tile;
+            s_item = it;
+        }
+        __syncthreads();
+        const int tile = s_tile, item = s_item;
+        if (tile >= ntiles) break;
+        const BatchItem &it = scr->items[item];
+        const long long ts = scr->tile_states[item];
+        const long long begin = (long long)(tile - scr->tile_first[item]) * ts;
+        const long long end = min(begin + ts, scr->n_states[item]);
+        Grp g;
+        g.wps = it.wps;
+        g.G = it.wps * 32;
+        g.grp = threadIdx.x / g.G;
+        g.t = threadIdx.x - g.grp * g.G;
+        g.lane = threadIdx.x & 31;
+        g.wg = g.t >> 5;
+        double *S = smem + it.shared_const + size_t(g.grp) * it.sc.total;
+        if (item != cur) {
+            const int *src = reinterpret_cast<const int *>(it.m);
+            int *dst = reinterpret_cast<int *>(&s_m);
+            for (int w = threadIdx.x; w < int(sizeof(DevModel) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            load_model_consts(s_m, smem);
+            if (g.grp < it.groups) init_neutral<JAC>(s_m, it.sc, S, g.t);
+            cur = item;
+            __syncthreads();
+        }
+        if (g.grp < it.groups)
+            for (long long st = begin + g.grp; st < end; st += it.groups) eval_state<JAC, 0>(s_m, it.sc, S, smem, it.io, st, g);
+        __syncthreads();
+    }
+}
+
+}  // namespace pj
+
+namespace {
+
+// Device address of g_noalloc_scratch, looked up once per device (the symbol's host-side name is
+// only a stand-in and must never be handed to a kernel).
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+int noalloc_fail(int code, const std::string &msg) { return pj::set_error(code, msg); }
+
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const pj_batch_item *items, int n_items,
+                                                                          int which, int tile_states, void *stream) {
+    using namespace pj;
+    if (!items || n_items < 1 || (which != 0 && which != 1) || tile_states < 0)
+        return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: bad argument");
+    if (n_items > kNoAllocMaxItems)
+        return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: " + std::to_string(n_items) +
+                                           " items, more than the static scratch holds (" +
+                                           std::to_string(kNoAllocMaxItems) + ")");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return noalloc_fail(PJ_EUNSUPPORTED, "pj_batch_run_noalloc: device index above 63");
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // first call on this device: the set-up (do it before any stream capture)
+            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return noalloc_fail(PJ_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
+                                                  cudaGetErrorString(e));
+            }
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool jac = which == 0;
+    cudaFuncAttributes fa{};
+    e = jac ? cudaFuncGetAttributes(&fa, pj_batch_noalloc_kernel<true>)
+            : cudaFuncGetAttributes(&fa, pj_batch_noalloc_kernel<false>);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    const size_t budget = size_t(optin) > fa.sharedSizeBytes ? size_t(optin) - fa.sharedSizeBytes : 0;
+    const int threads = 512;
+
+    // the item table, built on the host stack and copied into the static scratch
+    NoAllocScratch h;
+    std::memset(&h, 0, sizeof(h));
+    h.n_items = n_items;
+    size_t smem = 0;
+    int ntiles = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const pj_batch_item &x = items[i];
+        const pj_mech *m = x.mech;
+        if (!m || x.n < 0) return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: null model or n < 0");
+        if (m->device != dev) return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: model lives on another device");
+        const int64_t N = m->N, nn = (N + 1) * (N + 1);
+        if (x.ldy < N || (jac && x.ldj < nn) || ((!jac || x.dydt) && x.ldd < N + 1))
+            return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: leading dimension too small");
+        if (x.n > 0 && (!x.T || !x.P || !x.Y || (jac && !x.jac) || (!jac && !x.dydt)))
+            return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: null input or output pointer");
+        int wps = (jac ? m->jac_cfg : m->dydt_cfg).wps;
+        while (wps * 32 > threads && wps > 1) wps /= 2;
+        const Scratch sc = make_scratch(m->N, m->R, m->dev.nslot, jac, wps, m->dev.rpc);
+        const int sconst = shared_const_doubles(m->N);
+        int groups = threads / (32 * wps);
+        if (wps > 1) groups = std::min(groups, 15);
+        while (groups > 0 && (size_t(sconst) + size_t(sc.total) * groups) * 8 > budget) --groups;
+        if (groups < 1) return noalloc_fail(PJ_EUNSUPPORTED, "pj_batch_run_noalloc: state working set exceeds shared memory");
+        smem = std::max(smem, (size_t(sconst) + size_t(sc.total) * groups) * 8);
+        BatchItem &b = h.items[i];
+        b.m = m->dev_model;
+        b.sc = sc;
+        b.io = BatchIO{x.T, x.P, x.Y, x.ldy, x.jac, x.ldj, x.dydt, x.ldd};
+        b.wps = wps;
+        b.groups = groups;
+        b.shared_const = sconst;
+        const long long ts = tile_states > 0 ? tile_states : 4LL * groups;
+        h.tile_states[i] = ts;
+        h.n_states[i] = x.n;
+        h.tile_first[i] = ntiles;
+        const long long nt = (x.n + ts - 1) / ts;
+        if (ntiles + nt > 0x7fffffffLL) return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: too many tiles");
+        ntiles += int(nt);
+    }
+    h.tile_first[n_items] = ntiles;
+    h.counter = 0;                     // what must start at zero: the tile counter
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the copy brings the zeroed counter and this call's table; a call still running on the GPU
+    // with the same array would race with it
+    e = cudaMemcpyAsync(scratch, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
+    if (ntiles == 0) return PJ_OK;
+    e = jac ? cudaFuncSetAttribute(pj_batch_noalloc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
+            : cudaFuncSetAttribute(pj_batch_noalloc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+    const int blocks = std::max(1, std::min(sms, ntiles));
+    NoAllocScratch *scr = static_cast<NoAllocScratch *>(scratch);
+    if (jac) pj_batch_noalloc_kernel<true><<<blocks, threads, smem, st>>>(scr, ntiles);
+    else pj_batch_noalloc_kernel<false><<<blocks, threads, smem, st>>>(scr, ntiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return PJ_OK;
+}
