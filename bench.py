@@ -407,7 +407,7 @@ def _request_trace(models, n_req, seed):
     return out
 
 
-def serving_form(seed: int = 7, open_loop_s: float = 3.0):
+def serving_form(seed: int = 7, open_loop_s: float = 2.0):
     """The serving form: continuous batching over the four resident models, against the plain
     per-mechanism launch (one request at a time, no merging, no overlap) on the same requests.
     Capacity = closed-loop throughput of a fixed trace; then Poisson arrivals at 0.5x and 0.8x that
@@ -423,7 +423,7 @@ def serving_form(seed: int = 7, open_loop_s: float = 3.0):
         models[synth.CONFIGS[cfg]["name"]] = g
 
     def run(trace, arrivals, **kw):
-        with Server(models, **kw) as srv:
+        with Server(models, discard_results=True, **kw) as srv:
             t0 = time.perf_counter()
             futs = []
             for (name, T, P, Y), ta in zip(trace, arrivals):
@@ -432,7 +432,7 @@ def serving_form(seed: int = 7, open_loop_s: float = 3.0):
                     time.sleep(dt)
                 futs.append(srv.submit(name, T, P, Y))
             for f in futs:
-                f.result()
+                f.result(timeout=300)
             wall = time.perf_counter() - t0
             stats = dict(srv.stats)
         states = sum(len(r[1]) for r in trace)
@@ -442,7 +442,7 @@ def serving_form(seed: int = 7, open_loop_s: float = 3.0):
         return out
 
     torch.cuda.synchronize()
-    cap_trace = _request_trace(models, 240, seed)
+    cap_trace = _request_trace(models, 160, seed)
     run(cap_trace[:20], [0.0] * 20)                          # warm-up (allocator, streams)
     cap = run(cap_trace, [0.0] * len(cap_trace))
     cap_plain = run(cap_trace, [0.0] * len(cap_trace), max_inflight=1, max_batch_states=1)

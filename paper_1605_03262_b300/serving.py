@@ -55,10 +55,13 @@ class Server:
     models: name -> paper_1605_03262_b300.Model (already loaded; their launch shapes are used).
     hbm_budget: bytes of device memory in-flight iterations may hold (default: half of the free
     memory at start). max_inflight: concurrent iterations (and streams). max_batch_states: states
-    merged into one launch. host_results: copy results to host memory (numpy) before completing."""
+    merged into one launch. host_results: copy results to host memory (numpy) before completing.
+    discard_results: complete futures with None and free the device results at once (throughput
+    and latency measurement). The budget covers in-flight work: results handed to clients as
+    device tensors are the clients' memory from then on."""
 
     def __init__(self, models: Dict[str, object], hbm_budget: Optional[int] = None, max_inflight: int = 6,
-                 max_batch_states: int = 65536, host_results: bool = False):
+                 max_batch_states: int = 65536, host_results: bool = False, discard_results: bool = False):
         import torch
         self.torch = torch
         self.models = dict(models)
@@ -68,6 +71,7 @@ class Server:
         self.max_inflight = int(max_inflight)
         self.max_batch_states = int(max_batch_states)
         self.host_results = bool(host_results)
+        self.discard_results = bool(discard_results)
         self._queue: collections.deque = collections.deque()
         self._inflight: List[_Iteration] = []
         self._streams = [torch.cuda.Stream(device=self.device) for _ in range(self.max_inflight)]
@@ -75,6 +79,8 @@ class Server:
         self._held = 0
         self._cv = threading.Condition()
         self._stop = False
+        self._drain = True
+        self.error: Optional[BaseException] = None
         self._thread: Optional[threading.Thread] = None
         self._next_id = 0
         self.stats = {"iterations": 0, "requests": 0, "states": 0, "max_inflight_seen": 0, "waits_for_memory": 0,
@@ -86,6 +92,8 @@ class Server:
         (n, N+1, N+1) as a CUDA tensor (or numpy array with host_results), or (J, dydt)."""
         if name not in self.models:
             raise KeyError("unknown model %r" % name)
+        if self.error is not None:
+            raise RuntimeError("server failed") from self.error
         need = self._bytes(self.models[name], int(Y.shape[0]))
         if need > self.hbm_budget:
             raise ValueError("request needs %d bytes of device memory, above the server's budget %d"
@@ -130,21 +138,33 @@ class Server:
     def _loop(self):
         torch = self.torch
         torch.cuda.set_device(self.device)
-        self._drain = True
-        while True:
-            progressed = self._retire()
-            with self._cv:
-                if self._stop and (not self._drain or (not self._queue and not self._inflight)):
-                    break
-            progressed |= self._admit()
-            if not progressed:
+        error = None
+        try:
+            while True:
+                progressed = self._retire()
                 with self._cv:
-                    if not self._queue or len(self._inflight) >= self.max_inflight:
-                        self._cv.wait(timeout=0.0002 if self._inflight else 0.05)
-        # fail whatever is left (stop without drain)
+                    if self._stop and (not self._drain or (not self._queue and not self._inflight)):
+                        break
+                progressed |= self._admit()
+                if not progressed:
+                    with self._cv:
+                        if not self._queue or len(self._inflight) >= self.max_inflight or not self._free_streams:
+                            self._cv.wait(timeout=0.0002 if self._inflight else 0.05)
+        except BaseException as exc:          # a failed launch or allocation must not strand clients
+            error = exc
+        # fail whatever is left: queued requests (stop without drain, or an error) and, after an
+        # error, the requests of iterations that will not be retired
         with self._cv:
-            while self._queue:
-                self._queue.popleft().future.set_exception(RuntimeError("server stopped"))
+            self.error = error
+            pending = list(self._queue)
+            self._queue.clear()
+        if error is not None:
+            for it in self._inflight:
+                pending += it.reqs
+            self._inflight = []
+        for r in pending:
+            if not r.future.done():
+                r.future.set_exception(error if error is not None else RuntimeError("server stopped"))
 
     def _retire(self) -> bool:
         done = [it for it in self._inflight if it.event.query()]
@@ -153,6 +173,9 @@ class Server:
             t = time.perf_counter()
             for r, (a, b) in zip(it.reqs, it.offsets):
                 r.t_done = t
+                if self.discard_results:
+                    r.future.set_result(None)
+                    continue
                 if self.host_results:
                     J = it.host[0][a:b]
                     res = (J, it.host[1][a:b]) if r.dydt else J
