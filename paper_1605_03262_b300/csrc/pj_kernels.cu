@@ -81,6 +81,27 @@ __device__ __forceinline__ double sel4(const double (&v)[kMaxSlots], int i) {
     return i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
 }
 
+// Runs f(item, aux) over one lane's items of a schedule chunk (lane-interleaved, stride 32),
+// issuing the item loads of kSchedBatch iterations together so that their latency overlaps.
+constexpr int kSchedBatch = 8;
+
+template <bool AUX, class F>
+__device__ __forceinline__ void run_items(const unsigned *it, const int *ax, int len, F &&f) {
+    for (int x0 = 0; x0 < len; x0 += kSchedBatch) {
+        unsigned v[kSchedBatch];
+        int a[kSchedBatch];
+#pragma unroll
+        for (int u = 0; u < kSchedBatch; ++u) {
+            v[u] = (x0 + u < len) ? __ldg(it + 32 * (x0 + u)) : 0u;
+            if constexpr (AUX) a[u] = (x0 + u < len) ? __ldg(ax + 32 * (x0 + u)) : 0;
+            else a[u] = 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSchedBatch; ++u)
+            if (x0 + u < len) f(v[u], a[u]);
+    }
+}
+
 struct StateScalars {
     double T, invT, lnT, P, lnP, W, rho, Ctot;
 };
@@ -510,18 +531,17 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         for (int c = wg; c < m.ng; c += NW) {       // omega_k through the species-gather schedule
             const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
             const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-            const unsigned *it = m.g_items + ioff + lane;
+            int k_next = __ldg(dst);
             double w = 0.0;
-            for (int x = 0; x < len; ++x) {
-                const unsigned v = __ldg(it + 32 * x);
+            run_items<false>(m.g_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
                 w = fma(sNu[(v >> 24) & 127], sq[v & 0xffffff], w);
                 if (v >> 31) {
-                    const int k = __ldg(dst);
-                    dst += 32;
-                    sf[k] = __ldg(m.W + k) * invrho * w;
+                    sf[k_next] = __ldg(m.W + k_next) * invrho * w;
                     w = 0.0;
+                    dst += 32;
+                    k_next = __ldg(dst);
                 }
-            }
+            });
         }
         group_sync<WPS>(g);
         double hf = 0.0;
@@ -537,60 +557,60 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         for (int c = wg; c < m.ng; c += NW) {       // omega_k, J_k0, A_k
             const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
             const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-            const unsigned *it = m.g_items + ioff + lane;
+            int k_next = __ldg(dst);
             double wq = 0.0, wt = 0.0, wa = 0.0;
-            for (int x = 0; x < len; ++x) {
-                const unsigned v = __ldg(it + 32 * x);
+            run_items<false>(m.g_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
                 const int i = v & 0xffffff;
                 const double nu = sNu[(v >> 24) & 127];
                 wq = fma(nu, sq[i], wq);
                 wt = fma(nu, sth[i], wt);
                 wa = fma(nu, sa[i], wa);
                 if (v >> 31) {
-                    const int k = __ldg(dst);
-                    dst += 32;
+                    const int k = k_next;
                     const double pre = __ldg(m.W + k) * invrho;
                     sf[k] = pre * wq;
                     sJk0[k] = pre * wt;
                     sA[k] = pre * fma(s.W, wq, wa);
                     wq = wt = wa = 0.0;
+                    dst += 32;
+                    k_next = __ldg(dst);
                 }
-            }
+            });
         }
         for (int c = wg; c < m.nh; c += NW) {       // HS_j = (1/W_j) sum_i dH_i b'_ij
             const int ioff = __ldg(m.h_chunk + 3 * c), len = __ldg(m.h_chunk + 3 * c + 1);
             const int *dst = m.h_dst + __ldg(m.h_chunk + 3 * c + 2) + lane;
-            const unsigned *it = m.h_items + ioff + lane;
-            const int *ax = m.h_aux + ioff + lane;
+            int j_next = __ldg(dst);
             double acc = 0.0;
-            for (int x = 0; x < len; ++x) {
-                const unsigned v = __ldg(it + 32 * x);
-                acc = fma(sdH[__ldg(ax + 32 * x)], sb[v & 0xffffff], acc);
+            run_items<true>(m.h_items + ioff + lane, m.h_aux + ioff + lane, len, [&](unsigned v, int rxn) {
+                acc = fma(sdH[rxn], sb[v & 0xffffff], acc);
                 if (v >> 31) {
-                    const int j = __ldg(dst);
-                    dst += 32;
-                    sHS[j] = acc * sInvW[j];
+                    sHS[j_next] = acc * sInvW[j_next];
                     acc = 0.0;
+                    dst += 32;
+                    j_next = __ldg(dst);
                 }
-            }
+            });
         }
         for (int c = wg; c < m.ncc; c += NW) {      // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
             const int ioff = __ldg(m.c_chunk + 3 * c), len = __ldg(m.c_chunk + 3 * c + 1);
             const int eoff = __ldg(m.c_chunk + 3 * c + 2) + lane;
             const int *dst = m.c_dst + eoff;
             const double *scl = m.c_scale + eoff;
-            const unsigned *it = m.c_items + ioff + lane;
+            int k_next = __ldg(dst);
+            double s_next = __ldg(scl);
             double acc = 0.0;
-            for (int x = 0; x < len; ++x) {
-                const unsigned v = __ldg(it + 32 * x);
+            run_items<false>(m.c_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
                 acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
                 if (v >> 31) {
-                    sCk[__ldg(dst)] = -__ldg(scl) * acc;
+                    sCk[k_next] = -s_next * acc;
+                    acc = 0.0;
                     dst += 32;
                     scl += 32;
-                    acc = 0.0;
+                    k_next = __ldg(dst);
+                    s_next = __ldg(scl);
                 }
-            }
+            });
         }
         group_sync<WPS>(g);
         double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
@@ -614,14 +634,26 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         double *Jout = io.jac + st * io.ldj;
         for (int c = wg; c < m.n_row_chunks; c += NW) {
             const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
-            for (int x = lane; x < nel; x += 32) {
-                const int rr = x / ld, j = x - rr * ld, r = r0 + rr;
-                double v;
-                if (j == 0) v = (r == 0) ? J00 : sJk0[r - 1];
-                else if (j == N) v = 0.0;
-                else if (r == 0) v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
-                else v = fma(sA[r - 1], sDelta[j - 1], sCk[r - 1]);
-                stage[x] = v;
+            {
+                int rr = 0, j = lane;                  // (row in chunk, column) of element x
+                while (j >= ld) {
+                    j -= ld;
+                    ++rr;
+                }
+                for (int x = lane; x < nel; x += 32) {
+                    const int r = r0 + rr;
+                    double v;
+                    if (j == 0) v = (r == 0) ? J00 : sJk0[r - 1];
+                    else if (j == N) v = 0.0;
+                    else if (r == 0) v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
+                    else v = fma(sA[r - 1], sDelta[j - 1], sCk[r - 1]);
+                    stage[x] = v;
+                    j += 32;
+                    while (j >= ld) {
+                        j -= ld;
+                        ++rr;
+                    }
+                }
             }
             __syncwarp();
             {
@@ -629,19 +661,20 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                 const int eoff = __ldg(m.s_chunk + 3 * c + 2) + lane;
                 const int *dst = m.s_dst + eoff;
                 const double *scl = m.s_scale + eoff;
-                const unsigned *it = m.s_items + ioff + lane;
+                int d_next = __ldg(dst);
+                double s_next = __ldg(scl);
                 double acc = 0.0;
-                for (int x = 0; x < len; ++x) {
-                    const unsigned v = __ldg(it + 32 * x);
+                run_items<false>(m.s_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
                     acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
                     if (v >> 31) {
-                        const int d = __ldg(dst);
-                        stage[d] = fma(__ldg(scl), acc, stage[d]);
+                        stage[d_next] = fma(s_next, acc, stage[d_next]);
+                        acc = 0.0;
                         dst += 32;
                         scl += 32;
-                        acc = 0.0;
+                        d_next = __ldg(dst);
+                        s_next = __ldg(scl);
                     }
-                }
+                });
             }
             __syncwarp();
             store_segment(Jout + (long long)r0 * ld, stage, nel, lane);

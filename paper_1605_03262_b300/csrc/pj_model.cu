@@ -599,6 +599,9 @@ HostImage build_image(const void *buf, size_t len) {
             emit_chunk(ptrs, zero_slot, zero_code, 0, im.s_items, nullptr, im.s_dst, &im.s_scale, im.s_chunk);
         }
     }
+    // one row of padding after the last chunk's entries: a lane prefetches its next entry record
+    for (auto *v : {&im.g_dst, &im.h_dst, &im.c_dst, &im.s_dst}) v->insert(v->end(), 32, 0);
+    for (auto *v : {&im.c_scale, &im.s_scale}) v->insert(v->end(), 32, 0.0);
     return im;
 }
 
