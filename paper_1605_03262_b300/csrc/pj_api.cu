@@ -45,7 +45,7 @@ DeviceProps device_props(int dev) {
 
 
 size_t smem_bytes(const pj_mech *m, bool jac, const pj::LaunchCfg &c) {
-    pj::Scratch sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, m->dev.rpc);
+    pj::Scratch sc = pj::make_scratch(m->dev, jac, c.wps);
     return (size_t(pj::shared_const_doubles(m->N)) + size_t(sc.total) * c.groups) * sizeof(double);
 }
 
@@ -79,8 +79,7 @@ pj::LaunchCfg default_cfg(const pj_mech *m, bool jac, int wps) {
 
 pj::LaunchCfg pick_default(const pj_mech *m, bool jac) {
     const int N = m->N;
-    // measured on B300: two warps per state up to ~100 species, then wider groups
-    int wps = jac ? (N <= 24 ? 1 : N <= 96 ? 2 : N <= 200 ? 4 : 16) : (N <= 128 ? 1 : 2);
+    int wps = pj::default_wps(N, jac);
     pj::LaunchCfg c = default_cfg(m, jac, wps);
     while (c.groups == 0 && wps < 16) {   // grow the group until one state fits
         wps *= 2;
@@ -122,7 +121,7 @@ int launch(const pj_mech *m, bool jac, int64_t n, const double *T, const double 
         return fail(PJ_EUNSUPPORTED, "one state's working set does not fit in shared memory for this model");
     pj::KParams p{};
     p.m = m->dev;
-    p.sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, c.wps, m->dev.rpc);
+    p.sc = pj::make_scratch(m->dev, jac, c.wps);
     p.n = n;
     p.T = T;
     p.P = P;
@@ -187,7 +186,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
            o_ci = push(blob, im.c_items), o_ha = push(blob, im.h_aux), o_sc = push(blob, im.s_chunk),
            o_gc = push(blob, im.g_chunk), o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk),
            o_sd = push(blob, im.s_dst), o_gd = push(blob, im.g_dst), o_hd = push(blob, im.h_dst),
-           o_cd = push(blob, im.c_dst), o_ss = push(blob, im.s_scale), o_cs2 = push(blob, im.c_scale);
+           o_cd = push(blob, im.c_dst), o_ss = push(blob, im.s_scale), o_cs2 = push(blob, im.c_scale),
+           o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst);
     pj::MathTables tables;
     pj::build_math_tables(tables);
     std::vector<pj::MathTables> tvec(1, tables);
@@ -252,6 +252,10 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.ng = im.ng;
     d.nh = im.nh;
     d.ncc = im.ncc;
+    d.ngp = im.ngp;
+    d.nhp = im.nhp;
+    d.g_pfirst = reinterpret_cast<const int *>(b + o_gpf);
+    d.h_pfirst = reinterpret_cast<const int *>(b + o_hpf);
     d.s_items = reinterpret_cast<const unsigned *>(b + o_si);
     d.g_items = reinterpret_cast<const unsigned *>(b + o_gi);
     d.h_items = reinterpret_cast<const unsigned *>(b + o_hi);

@@ -93,7 +93,7 @@ int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj
         }
         int wps = (jac ? m->jac_cfg : m->dydt_cfg).wps;
         while (wps * 32 > threads && wps > 1) wps /= 2;
-        const pj::Scratch sc = pj::make_scratch(m->N, m->R, m->dev.nslot, jac, wps, m->dev.rpc);
+        const pj::Scratch sc = pj::make_scratch(m->dev, jac, wps);
         const int sconst = pj::shared_const_doubles(m->N);
         int groups = threads / (32 * wps);
         if (wps > 1) groups = std::min(groups, 15);

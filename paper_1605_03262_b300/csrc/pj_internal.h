@@ -78,6 +78,8 @@ struct DevModel {
     // end-of-sum flag (bit 31); entries (one per finished sum) are lane-interleaved too.
     int rpc, n_row_chunks;    // rows per staged chunk, chunks covering the N+1 rows
     int ng, nh, ncc;          // chunks of the species-gather, column-sum and C_k schedules
+    int ngp, nhp;             // pieces of the species-gather and column-sum lists (partial sums)
+    const int *g_pfirst, *h_pfirst;   // per species / column: first piece (N + 1 entries)
     const unsigned *s_items, *g_items, *h_items, *c_items;
     const int *h_aux;         // reaction of each column-sum item
     const int *s_chunk, *g_chunk, *h_chunk, *c_chunk;   // per chunk: item offset, length, entry offset
@@ -88,7 +90,7 @@ struct DevModel {
 
 // Offsets (in doubles) of one state's scratch in shared memory.
 struct Scratch {
-    int C, B, dB, H, cpk, Jk0, A, Ck, f, HS, q, th, a, dH, b, rows, total;
+    int C, B, dB, H, cpk, Jk0, A, Ck, f, HS, q, th, a, dH, b, rows, part, total;
     int rows_per_chunk;       // rows staged per warp chunk
 };
 
@@ -157,7 +159,8 @@ struct HostImage {
     std::vector<int> perm;
     int N = 0, R = 0, NE = 0;
     // lane-balanced schedules
-    int rpc = 1, n_row_chunks = 0, ng = 0, nh = 0, ncc = 0;
+    int rpc = 1, n_row_chunks = 0, ng = 0, nh = 0, ncc = 0, ngp = 0, nhp = 0;
+    std::vector<int> g_pfirst, h_pfirst;
     std::vector<unsigned> s_items, g_items, h_items, c_items;
     std::vector<int> h_aux, s_chunk, g_chunk, h_chunk, c_chunk, s_dst, g_dst, h_dst, c_dst;
     std::vector<double> s_scale, c_scale;
@@ -166,7 +169,12 @@ struct HostImage {
 constexpr int kNuBias = 64;          // coefficient code = nu + kNuBias (7 bits)
 
 HostImage build_image(const void *buf, size_t len);                 // throws FormatError / Unsupported
-Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_chunk);
+Scratch make_scratch(const DevModel &m, bool jac, int wps);
+// Warps per state of the default launch shape; also the number of warps the gather schedules are
+// split for (measured on B300: two warps per state up to ~100 species, then wider groups).
+inline int default_wps(int N, bool jac) {
+    return jac ? (N <= 24 ? 1 : N <= 96 ? 2 : N <= 200 ? 4 : 16) : (N <= 128 ? 1 : 2);
+}
 int shared_const_doubles(int N);
 cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream);
 cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem);

@@ -485,6 +485,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
     double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
     double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
+    double *spart = S + sc.part;
     (void)sHS;
     // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
     StateScalars s;
@@ -531,17 +532,23 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         for (int c = wg; c < m.ng; c += NW) {       // omega_k through the species-gather schedule
             const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
             const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-            int k_next = __ldg(dst);
+            int p_next = __ldg(dst);
             double w = 0.0;
             run_items<false>(m.g_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
                 w = fma(sNu[(v >> 24) & 127], sq[v & 0xffffff], w);
                 if (v >> 31) {
-                    sf[k_next] = __ldg(m.W + k_next) * invrho * w;
+                    spart[p_next] = w;
                     w = 0.0;
                     dst += 32;
-                    k_next = __ldg(dst);
+                    p_next = __ldg(dst);
                 }
             });
+        }
+        group_sync<WPS>(g);
+        for (int k = t; k < N; k += G) {                // each species: its pieces' partials, in order
+            double w = 0.0;
+            for (int p = __ldg(m.g_pfirst + k); p < __ldg(m.g_pfirst + k + 1); ++p) w += spart[p];
+            sf[k] = __ldg(m.W + k) * invrho * w;
         }
         group_sync<WPS>(g);
         double hf = 0.0;
@@ -566,11 +573,10 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                 wt = fma(nu, sth[i], wt);
                 wa = fma(nu, sa[i], wa);
                 if (v >> 31) {
-                    const int k = k_next;
-                    const double pre = __ldg(m.W + k) * invrho;
-                    sf[k] = pre * wq;
-                    sJk0[k] = pre * wt;
-                    sA[k] = pre * fma(s.W, wq, wa);
+                    double *pp = spart + 3 * k_next;   // k_next: this piece's partial slot
+                    pp[0] = wq;
+                    pp[1] = wt;
+                    pp[2] = wa;
                     wq = wt = wa = 0.0;
                     dst += 32;
                     k_next = __ldg(dst);
@@ -585,7 +591,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
             run_items<true>(m.h_items + ioff + lane, m.h_aux + ioff + lane, len, [&](unsigned v, int rxn) {
                 acc = fma(sdH[rxn], sb[v & 0xffffff], acc);
                 if (v >> 31) {
-                    sHS[j_next] = acc * sInvW[j_next];
+                    spart[3 * m.ngp + j_next] = acc;
                     acc = 0.0;
                     dst += 32;
                     j_next = __ldg(dst);
@@ -611,6 +617,28 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                     s_next = __ldg(scl);
                 }
             });
+        }
+        group_sync<WPS>(g);
+        // combine: each species / column sums its pieces' partials, in order
+        for (int item = t; item < 2 * N; item += G) {
+            if (item < N) {
+                const int k = item;
+                double wq = 0.0, wt = 0.0, wa = 0.0;
+                for (int p = __ldg(m.g_pfirst + k); p < __ldg(m.g_pfirst + k + 1); ++p) {
+                    wq += spart[3 * p];
+                    wt += spart[3 * p + 1];
+                    wa += spart[3 * p + 2];
+                }
+                const double pre = __ldg(m.W + k) * invrho;
+                sf[k] = pre * wq;
+                sJk0[k] = pre * wt;
+                sA[k] = pre * fma(s.W, wq, wa);
+            } else {
+                const int j = item - N;
+                double hs = 0.0;
+                for (int p = __ldg(m.h_pfirst + j); p < __ldg(m.h_pfirst + j + 1); ++p) hs += spart[3 * m.ngp + p];
+                sHS[j] = hs * sInvW[j];
+            }
         }
         group_sync<WPS>(g);
         double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
@@ -752,7 +780,8 @@ __global__ void __launch_bounds__(512, 1) pj_batch_kernel(const __grid_constant_
 // ---------------------------------------------------------------------------------------------
 // host-side launch helpers
 
-Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_chunk) {
+Scratch make_scratch(const DevModel &m, bool jac, int wps) {
+    const int N = m.N, R = m.R;
     Scratch sc{};
     int o = 0;
     auto take = [&](int n) {
@@ -775,12 +804,15 @@ Scratch make_scratch(int N, int R, int nslot, bool jac, int wps, int rows_per_ch
         sc.th = take(R + 1);
         sc.a = take(R + 1);
         sc.dH = take(R + 1);
-        sc.b = take(nslot + 1);
-        sc.rows_per_chunk = rows_per_chunk;
-        sc.rows = take(wps * rows_per_chunk * (N + 1));
+        sc.b = take(m.nslot + 1);
+        sc.rows_per_chunk = m.rpc;
+        // the row-staging buffers and the gather's partial sums are never live at the same time
+        sc.rows = take(std::max(wps * m.rpc * (N + 1), 3 * m.ngp + m.nhp));
+        sc.part = sc.rows;
     } else {
         sc.dB = sc.Jk0 = sc.A = sc.Ck = sc.HS = sc.th = sc.a = sc.dH = sc.b = sc.rows = 0;
         sc.rows_per_chunk = 0;
+        sc.part = take(m.ngp);
     }
     sc.total = o;
     return sc;
@@ -975,7 +1007,7 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const
             return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: null input or output pointer");
         int wps = (jac ? m->jac_cfg : m->dydt_cfg).wps;
         while (wps * 32 > threads && wps > 1) wps /= 2;
-        const Scratch sc = make_scratch(m->N, m->R, m->dev.nslot, jac, wps, m->dev.rpc);
+        const Scratch sc = make_scratch(m->dev, jac, wps);
         const int sconst = shared_const_doubles(m->N);
         int groups = threads / (32 * wps);
         if (wps > 1) groups = std::min(groups, 15);

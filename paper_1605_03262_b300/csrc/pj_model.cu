@@ -258,15 +258,16 @@ void ensure_nonempty(Task &t, unsigned pad_idx, int pad_code, int pad_aux) {
 }
 
 // Splits tasks into chunks with at least 32 x (longest task) items each, so that the longest
-// task does not dominate its chunk; returns the chunks' task lists (balanced by item count).
-std::vector<std::vector<const Task *>> split_chunks(const std::vector<Task> &tasks) {
+// task does not dominate its chunk, and at most n_max chunks; returns the chunks' task lists
+// (balanced by item count).
+std::vector<std::vector<const Task *>> split_chunks(const std::vector<Task> &tasks, int n_max = 16) {
     size_t total = 0, longest = 1;
     for (auto &t : tasks) {
         total += t.idx.size();
         longest = std::max(longest, t.idx.size());
     }
     int n = int(std::max<size_t>(1, total / (32 * longest)));
-    n = std::min(n, 16);
+    n = std::min(n, n_max);
     std::vector<std::vector<const Task *>> out(n);
     std::vector<size_t> load(n, 0);
     std::vector<const Task *> order;
@@ -281,6 +282,37 @@ std::vector<std::vector<const Task *>> split_chunks(const std::vector<Task> &tas
         load[best] += t->idx.size();
     }
     return out;
+}
+
+// Cuts every task into consecutive pieces of at most piece_len items (each piece one lane's
+// ordered partial sum, written to partial slot dst = piece id). first[k] .. first[k+1] are the
+// pieces of task k, in order.
+std::vector<Task> cut_pieces(const std::vector<Task> &tasks, size_t piece_len, std::vector<int> &first) {
+    std::vector<Task> out;
+    first.assign(tasks.size() + 1, 0);
+    for (size_t k = 0; k < tasks.size(); ++k) {
+        first[k] = int(out.size());
+        const Task &t = tasks[k];
+        for (size_t b = 0; b < t.idx.size(); b += piece_len) {
+            Task p;
+            const size_t e = std::min(t.idx.size(), b + piece_len);
+            p.idx.assign(t.idx.begin() + b, t.idx.begin() + e);
+            p.code.assign(t.code.begin() + b, t.code.begin() + e);
+            p.aux.assign(t.aux.begin() + b, t.aux.begin() + e);
+            p.dst = int(out.size());
+            p.scale = t.scale;
+            out.push_back(std::move(p));
+        }
+    }
+    first[tasks.size()] = int(out.size());
+    return out;
+}
+
+// Piece length that lets the gather lists spread over n_warps warps of 32 lanes.
+size_t piece_length(const std::vector<Task> &tasks, int n_warps) {
+    size_t total = 0;
+    for (auto &t : tasks) total += t.idx.size();
+    return std::max<size_t>(8, (total + 32 * size_t(n_warps) - 1) / (32 * size_t(n_warps)));
 }
 
 int nu_code(double nu) {
@@ -529,7 +561,10 @@ HostImage build_image(const void *buf, size_t len) {
             }
             ensure_nonempty(tasks[k], zero_rxn, zero_code, 0);
         }
-        auto chunks = split_chunks(tasks);
+        const int nw = default_wps(N, true);
+        auto pieces = cut_pieces(tasks, piece_length(tasks, nw), im.g_pfirst);
+        im.ngp = int(pieces.size());
+        auto chunks = split_chunks(pieces, nw);
         for (auto &c : chunks) emit_chunk(c, zero_rxn, zero_code, 0, im.g_items, nullptr, im.g_dst, nullptr, im.g_chunk);
         im.ng = int(chunks.size());
     }
@@ -545,7 +580,10 @@ HostImage build_image(const void *buf, size_t len) {
             }
             ensure_nonempty(tasks[l], zero_slot, zero_code, R);
         }
-        auto chunks = split_chunks(tasks);
+        const int nw = default_wps(N, true);
+        auto pieces = cut_pieces(tasks, piece_length(tasks, nw), im.h_pfirst);
+        im.nhp = int(pieces.size());
+        auto chunks = split_chunks(pieces, nw);
         for (auto &c : chunks)
             emit_chunk(c, zero_slot, zero_code, R, im.h_items, &im.h_aux, im.h_dst, nullptr, im.h_chunk);
         im.nh = int(chunks.size());
