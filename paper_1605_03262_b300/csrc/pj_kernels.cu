@@ -485,7 +485,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
     double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
     double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
-    double *spart = S + sc.part;
+    double *spart = S + sc.part, *sred = S + sc.red;
     (void)sHS;
     // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
     StateScalars s;
@@ -507,15 +507,33 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         }
     }
     group_sync<WPS>(g);
-    double r1 = 0.0, r2 = 0.0, r3 = 0.0;
-    for (int k = lane; k < N; k += 32) {
-        const double y = sY[k];
-        r1 = fma(y, sInvW[k], r1);
-        r2 = fma(y, scp[k], r2);
-        if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
+    // species sums sum Y/W, sum Y cp_k, sum Y dcp_k/dT in a fixed 32-lane order: repeated per
+    // warp in narrow groups, one warp each in wide ones (same order, same bits)
+    double sYW, cp, dcpdT;
+    if (NW < 4) {
+        double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        for (int k = lane; k < N; k += 32) {
+            const double y = sY[k];
+            r1 = fma(y, sInvW[k], r1);
+            r2 = fma(y, scp[k], r2);
+            if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
+        }
+        sYW = warp_sum(r1);
+        cp = warp_sum(r2);
+        dcpdT = JAC ? warp_sum(r3) : 0.0;
+    } else {
+        if (wg < (JAC ? 3 : 2)) {
+            const double *xs = wg == 0 ? sInvW : wg == 1 ? scp : sJk0;
+            double r = 0.0;
+            for (int k = lane; k < N; k += 32) r = fma(sY[k], xs[k], r);
+            r = warp_sum(r);
+            if (lane == 0) sred[wg] = r;
+        }
+        group_sync<WPS>(g);
+        sYW = sred[0];
+        cp = sred[1];
+        dcpdT = JAC ? sred[2] : 0.0;
     }
-    const double sYW = warp_sum(r1), cp = warp_sum(r2);
-    const double dcpdT = JAC ? warp_sum(r3) : 0.0;
     s.W = 1.0 / sYW;
     s.Ctot = s.P / (kR * s.T);
     s.rho = s.Ctot * s.W;
@@ -641,15 +659,38 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
             }
         }
         group_sync<WPS>(g);
-        double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
-        for (int k = lane; k < N; k += 32) {
-            const double hk = sH[k] * sInvW[k];
-            x1 = fma(hk, sA[k], x1);
-            x2 = fma(hk, sf[k], x2);
-            x3 = fma(hk, sJk0[k], x3);
-            x4 = fma(scp[k], sf[k], x4);
+        // energy sums HA, Hf, HJ0, CF: repeated per warp in narrow groups, one warp each in wide ones
+        double HA, Hf, HJ0, CF;
+        if (NW < 4) {
+            double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
+            for (int k = lane; k < N; k += 32) {
+                const double hk = sH[k] * sInvW[k];
+                x1 = fma(hk, sA[k], x1);
+                x2 = fma(hk, sf[k], x2);
+                x3 = fma(hk, sJk0[k], x3);
+                x4 = fma(scp[k], sf[k], x4);
+            }
+            HA = warp_sum(x1);
+            Hf = warp_sum(x2);
+            HJ0 = warp_sum(x3);
+            CF = warp_sum(x4);
+        } else {
+            if (wg < 4) {
+                const double *v = wg == 0 ? sA : wg == 2 ? sJk0 : sf;
+                double x = 0.0;
+                for (int k = lane; k < N; k += 32) {
+                    const double uk = wg == 3 ? scp[k] : sH[k] * sInvW[k];
+                    x = fma(uk, v[k], x);
+                }
+                x = warp_sum(x);
+                if (lane == 0) sred[4 + wg] = x;
+            }
+            group_sync<WPS>(g);
+            HA = sred[4];
+            Hf = sred[5];
+            HJ0 = sred[6];
+            CF = sred[7];
         }
-        const double HA = warp_sum(x1), Hf = warp_sum(x2), HJ0 = warp_sum(x3), CF = warp_sum(x4);
         const double invcp = 1.0 / cp;
         const double J00 = -invcp * (fma(-dcpdT * invcp, Hf, CF) + HJ0);
         const double HSN = sHS[N - 1], cpN = scp[N - 1];
@@ -794,6 +835,7 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
     sc.H = take(N);
     sc.cpk = take(N);
     sc.f = take(N);
+    sc.red = take(8);
     sc.q = take(R + 1);
     if (jac) {
         sc.dB = take(N);
