@@ -182,12 +182,9 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
            o_cs = push(blob, im.col_slot), o_cr = push(blob, im.col_rxn), o_rp = push(blob, im.row_ptr),
            o_nc = push(blob, im.nnz_col), o_ncp = push(blob, im.nnz_cptr), o_nw = push(blob, im.nnz_wr),
            o_cns = push(blob, im.con_slot), o_cnn = push(blob, im.con_nu), o_cN = push(blob, im.colN_nnz);
-    size_t o_si = push(blob, im.s_items), o_gi = push(blob, im.g_items), o_hi = push(blob, im.h_items),
-           o_ci = push(blob, im.c_items), o_ha = push(blob, im.h_aux), o_sc = push(blob, im.s_chunk),
-           o_gc = push(blob, im.g_chunk), o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk),
-           o_sd = push(blob, im.s_dst), o_gd = push(blob, im.g_dst), o_hd = push(blob, im.h_dst),
-           o_cd = push(blob, im.c_dst), o_ss = push(blob, im.s_scale), o_cs2 = push(blob, im.c_scale),
-           o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst);
+    size_t o_gr = push(blob, im.g_rec), o_hr = push(blob, im.h_rec), o_cr2 = push(blob, im.c_rec),
+           o_sr = push(blob, im.s_rec), o_sc = push(blob, im.s_chunk), o_gc = push(blob, im.g_chunk),
+           o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst);
     pj::MathTables tables;
     pj::build_math_tables(tables);
     std::vector<pj::MathTables> tvec(1, tables);
@@ -256,21 +253,14 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.nhp = im.nhp;
     d.g_pfirst = reinterpret_cast<const int *>(b + o_gpf);
     d.h_pfirst = reinterpret_cast<const int *>(b + o_hpf);
-    d.s_items = reinterpret_cast<const unsigned *>(b + o_si);
-    d.g_items = reinterpret_cast<const unsigned *>(b + o_gi);
-    d.h_items = reinterpret_cast<const unsigned *>(b + o_hi);
-    d.c_items = reinterpret_cast<const unsigned *>(b + o_ci);
-    d.h_aux = reinterpret_cast<const int *>(b + o_ha);
-    d.s_chunk = reinterpret_cast<const int *>(b + o_sc);
-    d.g_chunk = reinterpret_cast<const int *>(b + o_gc);
-    d.h_chunk = reinterpret_cast<const int *>(b + o_hc);
-    d.c_chunk = reinterpret_cast<const int *>(b + o_cc);
-    d.s_dst = reinterpret_cast<const int *>(b + o_sd);
-    d.g_dst = reinterpret_cast<const int *>(b + o_gd);
-    d.h_dst = reinterpret_cast<const int *>(b + o_hd);
-    d.c_dst = reinterpret_cast<const int *>(b + o_cd);
-    d.s_scale = reinterpret_cast<const double *>(b + o_ss);
-    d.c_scale = reinterpret_cast<const double *>(b + o_cs2);
+    d.g_rec = reinterpret_cast<const uint2 *>(b + o_gr);
+    d.h_rec = reinterpret_cast<const uint4 *>(b + o_hr);
+    d.c_rec = reinterpret_cast<const uint4 *>(b + o_cr2);
+    d.s_rec = reinterpret_cast<const uint4 *>(b + o_sr);
+    d.s_chunk = reinterpret_cast<const int2 *>(b + o_sc);
+    d.g_chunk = reinterpret_cast<const int2 *>(b + o_gc);
+    d.h_chunk = reinterpret_cast<const int2 *>(b + o_hc);
+    d.c_chunk = reinterpret_cast<const int2 *>(b + o_cc);
     d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
     m->dev_model = reinterpret_cast<const pj::DevModel *>(b + o_dm);
     e = cudaMemcpy(b + o_dm, &d, sizeof(d), cudaMemcpyHostToDevice);

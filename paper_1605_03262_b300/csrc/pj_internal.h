@@ -73,18 +73,19 @@ struct DevModel {
     const double *con_nu;
     const int *colN_nnz;      // per row k: nnz index of column N-1, or -1
     double lnPatmR;           // ln(p_atm / R)
-    // Lane-balanced schedules (see pj_model.cu): items are lane-interleaved (chunk offset +
-    // t*32 + lane); an item packs an index (24 bits), a coefficient code (7 bits) and an
-    // end-of-sum flag (bit 31); entries (one per finished sum) are lane-interleaved too.
+    // Lane-balanced schedules (see pj_model.cu). Records are lane-interleaved (chunk offset +
+    // 32 t + lane is the lane's t-th item). Species gather (8 bytes) and column sums (16 bytes):
+    // x = index (24 bits) | coefficient code (7 bits) << 24 | end-of-sum flag (bit 31), y = the
+    // destination of the sum the item ends, z = the item's reaction (column sums). Rows and C_k
+    // (16 bytes): x = index | first-item flag (bit 30) | end flag (bit 31), y = the sum's
+    // destination, z, w = the item's coefficient (scale times nu) as a double.
     int rpc, n_row_chunks;    // rows per staged chunk, chunks covering the N+1 rows
     int ng, nh, ncc;          // chunks of the species-gather, column-sum and C_k schedules
     int ngp, nhp;             // pieces of the species-gather and column-sum lists (partial sums)
     const int *g_pfirst, *h_pfirst;   // per species / column: first piece (N + 1 entries)
-    const unsigned *s_items, *g_items, *h_items, *c_items;
-    const int *h_aux;         // reaction of each column-sum item
-    const int *s_chunk, *g_chunk, *h_chunk, *c_chunk;   // per chunk: item offset, length, entry offset
-    const int *s_dst, *g_dst, *h_dst, *c_dst;
-    const double *s_scale, *c_scale;
+    const uint2 *g_rec;               // species gather
+    const uint4 *h_rec, *c_rec, *s_rec;   // column sums, C_k, sparse rows
+    const int2 *g_chunk, *h_chunk, *c_chunk, *s_chunk;   // per chunk: record offset, rows
     const MathTables *tables;  // exp/log tables (pj_fastmath.cuh)
 };
 
@@ -161,9 +162,8 @@ struct HostImage {
     // lane-balanced schedules
     int rpc = 1, n_row_chunks = 0, ng = 0, nh = 0, ncc = 0, ngp = 0, nhp = 0;
     std::vector<int> g_pfirst, h_pfirst;
-    std::vector<unsigned> s_items, g_items, h_items, c_items;
-    std::vector<int> h_aux, s_chunk, g_chunk, h_chunk, c_chunk, s_dst, g_dst, h_dst, c_dst;
-    std::vector<double> s_scale, c_scale;
+    std::vector<uint32_t> g_rec, h_rec, c_rec, s_rec;       // 2, 4, 4, 4 words per record
+    std::vector<int> g_chunk, h_chunk, c_chunk, s_chunk;   // (record offset, rows) per chunk
 };
 
 constexpr int kNuBias = 64;          // coefficient code = nu + kNuBias (7 bits)

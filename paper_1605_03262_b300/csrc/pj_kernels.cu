@@ -81,26 +81,81 @@ __device__ __forceinline__ double sel4(const double (&v)[kMaxSlots], int i) {
     return i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : v[3];
 }
 
-// Runs f(item, aux) over one lane's items of a schedule chunk (lane-interleaved, stride 32),
-// issuing the item loads of kSchedBatch iterations together so that their latency overlaps.
-constexpr int kSchedBatch = 8;
+// A warp's walk over chunks c0, c0 + step, ... of one schedule. Each lane takes its records of a
+// chunk in order, B rows at a time, with the rows after the current batch in flight while it runs
+// (with FIRST, the next chunk's first rows are requested when a chunk starts, before pre). With
+// OPS the shared-memory operands of a whole batch are read (load) before any of its sums is stored
+// (use), so those loads overlap instead of waiting on the stores; it costs registers, which the
+// gathers (between the reaction stage and the combine) do not have to spare. pre(c) and post(c)
+// run around chunk c.
+template <int B, class R>
+__device__ __forceinline__ void load_recs(R (&r)[B], const R *base, int x0, int len) {
+#pragma unroll
+    for (int u = 0; u < B; ++u) r[u] = (x0 + u < len) ? __ldg(base + 32 * (x0 + u)) : R{};
+}
 
-template <bool AUX, class F>
-__device__ __forceinline__ void run_items(const unsigned *it, const int *ax, int len, F &&f) {
-    for (int x0 = 0; x0 < len; x0 += kSchedBatch) {
-        unsigned v[kSchedBatch];
-        int a[kSchedBatch];
+template <int B, bool FIRST, bool OPS, class R, class Pre, class Load, class Use, class Post>
+__device__ __forceinline__ void walk(const int2 *tab, int n, int c0, int step, const R *recs, int lane, Pre &&pre,
+                                     Load &&load, Use &&use, Post &&post) {
+    if (c0 >= n) return;
+    int2 h = __ldg(tab + c0);
+    int2 hn = (c0 + step < n) ? __ldg(tab + c0 + step) : make_int2(0, 0);
+    R cur[B];
+    load_recs<B>(cur, recs + h.x + lane, 0, h.y);
+    for (int c = c0; c < n; c += step) {
+        const int2 hnn = (c + 2 * step < n) ? __ldg(tab + c + 2 * step) : make_int2(0, 0);
+        R first[FIRST ? B : 1];
+        if constexpr (FIRST) load_recs<B>(first, recs + hn.x + lane, 0, hn.y);
+        pre(c);
+        for (int x0 = 0; x0 < h.y; x0 += B) {
+            R nxt[B];
+            if (FIRST || x0 + B < h.y) load_recs<B>(nxt, recs + h.x + lane, x0 + B, h.y);
+            else load_recs<B>(nxt, recs + hn.x + lane, 0, hn.y);      // next chunk's first rows
+            if (x0 + B <= h.y) {                      // a full batch: no predicated arithmetic
+                if constexpr (OPS) {
+                    decltype(load(cur[0])) ops[B];
 #pragma unroll
-        for (int u = 0; u < kSchedBatch; ++u) {
-            v[u] = (x0 + u < len) ? __ldg(it + 32 * (x0 + u)) : 0u;
-            if constexpr (AUX) a[u] = (x0 + u < len) ? __ldg(ax + 32 * (x0 + u)) : 0;
-            else a[u] = 0;
+                    for (int u = 0; u < B; ++u) ops[u] = load(cur[u]);
+#pragma unroll
+                    for (int u = 0; u < B; ++u) use(cur[u], ops[u]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < B; ++u) use(cur[u], load(cur[u]));
+                }
+            } else {
+                // the chunk's last, partial batch: a loop over the remaining items (the window
+                // shifts down), so that no FP64 instruction of a missing item is issued with every
+                // lane predicated off; those would take FP64 pipe time like real ones
+#pragma unroll 1
+                for (int rem = h.y - x0; rem > 0; --rem) {
+                    use(cur[0], load(cur[0]));
+#pragma unroll
+                    for (int u = 0; u + 1 < B; ++u) cur[u] = cur[u + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) cur[u] = nxt[u];
         }
+        post(c);
+        if constexpr (FIRST) {
 #pragma unroll
-        for (int u = 0; u < kSchedBatch; ++u)
-            if (x0 + u < len) f(v[u], a[u]);
+            for (int u = 0; u < B; ++u) cur[u] = first[u];
+        } else if (h.y == 0) {
+            load_recs<B>(cur, recs + hn.x + lane, 0, hn.y);
+        }
+        h = hn;
+        hn = hnn;
     }
 }
+
+__device__ __forceinline__ void no_op(int) {}
+
+constexpr int GB = 8, HB = 4, SB = 4;
+constexpr unsigned kFirstItem = 0x40000000u;   // first item of a sum (coefficient records)   // record rows per batch: species gather, column sums and C_k, rows
+
+struct Ops4 {
+    double nu, q, th, a;
+};
 
 struct StateScalars {
     double T, invT, lnT, P, lnP, W, rho, Ctot;
@@ -547,21 +602,17 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
 
     const double invrho = 1.0 / s.rho;
     if constexpr (!JAC) {
-        for (int c = wg; c < m.ng; c += NW) {       // omega_k through the species-gather schedule
-            const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
-            const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-            int p_next = __ldg(dst);
-            double w = 0.0;
-            run_items<false>(m.g_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
-                w = fma(sNu[(v >> 24) & 127], sq[v & 0xffffff], w);
-                if (v >> 31) {
-                    spart[p_next] = w;
-                    w = 0.0;
-                    dst += 32;
-                    p_next = __ldg(dst);
-                }
-            });
-        }
+        double w = 0.0;                                 // omega_k through the species-gather schedule
+        walk<GB, false, false>(m.g_chunk, m.ng, wg, NW, m.g_rec, lane, no_op,
+             [&](const uint2 &r) { return make_double2(sNu[(r.x >> 24) & 127], sq[r.x & 0xffffff]); },
+             [&](const uint2 &r, const double2 &o) {
+                 w = fma(o.x, o.y, w);
+                 if (r.x >> 31) {
+                     spart[r.y] = w;
+                     w = 0.0;
+                 }
+             },
+             no_op);
         group_sync<WPS>(g);
         for (int k = t; k < N; k += G) {                // each species: its pieces' partials, in order
             double w = 0.0;
@@ -579,62 +630,53 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         return;
     } else {
         // ---- gather stage: lane-balanced schedules (each sum is one lane's, in list order) ----
-        for (int c = wg; c < m.ng; c += NW) {       // omega_k, J_k0, A_k
-            const int ioff = __ldg(m.g_chunk + 3 * c), len = __ldg(m.g_chunk + 3 * c + 1);
-            const int *dst = m.g_dst + __ldg(m.g_chunk + 3 * c + 2) + lane;
-            int k_next = __ldg(dst);
+        {                                               // omega_k, J_k0, A_k
             double wq = 0.0, wt = 0.0, wa = 0.0;
-            run_items<false>(m.g_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
-                const int i = v & 0xffffff;
-                const double nu = sNu[(v >> 24) & 127];
-                wq = fma(nu, sq[i], wq);
-                wt = fma(nu, sth[i], wt);
-                wa = fma(nu, sa[i], wa);
-                if (v >> 31) {
-                    double *pp = spart + 3 * k_next;   // k_next: this piece's partial slot
-                    pp[0] = wq;
-                    pp[1] = wt;
-                    pp[2] = wa;
-                    wq = wt = wa = 0.0;
-                    dst += 32;
-                    k_next = __ldg(dst);
-                }
-            });
+            walk<GB, false, false>(m.g_chunk, m.ng, wg, NW, m.g_rec, lane, no_op,
+                 [&](const uint2 &r) {
+                     const int i = r.x & 0xffffff;
+                     return Ops4{sNu[(r.x >> 24) & 127], sq[i], sth[i], sa[i]};
+                 },
+                 [&](const uint2 &r, const Ops4 &o) {
+                     wq = fma(o.nu, o.q, wq);
+                     wt = fma(o.nu, o.th, wt);
+                     wa = fma(o.nu, o.a, wa);
+                     if (r.x >> 31) {
+                         double *pp = spart + 3 * r.y;   // this piece's partial slot
+                         pp[0] = wq;
+                         pp[1] = wt;
+                         pp[2] = wa;
+                         wq = wt = wa = 0.0;
+                     }
+                 },
+                 no_op);
         }
-        for (int c = wg; c < m.nh; c += NW) {       // HS_j = (1/W_j) sum_i dH_i b'_ij
-            const int ioff = __ldg(m.h_chunk + 3 * c), len = __ldg(m.h_chunk + 3 * c + 1);
-            const int *dst = m.h_dst + __ldg(m.h_chunk + 3 * c + 2) + lane;
-            int j_next = __ldg(dst);
+        {                                               // HS_j = (1/W_j) sum_i dH_i b'_ij
             double acc = 0.0;
-            run_items<true>(m.h_items + ioff + lane, m.h_aux + ioff + lane, len, [&](unsigned v, int rxn) {
-                acc = fma(sdH[rxn], sb[v & 0xffffff], acc);
-                if (v >> 31) {
-                    spart[3 * m.ngp + j_next] = acc;
-                    acc = 0.0;
-                    dst += 32;
-                    j_next = __ldg(dst);
-                }
-            });
+            double *hpart = spart + 3 * m.ngp;
+            walk<HB, false, false>(m.h_chunk, m.nh, wg, NW, m.h_rec, lane, no_op,
+                 [&](const uint4 &r) { return make_double2(sdH[r.z], sb[r.x & 0xffffff]); },
+                 [&](const uint4 &r, const double2 &o) {
+                     acc = fma(o.x, o.y, acc);
+                     if (r.x >> 31) {
+                         hpart[r.y] = acc;
+                         acc = 0.0;
+                     }
+                 },
+                 no_op);
         }
-        for (int c = wg; c < m.ncc; c += NW) {      // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
-            const int ioff = __ldg(m.c_chunk + 3 * c), len = __ldg(m.c_chunk + 3 * c + 1);
-            const int eoff = __ldg(m.c_chunk + 3 * c + 2) + lane;
-            const int *dst = m.c_dst + eoff;
-            const double *scl = m.c_scale + eoff;
-            int k_next = __ldg(dst);
-            double s_next = __ldg(scl);
-            double acc = 0.0;
-            run_items<false>(m.c_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
-                acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
-                if (v >> 31) {
-                    sCk[k_next] = -s_next * acc;
-                    acc = 0.0;
-                    dst += 32;
-                    scl += 32;
-                    k_next = __ldg(dst);
-                    s_next = __ldg(scl);
-                }
-            });
+        {                                               // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
+            double acc = 0.0;                           // (coefficients -(W_k/W_N) nu_ki in the records)
+            walk<HB, false, false>(m.c_chunk, m.ncc, wg, NW, m.c_rec, lane, no_op,
+                 [&](const uint4 &r) { return sb[r.x & 0xffffff]; },
+                 [&](const uint4 &r, double b) {
+                     acc = fma(__hiloint2double(int(r.w), int(r.z)), b, acc);
+                     if (r.x >> 31) {
+                         sCk[r.y] = acc;
+                         acc = 0.0;
+                     }
+                 },
+                 no_op);
         }
         group_sync<WPS>(g);
         // combine: each species / column sums its pieces' partials, in order
@@ -701,54 +743,74 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         const int ld = N + 1, RPC = m.rpc;
         double *stage = S + sc.rows + wg * RPC * ld;
         double *Jout = io.jac + st * io.ldj;
-        for (int c = wg; c < m.n_row_chunks; c += NW) {
-            const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
-            {
-                int rr = 0, j = lane;                  // (row in chunk, column) of element x
-                while (j >= ld) {
-                    j -= ld;
-                    ++rr;
-                }
-                for (int x = lane; x < nel; x += 32) {
-                    const int r = r0 + rr;
-                    double v;
-                    if (j == 0) v = (r == 0) ? J00 : sJk0[r - 1];
-                    else if (j == N) v = 0.0;
-                    else if (r == 0) v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
-                    else v = fma(sA[r - 1], sDelta[j - 1], sCk[r - 1]);
-                    stage[x] = v;
-                    j += 32;
-                    while (j >= ld) {
-                        j -= ld;
-                        ++rr;
-                    }
-                }
-            }
-            __syncwarp();
-            {
-                const int ioff = __ldg(m.s_chunk + 3 * c), len = __ldg(m.s_chunk + 3 * c + 1);
-                const int eoff = __ldg(m.s_chunk + 3 * c + 2) + lane;
-                const int *dst = m.s_dst + eoff;
-                const double *scl = m.s_scale + eoff;
-                int d_next = __ldg(dst);
-                double s_next = __ldg(scl);
-                double acc = 0.0;
-                run_items<false>(m.s_items + ioff + lane, nullptr, len, [&](unsigned v, int) {
-                    acc = fma(sNu[(v >> 24) & 127], sb[v & 0xffffff], acc);
-                    if (v >> 31) {
-                        stage[d_next] = fma(s_next, acc, stage[d_next]);
-                        acc = 0.0;
-                        dst += 32;
-                        scl += 32;
-                        d_next = __ldg(dst);
-                        s_next = __ldg(scl);
-                    }
-                });
-            }
-            __syncwarp();
-            store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
-            __syncwarp();
-        }
+        constexpr int kDense = 4;
+        double acc = 0.0;
+        walk<SB, true, true>(m.s_chunk, m.n_row_chunks, wg, NW, m.s_rec, lane,
+             [&](int c) {                               // dense part of chunk c
+                 const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+                 int x0 = lane;
+                 if (r0 == 0) {                         // energy row: its own loop, so that the
+                     for (int j = lane; j < ld; j += 32) {   // species rows carry no FP64 work of it
+                         double v;
+                         if (j == 0) v = J00;
+                         else if (j == N) v = 0.0;
+                         else v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
+                         stage[j] = v;
+                     }
+                     x0 += ld;
+                 }
+                 int rr = 0, j = x0;                    // (row in chunk, column) of element x
+                 while (j >= ld) {
+                     j -= ld;
+                     ++rr;
+                 }
+                 auto value = [&](int rr_, int j_) {    // species row r0 + rr_ >= 1
+                     const int k = r0 + rr_ - 1;
+                     const double d = (j_ == 0 || j_ == N) ? 0.0 : sDelta[j_ - 1];
+                     return (j_ == 0) ? sJk0[k] : (j_ == N) ? 0.0 : fma(sA[k], d, sCk[k]);
+                 };
+                 auto step = [&]() {
+                     j += 32;
+                     while (j >= ld) {
+                         j -= ld;
+                         ++rr;
+                     }
+                 };
+                 // full batches of kDense elements per lane (loads first, then stores), then the
+                 // tail one element at a time: no position is issued with every lane predicated off
+                 for (; x0 - lane + 32 * kDense <= nel; x0 += 32 * kDense) {
+                     double v[kDense];
+#pragma unroll
+                     for (int u = 0; u < kDense; ++u) {
+                         v[u] = value(rr, j);
+                         step();
+                     }
+#pragma unroll
+                     for (int u = 0; u < kDense; ++u) stage[x0 + 32 * u] = v[u];
+                 }
+                 for (; x0 < nel; x0 += 32) {
+                     stage[x0] = value(rr, j);
+                     step();
+                 }
+                 __syncwarp();
+             },
+             // sparse part: the chunk's lane-balanced schedule. An entry's sum starts from its dense
+             // value (read at the entry's first item) and adds (W_k/W_j) nu_ki b'_ij item by item
+             // (coefficients in the records), so finishing an entry is a plain store
+             [&](const uint4 &r) {
+                 return make_double2(sb[r.x & 0xffffff], (r.x & kFirstItem) ? stage[r.y] : 0.0);
+             },
+             [&](const uint4 &r, const double2 &o) {
+                 acc = (r.x & kFirstItem) ? o.y : acc;
+                 acc = fma(__hiloint2double(int(r.w), int(r.z)), o.x, acc);
+                 if (r.x >> 31) stage[r.y] = acc;
+             },
+             [&](int c) {                               // 16-byte streaming stores of the finished rows
+                 const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+                 __syncwarp();
+                 store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
+                 __syncwarp();
+             });
         if (io.dydt) {
             double *out = io.dydt + st * io.ldd;
             for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -Hf * invcp : sf[k - 1];

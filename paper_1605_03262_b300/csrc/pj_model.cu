@@ -201,13 +201,23 @@ struct Task {
     double scale = 0.0;
 };
 
+// Record layouts of the lane-balanced schedules.
+enum RecMode {
+    kRecPlain = 0,   // 2 words: item word (index | code << 24 | end << 31), destination on the last item
+    kRecAux = 1,     // 4 words: item word, destination on the last item, aux value, 0
+    kRecCoef = 2,    // 4 words: index | first << 30 | end << 31, destination on every item, and the
+                     // item's coefficient scale * nu as a double (the task's scale folded in)
+};
+
 // Lays out one chunk of tasks over the 32 lanes of a warp. Tasks are packed largest first onto
 // the least-loaded lane (longest-processing-time rule); each lane's items run back to back with an
 // end flag on the last item of every task; shorter lanes are padded with neutral items. Which lane
 // evaluates a task does not change its value: a task is always summed by one lane, in item order.
-void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code, int pad_aux,
-                std::vector<unsigned> &items, std::vector<int> *aux, std::vector<int> &dst,
-                std::vector<double> *scale, std::vector<int> &chunk) {
+// Records are lane-interleaved (record ioff + 32 t + lane is the lane's t-th item). The chunk table
+// gets (ioff, rows).
+void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code, int pad_aux, RecMode mode,
+                std::vector<uint32_t> &recs, std::vector<int> &chunk) {
+    const int words = mode == kRecPlain ? 2 : 4;
     std::stable_sort(tasks.begin(), tasks.end(),
                      [](const Task *a, const Task *b) { return a->idx.size() > b->idx.size(); });
     std::vector<std::vector<const Task *>> lane(32);
@@ -219,33 +229,39 @@ void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code,
         lane[best].push_back(t);
         load[best] += t->idx.size();
     }
-    size_t len = 0, ents = 0;
-    for (int l = 0; l < 32; ++l) {
-        len = std::max(len, load[l]);
-        ents = std::max(ents, lane[l].size());
+    size_t len = 0;
+    for (int l = 0; l < 32; ++l) len = std::max(len, load[l]);
+    const size_t ioff = recs.size() / words;
+    recs.resize((ioff + len * 32) * words, 0u);
+    for (size_t x = ioff; x < ioff + len * 32; ++x) {           // neutral items (coefficient 0)
+        recs[x * words] = mode == kRecCoef ? pad_idx : pad_idx | (unsigned(pad_code) << 24);
+        if (mode == kRecAux) recs[x * words + 2] = uint32_t(pad_aux);
     }
-    const size_t ioff = items.size(), eoff = dst.size();
-    items.resize(ioff + len * 32, pad_idx | (unsigned(pad_code) << 24));
-    if (aux) aux->resize(ioff + len * 32, pad_aux);
-    dst.resize(eoff + ents * 32, 0);
-    if (scale) scale->resize(eoff + ents * 32, 0.0);
     for (int l = 0; l < 32; ++l) {
-        size_t pos = 0, m = 0;
+        size_t pos = 0;
         for (const Task *t : lane[l]) {
             for (size_t q = 0; q < t->idx.size(); ++q, ++pos) {
-                unsigned v = t->idx[q] | (unsigned(t->code[q]) << 24);
-                if (q + 1 == t->idx.size()) v |= 0x80000000u;
-                items[ioff + pos * 32 + l] = v;
-                if (aux) (*aux)[ioff + pos * 32 + l] = t->aux[q];
+                uint32_t *r = &recs[(ioff + pos * 32 + l) * words];
+                const bool last = q + 1 == t->idx.size();
+                const unsigned end = last ? 0x80000000u : 0u;
+                if (mode == kRecCoef) {
+                    r[0] = t->idx[q] | (q == 0 ? 0x40000000u : 0u) | end;
+                    r[1] = uint32_t(t->dst);
+                    const double coef = t->scale * double(t->code[q] - kNuBias);
+                    uint64_t bits;
+                    std::memcpy(&bits, &coef, 8);
+                    r[2] = uint32_t(bits);
+                    r[3] = uint32_t(bits >> 32);
+                } else {
+                    r[0] = t->idx[q] | (unsigned(t->code[q]) << 24) | end;
+                    r[1] = last ? uint32_t(t->dst) : 0u;
+                    if (mode == kRecAux) r[2] = uint32_t(t->aux[q]);
+                }
             }
-            dst[eoff + m * 32 + l] = t->dst;
-            if (scale) (*scale)[eoff + m * 32 + l] = t->scale;
-            ++m;
         }
     }
     chunk.push_back(int(ioff));
     chunk.push_back(int(len));
-    chunk.push_back(int(eoff));
 }
 
 // A task with no items still has to write its (zero) result: give it one neutral item.
@@ -565,7 +581,7 @@ HostImage build_image(const void *buf, size_t len) {
         auto pieces = cut_pieces(tasks, piece_length(tasks, nw), im.g_pfirst);
         im.ngp = int(pieces.size());
         auto chunks = split_chunks(pieces, nw);
-        for (auto &c : chunks) emit_chunk(c, zero_rxn, zero_code, 0, im.g_items, nullptr, im.g_dst, nullptr, im.g_chunk);
+        for (auto &c : chunks) emit_chunk(c, zero_rxn, zero_code, 0, kRecPlain, im.g_rec, im.g_chunk);
         im.ng = int(chunks.size());
     }
     // energy-row column sums HS_j from (b-slot, reaction)
@@ -585,7 +601,7 @@ HostImage build_image(const void *buf, size_t len) {
         im.nhp = int(pieces.size());
         auto chunks = split_chunks(pieces, nw);
         for (auto &c : chunks)
-            emit_chunk(c, zero_slot, zero_code, R, im.h_items, &im.h_aux, im.h_dst, nullptr, im.h_chunk);
+            emit_chunk(c, zero_slot, zero_code, R, kRecAux, im.h_rec, im.h_chunk);
         im.nh = int(chunks.size());
     }
     // C_k = -(W_k/W_N) sum nu_ki b'_iN, from the sparse entries of column N-1
@@ -595,7 +611,7 @@ HostImage build_image(const void *buf, size_t len) {
             tasks[k].dst = k;
             const int e = im.colN_nnz[k];
             if (e >= 0) {
-                tasks[k].scale = im.nnz_wr[e];
+                tasks[k].scale = -im.nnz_wr[e];   // C_k = -(W_k/W_N) sum ...
                 for (int c = im.nnz_cptr[e]; c < im.nnz_cptr[e + 1]; ++c) {
                     tasks[k].idx.push_back(unsigned(im.con_slot[c]));
                     tasks[k].code.push_back(nu_code(im.con_nu[c]));
@@ -606,7 +622,7 @@ HostImage build_image(const void *buf, size_t len) {
         }
         auto chunks = split_chunks(tasks);
         for (auto &c : chunks)
-            emit_chunk(c, zero_slot, zero_code, 0, im.c_items, nullptr, im.c_dst, &im.c_scale, im.c_chunk);
+            emit_chunk(c, zero_slot, zero_code, 0, kRecCoef, im.c_rec, im.c_chunk);
         im.ncc = int(chunks.size());
     }
     // sparse block, per chunk of rpc staged rows (row r = species r-1, row 0 = energy row)
@@ -634,12 +650,9 @@ HostImage build_image(const void *buf, size_t len) {
             }
             std::vector<const Task *> ptrs;
             for (auto &t : tasks) ptrs.push_back(&t);
-            emit_chunk(ptrs, zero_slot, zero_code, 0, im.s_items, nullptr, im.s_dst, &im.s_scale, im.s_chunk);
+            emit_chunk(ptrs, zero_slot, zero_code, 0, kRecCoef, im.s_rec, im.s_chunk);
         }
     }
-    // one row of padding after the last chunk's entries: a lane prefetches its next entry record
-    for (auto *v : {&im.g_dst, &im.h_dst, &im.c_dst, &im.s_dst}) v->insert(v->end(), 32, 0);
-    for (auto *v : {&im.c_scale, &im.s_scale}) v->insert(v->end(), 32, 0.0);
     return im;
 }
 
