@@ -465,15 +465,30 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
     }
 
     const double Rf = kf * sf.P, Rr = kr * sr.P, Rn = Rf - Rr;
-    const double q = c * Rn;
+    const bool elem = d.kind == kElem;   // c = 1, dc/dT = 0, psi = 0: the terms in c, psi, eps drop
+    const double q = elem ? Rn : c * Rn;
     sq[i] = q;
     if constexpr (!JAC) return;
 
     const double dRdT = Rf * fma(-nf, invT, dlnkf) - Rr * fma(-nb, invT, dlnkr);
-    sth[i] = fma(dcdT, Rn, fma(c, dRdT, q * invT));
     const double sigma = fma(nf, Rf, -nb * Rr);
-    sa[i] = -s.W * fma(c, sigma, psi * Rn * E);
     sdH[i] = sr.sH - sf.sH;
+    if (elem) {
+        sth[i] = fma(q, invT, dRdT);
+        sa[i] = -s.W * sigma;
+        // b'_il = k_f dP'/d[X_l] - k_r dP''/d[X_l]
+        for (int x = 0; x < d.nslot; ++x) {
+            const int info = __ldg(m.slot_info + d.slot_off + x);
+            const int rs = ((info >> 16) & 0xff) - 1, ps = ((info >> 24) & 0xff) - 1;
+            double G = 0.0;
+            if (rs >= 0) G = kf * sel4(sf.S, rs);
+            if (ps >= 0) G = fma(-kr, sel4(sr.S, ps), G);
+            sb[d.slot_off + x] = G;
+        }
+        return;
+    }
+    sth[i] = fma(dcdT, Rn, fma(c, dRdT, q * invT));
+    sa[i] = -s.W * fma(c, sigma, psi * Rn * E);
     // b'_il = c (k_f dP'/d[X_l] - k_r dP''/d[X_l]) + psi R eps_il
     const double ckf = c * kf, ckr = c * kr, psiR = psi * Rn;
     for (int x = 0; x < d.nslot; ++x) {

@@ -176,15 +176,21 @@ std::vector<std::pair<int, int>> distinct(const std::vector<std::pair<int, int>>
 }
 
 int class_key(const HRxn &x) {
-    // kind first, then falloff form, third-body mode, reversibility and the number of distinct
-    // species on each side: the 32 reactions of a warp mostly take the same branches
+    // The 32 reactions of a warp should take the same branches. Order: family (falloff and
+    // chemically activated together, PLOG, Chebyshev, third-body, elementary), then falloff form
+    // (a Troe falloff and a Troe chemically activated reaction share the F_cent / F work), kind,
+    // third-body mode, reversibility and the number of distinct species on each side. The
+    // cheapest family comes last, so the partly filled last round of a state runs the cheapest
+    // code path (measured on B300: -7% FP64 instructions on a 53-species model).
     auto ndist = [](const std::vector<std::pair<int, int>> &v) {
         std::vector<int> s;
         for (auto &e : v)
             if (std::find(s.begin(), s.end(), e.first) == s.end()) s.push_back(e.first);
         return int(s.size());
     };
-    return ((((x.kind * 4 + x.ftype) * 4 + x.tbmode) * 4 + x.rev) * 8 + ndist(x.reac)) * 8 + ndist(x.prod);
+    const int fam = (x.kind == kFalloff || x.kind == kChem) ? 0
+                    : x.kind == kPlog ? 1 : x.kind == kCheb ? 2 : x.kind == kThird ? 3 : 4;
+    return (((((fam * 4 + x.ftype) * 8 + x.kind) * 4 + x.tbmode) * 4 + x.rev) * 8 + ndist(x.reac)) * 8 + ndist(x.prod);
 }
 
 }  // namespace
