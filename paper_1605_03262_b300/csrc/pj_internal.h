@@ -91,7 +91,7 @@ struct DevModel {
 
 // Offsets (in doubles) of one state's scratch in shared memory.
 struct Scratch {
-    int C, B, dB, H, cpk, Jk0, A, Ck, f, HS, red, q, th, a, dH, b, rows, part, total;
+    int C, B, dB, H, cpk, Jk0, A, Ck, f, HS, red, scal, q, th, a, dH, b, rows, part, total;
     int rows_per_chunk;       // rows staged per warp chunk
 };
 

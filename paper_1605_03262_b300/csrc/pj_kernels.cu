@@ -25,8 +25,10 @@
 // block is written at one FMA per entry plus the reaction-local sparse terms (row stage).
 //
 // Parallel layout: a "group" of WPS warps evaluates one state at a time; a CTA holds several
-// groups and loops persistently over states. All of a state's intermediates live in shared
-// memory. Reductions over species use a fixed 32-lane order that every warp repeats, so the
+// groups and loops persistently over rounds of states, one per group. The reaction stage of a
+// round runs over the whole CTA, transposed (reaction-major, state-minor), so that small reaction
+// classes still fill warps with one code path. All of a state's intermediates live in shared
+// memory. Every sum has a fixed order (32-lane reductions, one lane per schedule entry), so the
 // result of a state is bitwise independent of the launch shape.
 #include <algorithm>
 #include <cstdint>
@@ -150,8 +152,8 @@ __device__ __forceinline__ void walk(const int2 *tab, int n, int c0, int step, c
 
 __device__ __forceinline__ void no_op(int) {}
 
-constexpr int GB = 8, HB = 4, SB = 4;
-constexpr unsigned kFirstItem = 0x40000000u;   // first item of a sum (coefficient records)   // record rows per batch: species gather, column sums and C_k, rows
+constexpr int GB = 8, HB = 4, SB = 4;           // record rows per batch: species gather, column sums and C_k, rows
+constexpr unsigned kFirstItem = 0x40000000u;    // first item of a sum (coefficient records)
 
 struct Ops4 {
     double nu, q, th, a;
@@ -545,18 +547,23 @@ __device__ __forceinline__ void init_neutral(const DevModel &m, const Scratch &s
 }
 
 // One state, evaluated by one group: state prep, thermodynamics, reaction stage, gathers and rows.
+// State scalars that the stages after the state prep use.
+struct Prep {
+    StateScalars s;
+    double cp, dcpdT;
+};
+
+// State prep and thermodynamics (Sections 2.1-2.2): Y, c_p,k, H_k, B_k (and derivatives) of every
+// species, the mixture sums, and the concentrations. Ends with the group synchronised.
 template <bool JAC, int WPS>
-__device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
+__device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
                                            const StateIO &io, long long st, const Grp &g) {
-    const int N = m.N, R = m.R;
+    const int N = m.N;
     const int G = WPS ? WPS * 32 : g.G, NW = WPS ? WPS : g.wps;
     const int t = g.t, lane = g.lane, wg = g.wg;
-    const double *sNu = smem_const, *sDelta = smem_const + 128, *sInvW = smem_const + 128 + N;
+    const double *sInvW = smem_const + 128 + N;
     double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
-    double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
-    double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
-    double *spart = S + sc.part, *sred = S + sc.red;
-    (void)sHS;
+    double *sJk0 = S + sc.Jk0, *sf = S + sc.f, *sred = S + sc.red;
     // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
     StateScalars s;
     s.T = __ldg(io.T + st);
@@ -610,10 +617,52 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     s.lnP = fast_log(s.P, m.tables);
     for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
     group_sync<WPS>(g);
+    return Prep{s, cp, dcpdT};
+}
 
-    // ---- reaction stage ----
-    for (int i = t; i < R; i += G) reaction<JAC>(m, i, s, sC, sB, sdB, sH, sNu, sq, sth, sa, sdH, sb);
-    group_sync<WPS>(g);
+// One round of a CTA: each group evaluates one state (prep, gathers, rows), and the reaction stage
+// of the round's states runs over the whole CTA. All threads of the CTA call this together.
+// active = false: a thread without a state in this round (a group past the last state, or a
+// thread outside the model's groups), which takes part in the reaction stage only. gact groups
+// have states; group gg's scratch is S0 + gg * stride.
+template <bool JAC, int WPS>
+__device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
+                                           const StateIO &io, long long st, const Grp &g, bool active, int gact,
+                                           double *S0, int stride) {
+    const int N = m.N, R = m.R;
+    const int G = WPS ? WPS * 32 : g.G, NW = WPS ? WPS : g.wps;
+    const int t = g.t, lane = g.lane, wg = g.wg;
+    const double *sNu = smem_const, *sDelta = smem_const + 128, *sInvW = smem_const + 128 + N;
+    double *sH = S + sc.H, *scp = S + sc.cpk;
+    double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck, *sf = S + sc.f, *sHS = S + sc.HS;
+    double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
+    double *spart = S + sc.part;
+    (void)sHS;
+    Prep pp{};
+    if (active) pp = state_prep<JAC, WPS>(m, sc, S, smem_const, io, st, g);
+    const StateScalars s = pp.s;
+    const double cp = pp.cp, dcpdT = pp.dcpdT;
+    double *sred = S + sc.red;
+    // ---- reaction stage, all of the round's states together ----
+    // Item k = (reaction i, group gg), reactions in code-path order and groups fastest: a warp's
+    // lanes run a few reactions for several states, so a warp mostly takes one code path even for
+    // small reaction classes. The arithmetic of a reaction does not depend on who evaluates it.
+    if (active && t == 0) {
+        double *o = S + sc.scal;
+        o[0] = s.T, o[1] = s.invT, o[2] = s.lnT, o[3] = s.P, o[4] = s.lnP, o[5] = s.W, o[6] = s.rho, o[7] = s.Ctot;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < R * gact; k += blockDim.x) {
+        const int i = k / gact, gg = k - i * gact;
+        double *Sg = S0 + size_t(gg) * stride;
+        const double *v = Sg + sc.scal;
+        StateScalars sg;
+        sg.T = v[0], sg.invT = v[1], sg.lnT = v[2], sg.P = v[3], sg.lnP = v[4], sg.W = v[5], sg.rho = v[6], sg.Ctot = v[7];
+        reaction<JAC>(m, i, sg, Sg + sc.C, Sg + sc.B, Sg + sc.dB, Sg + sc.H, sNu, Sg + sc.q, Sg + sc.th, Sg + sc.a,
+                      Sg + sc.dH, Sg + sc.b);
+    }
+    __syncthreads();
+    if (!active) return;
 
     const double invrho = 1.0 / s.rho;
     if constexpr (!JAC) {
@@ -850,8 +899,25 @@ __global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__
     init_neutral<JAC>(m, p.sc, S, g.t);
     __syncthreads();
     const StateIO io{p.T, p.P, p.Y, p.ldy, p.jac, p.ldj, p.dydt, p.ldd};
-    for (long long st = (long long)blockIdx.x * p.groups + g.grp; st < p.n; st += (long long)gridDim.x * p.groups)
-        eval_state<JAC, WPS>(m, p.sc, S, smem, io, st, g);
+    double *S0 = smem + p.shared_const;
+    for (long long base = (long long)blockIdx.x * p.groups; base < p.n; base += (long long)gridDim.x * p.groups) {
+        const long long st = base + g.grp;
+        const int gact = int(min((long long)p.groups, p.n - base));
+        eval_state<JAC, WPS>(m, p.sc, S, smem, io, st, g, st < p.n, gact, S0, p.sc.total);
+    }
+}
+
+// States [begin, end) of one tile of the batched form, in CTA rounds of it.groups states.
+template <bool JAC>
+__device__ __forceinline__ void run_tile(const DevModel &m, const BatchItem &it, double *smem, long long begin,
+                                         long long end, const Grp &g) {
+    double *S0 = smem + it.shared_const;
+    double *S = S0 + size_t(g.grp) * it.sc.total;   // used only by the model's groups
+    const bool member = g.grp < it.groups;
+    for (long long base = begin; base < end; base += it.groups) {
+        const int gact = int(min((long long)it.groups, end - base));
+        eval_state<JAC, 0>(m, it.sc, S, smem, it.io, base + g.grp, g, member && g.grp < gact, gact, S0, it.sc.total);
+    }
 }
 
 // Persistent kernel over tiles of states from several models (the batched form): each CTA takes
@@ -888,9 +954,7 @@ __global__ void __launch_bounds__(512, 1) pj_batch_kernel(const __grid_constant_
             cur = tl.item;
             __syncthreads();
         }
-        if (g.grp < it.groups)
-            for (long long st = tl.begin + g.grp; st < tl.begin + tl.count; st += it.groups)
-                eval_state<JAC, 0>(s_m, it.sc, S, smem, it.io, st, g);
+        run_tile<JAC>(s_m, it, smem, tl.begin, tl.begin + tl.count, g);
         __syncthreads();
     }
 }
@@ -913,6 +977,7 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
     sc.cpk = take(N);
     sc.f = take(N);
     sc.red = take(8);
+    sc.scal = take(8);
     sc.q = take(R + 1);
     if (jac) {
         sc.dB = take(N);
@@ -1051,8 +1116,7 @@ __global__ void __launch_bounds__(512, 1) pj_batch_noalloc_kernel(NoAllocScratch
             cur = item;
             __syncthreads();
         }
-        if (g.grp < it.groups)
-            for (long long st = begin + g.grp; st < end; st += it.groups) eval_state<JAC, 0>(s_m, it.sc, S, smem, it.io, st, g);
+        run_tile<JAC>(s_m, it, smem, begin, end, g);
         __syncthreads();
     }
 }
