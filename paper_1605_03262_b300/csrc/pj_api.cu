@@ -184,7 +184,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
            o_cns = push(blob, im.con_slot), o_cnn = push(blob, im.con_nu), o_cN = push(blob, im.colN_nnz);
     size_t o_gr = push(blob, im.g_rec), o_hr = push(blob, im.h_rec), o_cr2 = push(blob, im.c_rec),
            o_sr = push(blob, im.s_rec), o_sc = push(blob, im.s_chunk), o_gc = push(blob, im.g_chunk),
-           o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst);
+           o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk), o_scc = push(blob, im.s_comb_chunk),
+           o_scb = push(blob, im.s_comb), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst);
     pj::MathTables tables;
     pj::build_math_tables(tables);
     std::vector<pj::MathTables> tvec(1, tables);
@@ -261,6 +262,9 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.g_chunk = reinterpret_cast<const int2 *>(b + o_gc);
     d.h_chunk = reinterpret_cast<const int2 *>(b + o_hc);
     d.c_chunk = reinterpret_cast<const int2 *>(b + o_cc);
+    d.s_npart = im.s_npart;
+    d.s_comb_chunk = reinterpret_cast<const int2 *>(b + o_scc);
+    d.s_comb = reinterpret_cast<const int4 *>(b + o_scb);
     d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
     m->dev_model = reinterpret_cast<const pj::DevModel *>(b + o_dm);
     e = cudaMemcpy(b + o_dm, &d, sizeof(d), cudaMemcpyHostToDevice);

@@ -1,7 +1,8 @@
 // Batched form: one persistent launch over several (model, state batch) items of uneven size.
 //
 // pj_batch_create builds a plan once: per item the group width (the model's configured warps per
-// state) and the number of groups a CTA runs for it (limited by shared memory), and a tile list
+// state, halved while one state does not fit next to the kernel's own shared memory) and the
+// number of groups a CTA runs for it (limited by shared memory), and a tile list
 // (consecutive states of one item) ordered with the costliest tiles first. The plan's device
 // memory holds the item table, the tiles and a tile counter. pj_batch_run zeroes the counter and
 // launches the persistent kernel on the caller's stream; it allocates nothing and does not
@@ -91,16 +92,12 @@ int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj
             if (jac && (rc = check_dev(it.jac, dev, "jac"))) return rc;
             if ((!jac || it.dydt) && (rc = check_dev(it.dydt, dev, "dydt"))) return rc;
         }
-        int wps = (jac ? m->jac_cfg : m->dydt_cfg).wps;
-        while (wps * 32 > threads && wps > 1) wps /= 2;
-        const pj::Scratch sc = pj::make_scratch(m->dev, jac, wps);
-        const int sconst = pj::shared_const_doubles(m->N);
-        int groups = threads / (32 * wps);
-        if (wps > 1) groups = std::min(groups, 15);
-        while (groups > 0 && (size_t(sconst) + size_t(sc.total) * groups) * 8 > budget) --groups;
-        if (groups < 1)
+        int wps = 0, groups = 0;
+        pj::Scratch sc{};
+        if (!pj::batch_group_shape(*m, jac, threads, budget, &wps, &groups, &sc))
             return bfail(PJ_EUNSUPPORTED, "pj_batch_create: item " + std::to_string(i) +
                                               ": one state's working set does not fit in shared memory");
+        const int sconst = pj::shared_const_doubles(m->N);
         smem = std::max(smem, (size_t(sconst) + size_t(sc.total) * groups) * 8);
         pj::BatchItem &b = bi[i];
         b.m = m->dev_model;

@@ -86,8 +86,14 @@ struct DevModel {
     const uint2 *g_rec;               // species gather
     const uint4 *h_rec, *c_rec, *s_rec;   // column sums, C_k, sparse rows
     const int2 *g_chunk, *h_chunk, *c_chunk, *s_chunk;   // per chunk: record offset, rows
+    int s_npart;              // partial slots a warp needs for the split row entries of one chunk
+    const int2 *s_comb_chunk; // per row chunk: offset into s_comb, number of split entries
+    const int4 *s_comb;       // split row entry: staged position, first partial slot, partials, 0
     const MathTables *tables;  // exp/log tables (pj_fastmath.cuh)
 };
+
+// Doubles of one warp's row stage: rpc staged rows and the partial slots of split entries.
+__host__ __device__ inline int row_stride(const DevModel &m) { return (m.rpc * (m.N + 1) + m.s_npart + 1) & ~1; }
 
 // Offsets (in doubles) of one state's scratch in shared memory.
 struct Scratch {
@@ -164,6 +170,8 @@ struct HostImage {
     std::vector<int> g_pfirst, h_pfirst;
     std::vector<uint32_t> g_rec, h_rec, c_rec, s_rec;       // 2, 4, 4, 4 words per record
     std::vector<int> g_chunk, h_chunk, c_chunk, s_chunk;   // (record offset, rows) per chunk
+    int s_npart = 0;
+    std::vector<int> s_comb_chunk, s_comb;                 // (offset, count) per chunk; 4 ints per entry
 };
 
 constexpr int kNuBias = 64;          // coefficient code = nu + kNuBias (7 bits)
@@ -197,5 +205,12 @@ struct pj_mech {
     pj_host_staging *staging = nullptr;   // device buffers of pj_eval_jacobian_host (lazy)
     const pj::DevModel *dev_model = nullptr;   // device copy of dev (for batched plans)
 };
+
+namespace pj {
+// Group width, states per CTA and scratch of one model in a batched launch of `threads` threads
+// and `budget` bytes of dynamic shared memory per CTA: the model's configured width, halved while
+// it exceeds the CTA or while one state's working set does not fit. False if no width fits.
+bool batch_group_shape(const pj_mech &m, bool jac, int threads, size_t budget, int *wps, int *groups, Scratch *sc);
+}  // namespace pj
 
 void pj_host_staging_release(pj_mech *m);

@@ -154,6 +154,7 @@ __device__ __forceinline__ void no_op(int) {}
 
 constexpr int GB = 8, HB = 4, SB = 4;           // record rows per batch: species gather, column sums and C_k, rows
 constexpr unsigned kFirstItem = 0x40000000u;    // first item of a sum (coefficient records)
+constexpr unsigned kPartialItem = 0x20000000u;  // a later piece of a split row entry
 
 struct Ops4 {
     double nu, q, th, a;
@@ -805,13 +806,17 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
         //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
         const int ld = N + 1, RPC = m.rpc;
-        double *stage = S + sc.rows + wg * RPC * ld;
+        double *stage = S + sc.rows + wg * row_stride(m);
+        double *pbuf = stage + RPC * ld;          // partial sums of split entries
         double *Jout = io.jac + st * io.ldj;
         constexpr int kDense = 4;
         double acc = 0.0;
+        int2 comb = make_int2(0, 0);                 // this chunk's split-entry list
+        int4 crec = make_int4(0, 0, 0, 0);
         walk<SB, true, true>(m.s_chunk, m.n_row_chunks, wg, NW, m.s_rec, lane,
              [&](int c) {                               // dense part of chunk c
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+                 comb = __ldg(m.s_comb_chunk + c);     // split entries of this chunk
                  int x0 = lane;
                  if (r0 == 0) {                         // energy row: its own loop, so that the
                      for (int j = lane; j < ld; j += 32) {   // species rows carry no FP64 work of it
@@ -856,21 +861,31 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                      stage[x0] = value(rr, j);
                      step();
                  }
+                 crec = lane < comb.y ? __ldg(m.s_comb + comb.x + lane) : make_int4(0, 0, 0, 0);
                  __syncwarp();
              },
              // sparse part: the chunk's lane-balanced schedule. An entry's sum starts from its dense
              // value (read at the entry's first item) and adds (W_k/W_j) nu_ki b'_ij item by item
-             // (coefficients in the records), so finishing an entry is a plain store
+             // (coefficients in the records), so finishing an entry is a plain store. Later pieces
+             // of a split entry sum from zero into partial slots.
              [&](const uint4 &r) {
-                 return make_double2(sb[r.x & 0xffffff], (r.x & kFirstItem) ? stage[r.y] : 0.0);
+                 const bool from_dense = (r.x & (kFirstItem | kPartialItem)) == kFirstItem;
+                 return make_double2(sb[r.x & 0xffffff], from_dense ? stage[r.y] : 0.0);
              },
              [&](const uint4 &r, const double2 &o) {
                  acc = (r.x & kFirstItem) ? o.y : acc;
                  acc = fma(__hiloint2double(int(r.w), int(r.z)), o.x, acc);
-                 if (r.x >> 31) stage[r.y] = acc;
+                 if (r.x >> 31) ((r.x & kPartialItem) ? pbuf : stage)[r.y] = acc;
              },
              [&](int c) {                               // 16-byte streaming stores of the finished rows
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+                 __syncwarp();
+                 for (int e = lane; e < comb.y; e += 32) {   // split entries: add the partials in order
+                     const int4 cr = e == lane ? crec : __ldg(m.s_comb + comb.x + e);
+                     double v = stage[cr.x];
+                     for (int q = 0; q < cr.z; ++q) v += pbuf[cr.y + q];
+                     stage[cr.x] = v;
+                 }
                  __syncwarp();
                  store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
                  __syncwarp();
@@ -991,7 +1006,7 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
         sc.b = take(m.nslot + 1);
         sc.rows_per_chunk = m.rpc;
         // the row-staging buffers and the gather's partial sums are never live at the same time
-        sc.rows = take(std::max(wps * m.rpc * (N + 1), 3 * m.ngp + m.nhp));
+        sc.rows = take(std::max(wps * row_stride(m), 3 * m.ngp + m.nhp));
         sc.part = sc.rows;
     } else {
         sc.dB = sc.Jk0 = sc.A = sc.Ck = sc.HS = sc.th = sc.a = sc.dH = sc.b = sc.rows = 0;
@@ -1000,6 +1015,25 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
     }
     sc.total = o;
     return sc;
+}
+
+bool batch_group_shape(const pj_mech &m, bool jac, int threads, size_t budget, int *wps, int *groups, Scratch *sc) {
+    const int sconst = shared_const_doubles(m.N);
+    int w = (jac ? m.jac_cfg : m.dydt_cfg).wps;
+    while (w * 32 > threads && w > 1) w /= 2;
+    for (; w >= 1; w /= 2) {   // results do not depend on the width; narrower groups stage fewer rows
+        const Scratch s = make_scratch(m.dev, jac, w);
+        int g = threads / (32 * w);
+        if (w > 1) g = std::min(g, 15);
+        while (g > 0 && (size_t(sconst) + size_t(s.total) * g) * 8 > budget) --g;
+        if (g >= 1) {
+            *wps = w;
+            *groups = g;
+            *sc = s;
+            return true;
+        }
+    }
+    return false;
 }
 
 int shared_const_doubles(int N) { return 128 + (((2 * N) + 1) & ~1); }
@@ -1188,14 +1222,11 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const
             return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: leading dimension too small");
         if (x.n > 0 && (!x.T || !x.P || !x.Y || (jac && !x.jac) || (!jac && !x.dydt)))
             return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: null input or output pointer");
-        int wps = (jac ? m->jac_cfg : m->dydt_cfg).wps;
-        while (wps * 32 > threads && wps > 1) wps /= 2;
-        const Scratch sc = make_scratch(m->dev, jac, wps);
+        int wps = 0, groups = 0;
+        Scratch sc{};
+        if (!batch_group_shape(*m, jac, threads, budget, &wps, &groups, &sc))
+            return noalloc_fail(PJ_EUNSUPPORTED, "pj_batch_run_noalloc: state working set exceeds shared memory");
         const int sconst = shared_const_doubles(m->N);
-        int groups = threads / (32 * wps);
-        if (wps > 1) groups = std::min(groups, 15);
-        while (groups > 0 && (size_t(sconst) + size_t(sc.total) * groups) * 8 > budget) --groups;
-        if (groups < 1) return noalloc_fail(PJ_EUNSUPPORTED, "pj_batch_run_noalloc: state working set exceeds shared memory");
         smem = std::max(smem, (size_t(sconst) + size_t(sc.total) * groups) * 8);
         BatchItem &b = h.items[i];
         b.m = m->dev_model;

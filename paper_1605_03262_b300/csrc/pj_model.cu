@@ -205,14 +205,16 @@ struct Task {
     std::vector<int> aux;
     int dst = 0;
     double scale = 0.0;
+    bool partial = false;   // a later piece of a split row entry: sums from zero into partial slot dst
 };
 
 // Record layouts of the lane-balanced schedules.
 enum RecMode {
     kRecPlain = 0,   // 2 words: item word (index | code << 24 | end << 31), destination on the last item
     kRecAux = 1,     // 4 words: item word, destination on the last item, aux value, 0
-    kRecCoef = 2,    // 4 words: index | first << 30 | end << 31, destination on every item, and the
-                     // item's coefficient scale * nu as a double (the task's scale folded in)
+    kRecCoef = 2,    // 4 words: index | partial << 29 | first << 30 | end << 31, destination on every
+                     // item, and the item's coefficient scale * nu as a double (the task's scale
+                     // folded in)
 };
 
 // Lays out one chunk of tasks over the 32 lanes of a warp. Tasks are packed largest first onto
@@ -251,7 +253,7 @@ void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code,
                 const bool last = q + 1 == t->idx.size();
                 const unsigned end = last ? 0x80000000u : 0u;
                 if (mode == kRecCoef) {
-                    r[0] = t->idx[q] | (q == 0 ? 0x40000000u : 0u) | end;
+                    r[0] = t->idx[q] | (q == 0 ? 0x40000000u : 0u) | (t->partial ? 0x20000000u : 0u) | end;
                     r[1] = uint32_t(t->dst);
                     const double coef = t->scale * double(t->code[q] - kNuBias);
                     uint64_t bits;
@@ -631,13 +633,19 @@ HostImage build_image(const void *buf, size_t len) {
             emit_chunk(c, zero_slot, zero_code, 0, kRecCoef, im.c_rec, im.c_chunk);
         im.ncc = int(chunks.size());
     }
-    // sparse block, per chunk of rpc staged rows (row r = species r-1, row 0 = energy row)
+    // sparse block, per chunk of rpc staged rows (row r = species r-1, row 0 = energy row). A
+    // chunk's lanes are balanced only if no entry is much longer than the chunk's items / 32, so
+    // entries longer than that are cut into pieces: the first piece starts from the dense value
+    // and ends in the staged row as before; each later piece sums from zero into a partial slot of
+    // the warp, and a combine list adds an entry's partials to it in piece order.
     {
         im.rpc = std::max(1, std::min(4, 256 / (N + 1)));
         im.n_row_chunks = (N + 1 + im.rpc - 1) / im.rpc;
+        im.s_npart = 0;
         for (int c = 0; c < im.n_row_chunks; ++c) {
             const int r0 = c * im.rpc, r1 = std::min(r0 + im.rpc, N + 1);
             std::vector<Task> tasks;
+            size_t total = 0;
             for (int r = std::max(r0, 1); r < r1; ++r) {
                 const int k = r - 1;
                 for (int e = im.row_ptr[k]; e < im.row_ptr[k + 1]; ++e) {
@@ -651,13 +659,51 @@ HostImage build_image(const void *buf, size_t len) {
                         t.code.push_back(nu_code(im.con_nu[q]));
                         t.aux.push_back(0);
                     }
+                    total += t.idx.size();
                     tasks.push_back(std::move(t));
                 }
             }
+            const size_t plen = std::max<size_t>(2, (total + 31) / 32);
+            std::vector<Task> pieces;
+            int npart = 0;
+            const int coff = int(im.s_comb.size() / 4);
+            for (const Task &t : tasks) {
+                const size_t n = t.idx.size();
+                int first_part = -1, nparts = 0;
+                for (size_t b = 0; b < n; b += plen) {
+                    Task p;
+                    const size_t e = std::min(n, b + plen);
+                    for (size_t q = b; q < e; ++q) {
+                        p.idx.push_back(t.idx[q]);
+                        p.code.push_back(t.code[q]);
+                        p.aux.push_back(t.aux[q]);
+                    }
+                    p.scale = t.scale;
+                    if (b == 0) {
+                        p.dst = t.dst;
+                    } else {
+                        p.partial = true;
+                        p.dst = npart++;
+                        if (first_part < 0) first_part = p.dst;
+                        ++nparts;
+                    }
+                    pieces.push_back(std::move(p));
+                }
+                if (nparts > 0) {
+                    im.s_comb.push_back(t.dst);
+                    im.s_comb.push_back(first_part);
+                    im.s_comb.push_back(nparts);
+                    im.s_comb.push_back(0);
+                }
+            }
+            im.s_comb_chunk.push_back(coff);
+            im.s_comb_chunk.push_back(int(im.s_comb.size() / 4) - coff);
+            im.s_npart = std::max(im.s_npart, npart);
             std::vector<const Task *> ptrs;
-            for (auto &t : tasks) ptrs.push_back(&t);
+            for (auto &t : pieces) ptrs.push_back(&t);
             emit_chunk(ptrs, zero_slot, zero_code, 0, kRecCoef, im.s_rec, im.s_chunk);
         }
+        if (im.s_comb.empty()) im.s_comb.assign(4, 0);
     }
     return im;
 }
