@@ -185,7 +185,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     size_t o_gr = push(blob, im.g_rec), o_hr = push(blob, im.h_rec), o_cr2 = push(blob, im.c_rec),
            o_sr = push(blob, im.s_rec), o_sc = push(blob, im.s_chunk), o_gc = push(blob, im.g_chunk),
            o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk), o_scc = push(blob, im.s_comb_chunk),
-           o_scb = push(blob, im.s_comb), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst);
+           o_scb = push(blob, im.s_comb), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst),
+           o_cpf = push(blob, im.c_pfirst);
     pj::MathTables tables;
     pj::build_math_tables(tables);
     std::vector<pj::MathTables> tvec(1, tables);
@@ -252,6 +253,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.ncc = im.ncc;
     d.ngp = im.ngp;
     d.nhp = im.nhp;
+    d.ncp = im.ncp;
+    d.c_pfirst = reinterpret_cast<const int *>(b + o_cpf);
     d.g_pfirst = reinterpret_cast<const int *>(b + o_gpf);
     d.h_pfirst = reinterpret_cast<const int *>(b + o_hpf);
     d.g_rec = reinterpret_cast<const uint2 *>(b + o_gr);

@@ -81,8 +81,8 @@ struct DevModel {
     // destination, z, w = the item's coefficient (scale times nu) as a double.
     int rpc, n_row_chunks;    // rows per staged chunk, chunks covering the N+1 rows
     int ng, nh, ncc;          // chunks of the species-gather, column-sum and C_k schedules
-    int ngp, nhp;             // pieces of the species-gather and column-sum lists (partial sums)
-    const int *g_pfirst, *h_pfirst;   // per species / column: first piece (N + 1 entries)
+    int ngp, nhp, ncp;        // pieces of the species-gather, column-sum and C_k lists (partial sums)
+    const int *g_pfirst, *h_pfirst, *c_pfirst;   // per species / column: first piece (N + 1 entries)
     const uint2 *g_rec;               // species gather
     const uint4 *h_rec, *c_rec, *s_rec;   // column sums, C_k, sparse rows
     const int2 *g_chunk, *h_chunk, *c_chunk, *s_chunk;   // per chunk: record offset, rows
@@ -166,8 +166,8 @@ struct HostImage {
     std::vector<int> perm;
     int N = 0, R = 0, NE = 0;
     // lane-balanced schedules
-    int rpc = 1, n_row_chunks = 0, ng = 0, nh = 0, ncc = 0, ngp = 0, nhp = 0;
-    std::vector<int> g_pfirst, h_pfirst;
+    int rpc = 1, n_row_chunks = 0, ng = 0, nh = 0, ncc = 0, ngp = 0, nhp = 0, ncp = 0;
+    std::vector<int> g_pfirst, h_pfirst, c_pfirst;
     std::vector<uint32_t> g_rec, h_rec, c_rec, s_rec;       // 2, 4, 4, 4 words per record
     std::vector<int> g_chunk, h_chunk, c_chunk, s_chunk;   // (record offset, rows) per chunk
     int s_npart = 0;

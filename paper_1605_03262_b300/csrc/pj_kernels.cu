@@ -732,12 +732,14 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         }
         {                                               // C_k = -(W_k/W_N) sum_i nu_ki b'_iN
             double acc = 0.0;                           // (coefficients -(W_k/W_N) nu_ki in the records)
-            walk<HB, false, false>(m.c_chunk, m.ncc, wg, NW, m.c_rec, lane, no_op,
+            double *cpart = spart + 3 * m.ngp + m.nhp;
+            // the last warps take the C_k chunks, which the species gather and column sums load least
+            walk<HB, false, false>(m.c_chunk, m.ncc, NW - 1 - wg, NW, m.c_rec, lane, no_op,
                  [&](const uint4 &r) { return sb[r.x & 0xffffff]; },
                  [&](const uint4 &r, double b) {
                      acc = fma(__hiloint2double(int(r.w), int(r.z)), b, acc);
                      if (r.x >> 31) {
-                         sCk[r.y] = acc;
+                         cpart[r.y] = acc;
                          acc = 0.0;
                      }
                  },
@@ -745,7 +747,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         }
         group_sync<WPS>(g);
         // combine: each species / column sums its pieces' partials, in order
-        for (int item = t; item < 2 * N; item += G) {
+        for (int item = t; item < 3 * N; item += G) {
             if (item < N) {
                 const int k = item;
                 double wq = 0.0, wt = 0.0, wa = 0.0;
@@ -758,11 +760,17 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                 sf[k] = pre * wq;
                 sJk0[k] = pre * wt;
                 sA[k] = pre * fma(s.W, wq, wa);
-            } else {
+            } else if (item < 2 * N) {
                 const int j = item - N;
                 double hs = 0.0;
                 for (int p = __ldg(m.h_pfirst + j); p < __ldg(m.h_pfirst + j + 1); ++p) hs += spart[3 * m.ngp + p];
                 sHS[j] = hs * sInvW[j];
+            } else {
+                const int k = item - 2 * N;
+                const double *cpart = spart + 3 * m.ngp + m.nhp;
+                double ck = 0.0;
+                for (int p = __ldg(m.c_pfirst + k); p < __ldg(m.c_pfirst + k + 1); ++p) ck += cpart[p];
+                sCk[k] = ck;
             }
         }
         group_sync<WPS>(g);
@@ -1006,7 +1014,7 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
         sc.b = take(m.nslot + 1);
         sc.rows_per_chunk = m.rpc;
         // the row-staging buffers and the gather's partial sums are never live at the same time
-        sc.rows = take(std::max(wps * row_stride(m), 3 * m.ngp + m.nhp));
+        sc.rows = take(std::max(wps * row_stride(m), 3 * m.ngp + m.nhp + m.ncp));
         sc.part = sc.rows;
     } else {
         sc.dB = sc.Jk0 = sc.A = sc.Ck = sc.HS = sc.th = sc.a = sc.dH = sc.b = sc.rows = 0;

@@ -290,7 +290,7 @@ std::vector<std::vector<const Task *>> split_chunks(const std::vector<Task> &tas
         total += t.idx.size();
         longest = std::max(longest, t.idx.size());
     }
-    int n = int(std::max<size_t>(1, total / (32 * longest)));
+    int n = int(std::max<size_t>(1, (total + 32 * longest - 1) / (32 * longest)));
     n = std::min(n, n_max);
     std::vector<std::vector<const Task *>> out(n);
     std::vector<size_t> load(n, 0);
@@ -612,7 +612,8 @@ HostImage build_image(const void *buf, size_t len) {
             emit_chunk(c, zero_slot, zero_code, R, kRecAux, im.h_rec, im.h_chunk);
         im.nh = int(chunks.size());
     }
-    // C_k = -(W_k/W_N) sum nu_ki b'_iN, from the sparse entries of column N-1
+    // C_k = -(W_k/W_N) sum nu_ki b'_iN, from the sparse entries of column N-1 (cut into pieces
+    // like the gathers above; a combine adds a species' pieces in order)
     {
         std::vector<Task> tasks(N);
         for (int k = 0; k < N; ++k) {
@@ -628,7 +629,10 @@ HostImage build_image(const void *buf, size_t len) {
             }
             ensure_nonempty(tasks[k], zero_slot, zero_code, 0);
         }
-        auto chunks = split_chunks(tasks);
+        const int nw = default_wps(N, true);
+        auto pieces = cut_pieces(tasks, piece_length(tasks, nw), im.c_pfirst);
+        im.ncp = int(pieces.size());
+        auto chunks = split_chunks(pieces, nw);
         for (auto &c : chunks)
             emit_chunk(c, zero_slot, zero_code, 0, kRecCoef, im.c_rec, im.c_chunk);
         im.ncc = int(chunks.size());

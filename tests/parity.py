@@ -25,7 +25,8 @@ def compare(gpu, ora, scale, rel=REL, floor=FLOOR, kappa_mult=KAPPA_MULT):
     ok = finite & (err <= bound)
     strict = finite & (err <= rel * np.maximum(np.abs(ora), floor))
     rel_err = np.where(np.abs(ora) > floor, err / np.maximum(np.abs(ora), floor), 0.0)
-    kappa = np.where(np.abs(ora) > 0, scale / np.maximum(np.abs(ora), 1e-300), 0.0)
+    with np.errstate(over="ignore"):   # a huge scale over a tiny entry is an infinitely ill-conditioned entry
+        kappa = np.where(np.abs(ora) > 0, scale / np.maximum(np.abs(ora), 1e-300), 0.0)
     well = (kappa <= 4500.0) & (np.abs(ora) >= floor)
     return {
         "n": int(ora.size),
