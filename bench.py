@@ -50,67 +50,94 @@ def _distinct(side):
     return d
 
 
-def work_model(model) -> dict:
-    """FP64 operations the method needs per Jacobian, by kind.
+def _side_ops(nus, kc: bool) -> int:
+    """FP64 operations of one side of a reaction: powers [X]^nu and their derivatives (none for
+    nu = 1), the product and its partial derivatives, and the sums nu*B, nu*dB/dT (K_c only), nu*H."""
+    ops = sum({1: 0, 2: 2, 3: 3}.get(v, 4) for v in nus)
+    ops += {1: 0, 2: 3, 3: 7}.get(len(nus), 11)
+    return ops + len(nus) * (3 if kc else 1)
 
-    arith: FP64 add/mul/FMA operations of the formulation (each one FP64 pipe issue); exp, log,
-    div: calls of the transcendental functions and divisions. The counts follow the evaluation
-    order of the kernels (reaction terms once per reaction, gathers through the static lists, one
-    FMA per dense entry) and are a property of the model, not of a measurement."""
+
+def work_model(model) -> dict:
+    """FP64 operations the formulation needs per Jacobian, by kind.
+
+    arith: FP64 add/mul/FMA operations (each one FP64 pipe issue); exp, log, div: calls of the
+    transcendental functions and divisions. The counts follow the evaluation order of the kernels
+    (reaction terms once per reaction; a short path for elementary reactions, whose c = 1 and
+    psi = 0; gathers through the static lists at one FMA per term per sum; one FMA per sparse
+    contribution, the W_k/W_j scale folded into its coefficient; one FMA per dense entry) without
+    padding, replicated reductions or comparisons. It is a property of the model, not of a
+    measurement, and stays at or below the FP64 thread instructions ncu counts."""
     N, R = model.n_species, model.n_reactions
-    arith, n_exp, n_log, n_div = 24.0, 0.0, 2.0, 4.0          # per state: ln T, ln P, 1/T, 1/sum, 1/rho, 1/cp
-    arith += N * (33 + 3 + 2 + 5 + 5)                       # thermo, reductions, [X], gather finish, energy sums
+    # per state: 1/T, ln T, ln P, 1/sum(Y/W), P/(RT), rho, 1/cp, 1/rho, J00 and dydt_0
+    arith, n_exp, n_log, n_div = 12.0, 0.0, 2.0, 5.0
+    # per species: thermo (c_p, H, B, dB/dT, dc_p/dT), 3 mixture sums, [X], gather finish (5),
+    # HS scale, energy sums (5)
+    arith += N * (32 + 3 + 2 + 5 + 1 + 5)
     pairs = contributions = colent = 0
     nnz = set()
     for r in model.reactions:
         reac, prod = _distinct(r.reac), _distinct(r.prod)
-        nsp = len(reac) + len(prod)
+        kc = r.rev_mode == synth.REV_KC
+        elem = r.kind == synth.KIND_ELEMENTARY
         net = {}
-        for s, nu in reac.items():
-            net[s] = net.get(s, 0) - nu
-        for s, nu in prod.items():
-            net[s] = net.get(s, 0) + nu
-        net = [s for s, v in net.items() if v != 0]
+        for sp, nu in reac.items():
+            net[sp] = net.get(sp, 0) - nu
+        for sp, nu in prod.items():
+            net[sp] = net.get(sp, 0) + nu
+        net = [sp for sp, v in net.items() if v != 0]
         slots = set(reac) | set(prod)
+        neff = 0
         if r.kind in (synth.KIND_THIRD_BODY, synth.KIND_FALLOFF, synth.KIND_CHEM):
             if r.tb_mode == synth.TB_SPECIES:
                 slots.add(r.tb_species)
             else:
-                slots |= {s for s, a in r.eff if a != 1.0}
-        a = 4 + 4 * nsp + 20 + nsp + 2 * len(slots)         # ln k, products/partials, R, q, theta, sigma, a, dH, b'
-        if r.rev_mode == synth.REV_KC:
-            a += 4 * nsp + 3
+                slots |= {sp for sp, a in r.eff if a != 1.0}
+                neff = len(r.eff) + 1                       # efficiency terms and M = C_tot + sum
+        a = _side_ops(list(reac.values()), kc) + _side_ops(list(prod.values()), kc)
+        if kc:
+            a += 5                                          # ln K_c, k_r argument, d ln k_r / dT
             n_exp += 1
         elif r.rev_mode == synth.REV_EXPLICIT:
             a += 4
             n_exp += 1
+        a += 3 + 4 + 2 + 1                                  # R_f, R_r, R; dR/dT; sigma; dH
+        nside = sum((sp in reac) + (sp in prod) for sp in slots)
+        if elem:
+            a += 2 + nside                                  # theta, a; b' slots
+        else:
+            a += 1 + 3 + 4 + 3 + nside + len(slots)         # q, theta, a, c k_f / c k_r / psi R; b' slots
         if r.kind in (synth.KIND_ELEMENTARY, synth.KIND_THIRD_BODY):
+            a += 4                                          # ln k_f, d ln k_f / dT
             n_exp += 1
             if r.kind == synth.KIND_THIRD_BODY:
-                a += 2 * len(r.eff) + 3
+                a += neff + 1                               # [M], dc/dT
         elif r.kind in (synth.KIND_FALLOFF, synth.KIND_CHEM):
-            a += 8 + 2 * len(r.eff) + 14                      # k0, kinf, Pr, c, phi, psi, dc/dT
-            n_exp += 2
+            a += 8 + neff + 2 + 1 + 4                       # k_0, k_inf (+ derivatives), [M], Pr, 1 + Pr, dc/dT
+            n_exp += 2                                      # k_0 / k_inf, k_f
             n_div += 1
             if r.ftype == synth.F_TROE:
-                a += 30
+                a += 32 + (6 if r.troe_has_T2 else 0)
                 n_exp += 3 + (1 if r.troe_has_T2 else 0)
                 n_log += 2
-                n_div += 2
+                n_div += 3
             elif r.ftype == synth.F_SRI:
-                a += 20
+                a += 21
                 n_exp += 3
                 n_log += 2
                 n_div += 2
             if r.kind == synth.KIND_CHEM:
+                a += 5
                 n_div += 1
+            else:
+                a += 6
         elif r.kind == synth.KIND_PLOG:
-            a += 12
+            a += 16
             n_exp += 1
             n_div += 1
         else:
             nt, npc = r.cheb_shape
-            a += 2 * nt * npc + 6 * (nt + npc) + 8
+            a += 3 * nt * npc + 7 * nt + 11
             n_exp += 1
         arith += a
         pairs += len(net)
@@ -119,8 +146,10 @@ def work_model(model) -> dict:
             for l in slots:
                 nnz.add((k, l))
                 contributions += 1
-    arith += 3 * pairs + 2 * contributions + 2 * len(nnz) + colent + N
-    arith += N * (N - 1) + 4 * (N - 1) + 6                  # dense species block, energy row, J00
+    # gathers: omega, theta and A sums (3 per reaction-species pair), column sums (1 per reaction
+    # slot), sparse block and C_k (1 per contribution)
+    arith += 3 * pairs + colent + contributions
+    arith += N * (N - 1) + 5 * (N - 1)                      # dense species block, energy row
     return {"arith": arith, "exp": n_exp, "log": n_log, "div": n_div, "nnz": len(nnz),
             "contributions": contributions}
 
