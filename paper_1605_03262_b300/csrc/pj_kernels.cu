@@ -585,10 +585,11 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
         }
     }
     group_sync<WPS>(g);
-    // species sums sum Y/W, sum Y cp_k, sum Y dcp_k/dT in a fixed 32-lane order: repeated per
-    // warp in narrow groups, one warp each in wide ones (same order, same bits)
+    // species sums sum Y/W, sum Y cp_k, sum Y dcp_k/dT in a fixed 32-lane order: a one-warp group
+    // computes all three; in wider groups warp w computes every NW-th sum and shares it (same order,
+    // same bits)
     double sYW, cp, dcpdT;
-    if (NW < 4) {
+    if (NW == 1) {
         double r1 = 0.0, r2 = 0.0, r3 = 0.0;
         for (int k = lane; k < N; k += 32) {
             const double y = sY[k];
@@ -600,12 +601,12 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
         cp = warp_sum(r2);
         dcpdT = JAC ? warp_sum(r3) : 0.0;
     } else {
-        if (wg < (JAC ? 3 : 2)) {
-            const double *xs = wg == 0 ? sInvW : wg == 1 ? scp : sJk0;
+        for (int q = wg; q < (JAC ? 3 : 2); q += NW) {
+            const double *xs = q == 0 ? sInvW : q == 1 ? scp : sJk0;
             double r = 0.0;
             for (int k = lane; k < N; k += 32) r = fma(sY[k], xs[k], r);
             r = warp_sum(r);
-            if (lane == 0) sred[wg] = r;
+            if (lane == 0) sred[q] = r;
         }
         group_sync<WPS>(g);
         sYW = sred[0];
@@ -774,9 +775,9 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
             }
         }
         group_sync<WPS>(g);
-        // energy sums HA, Hf, HJ0, CF: repeated per warp in narrow groups, one warp each in wide ones
+        // energy sums HA, Hf, HJ0, CF: all by a one-warp group, else every NW-th by warp w, shared
         double HA, Hf, HJ0, CF;
-        if (NW < 4) {
+        if (NW == 1) {
             double x1 = 0.0, x2 = 0.0, x3 = 0.0, x4 = 0.0;
             for (int k = lane; k < N; k += 32) {
                 const double hk = sH[k] * sInvW[k];
@@ -790,15 +791,15 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
             HJ0 = warp_sum(x3);
             CF = warp_sum(x4);
         } else {
-            if (wg < 4) {
-                const double *v = wg == 0 ? sA : wg == 2 ? sJk0 : sf;
+            for (int q = wg; q < 4; q += NW) {
+                const double *v = q == 0 ? sA : q == 2 ? sJk0 : sf;
                 double x = 0.0;
                 for (int k = lane; k < N; k += 32) {
-                    const double uk = wg == 3 ? scp[k] : sH[k] * sInvW[k];
+                    const double uk = q == 3 ? scp[k] : sH[k] * sInvW[k];
                     x = fma(uk, v[k], x);
                 }
                 x = warp_sum(x);
-                if (lane == 0) sred[4 + wg] = x;
+                if (lane == 0) sred[4 + q] = x;
             }
             group_sync<WPS>(g);
             HA = sred[4];
@@ -825,6 +826,26 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
              [&](int c) {                               // dense part of chunk c
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
                  comb = __ldg(m.s_comb_chunk + c);     // split entries of this chunk
+                 if (RPC == 1 && r0 > 0) {              // one species row: its constants once
+                     const int k = r0 - 1;
+                     const double a = sA[k], ck = sCk[k], jk0 = sJk0[k];
+                     auto value1 = [&](int j) {
+                         const double d = (j == 0 || j == N) ? 0.0 : sDelta[j - 1];
+                         return (j == 0) ? jk0 : (j == N) ? 0.0 : fma(a, d, ck);
+                     };
+                     int x = lane;
+                     for (; x - lane + 32 * kDense <= ld; x += 32 * kDense) {
+                         double v[kDense];
+#pragma unroll
+                         for (int u = 0; u < kDense; ++u) v[u] = value1(x + 32 * u);
+#pragma unroll
+                         for (int u = 0; u < kDense; ++u) stage[x + 32 * u] = v[u];
+                     }
+                     for (; x < ld; x += 32) stage[x] = value1(x);
+                     crec = lane < comb.y ? __ldg(m.s_comb + comb.x + lane) : make_int4(0, 0, 0, 0);
+                     __syncwarp();
+                     return;
+                 }
                  int x0 = lane;
                  if (r0 == 0) {                         // energy row: its own loop, so that the
                      for (int j = lane; j < ld; j += 32) {   // species rows carry no FP64 work of it
