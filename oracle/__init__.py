@@ -76,6 +76,8 @@ def _bind(lib):
     lib.pjo_eval_jacobian.restype = i32
     lib.pjo_jacobian_complex_step.argtypes = [vp, i64, dp, dp, dp, i64, ctypes.c_double, dp, i64]
     lib.pjo_jacobian_complex_step.restype = i32
+    lib.pjo_jacobian_fd.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
+    lib.pjo_jacobian_fd.restype = i32
     lib.pjo_reaction_rates.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
     lib.pjo_reaction_rates.restype = i32
     lib.pjo_species_thermo.argtypes = [vp, ctypes.c_double, dp, dp, dp, dp]
@@ -162,6 +164,18 @@ class OracleModel:
         if rc:
             raise RuntimeError("oracle complex step failed (%d)" % rc)
         return J
+
+    def jacobian_fd(self, T, P, Y, with_scale: bool = False):
+        """First-order forward-difference Jacobian (the paper's finite-difference comparison),
+        (n, N+1, N+1); with_scale also returns the per-entry rounding scale (S(y+h) + S(y)) / h."""
+        T, P, Y = _f64(T).ravel(), _f64(P).ravel(), _f64(Y)
+        n, N = Y.shape
+        J = np.empty((n, N + 1, N + 1))
+        Js = np.empty_like(J) if with_scale else None
+        rc = self._lib.pjo_jacobian_fd(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, _ptr(J), (N + 1) ** 2, _ptr(Js))
+        if rc:
+            raise RuntimeError("oracle finite-difference jacobian failed (%d)" % rc)
+        return (J, Js) if with_scale else J
 
     # -- single-state introspection ------------------------------------------------------------
     def reaction_rates(self, T: float, P: float, Y):

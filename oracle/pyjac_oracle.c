@@ -673,6 +673,64 @@ int pjo_eval_jacobian(const pjo_mech *m, int64_t n, const double *T, const doubl
     return err;
 }
 
+/* First-order forward-difference Jacobian: the finite-difference comparison of the paper's
+ * performance section (a first-order forward difference adapted from CVODE). Column 0 moves T,
+ * column j (1..N-1) moves Y_j by +h_j and Y_N by -h_j (the directions of the analytical columns),
+ * column N is zero. Increment h_c = 2^-26 max(|y_c|, a_c) with a_0 = 1 K and a_c = 1e-10 for mass
+ * fractions: CVODE's relative increment sqrt(unit roundoff) |y_c|, with a fixed floor in place of
+ * its error-weight term (which needs an integrator's tolerances and step size). 2^-26 is exactly
+ * sqrt(DBL_EPSILON). J_kc = (f_k(y + h_c d_c) - f_k(y)) / h_c. With jac_scale, each entry also
+ * gets (S_k(y + h_c d_c) + S_k(y)) / h_c, S the source-term scale (sum of the absolute values of
+ * the terms of f_k): a bound on how far rounding in f can move the entry. */
+static double fd_increment(int c, double T, const double *Y)
+{
+    const double y = c == 0 ? T : Y[c - 1], a = c == 0 ? 1.0 : 1e-10;
+    return 0x1p-26 * fmax(fabs(y), a);
+}
+
+int pjo_jacobian_fd(const pjo_mech *m, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
+                    double *jac, int64_t ldj, double *jac_scale)
+{
+    if (!m || n < 0 || ldy < m->ns) return PJO_EINVAL;
+    const int N = m->ns;
+    if (ldj < (int64_t)(N + 1) * (N + 1)) return PJO_EINVAL;
+    if (n == 0) return PJO_OK;
+    if (!T || !P || !Y || !jac) return PJO_EINVAL;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(pjo_max_threads())
+    for (int64_t s = 0; s < n; ++s) {
+        /* f and its per-entry term scale come from the Jacobian routine (its J is discarded) */
+        double *buf = malloc(((size_t)N + 4 * ((size_t)N + 1) + (size_t)(N + 1) * (N + 1)) * sizeof(double));
+        if (!buf) { err = 1; continue; }
+        double *Yp = buf, *f0 = Yp + N, *s0 = f0 + N + 1, *f1 = s0 + N + 1, *s1 = f1 + N + 1, *Jt = s1 + N + 1;
+        const double *Ys = Y + s * ldy;
+        double *Jo = jac + s * ldj, *Jso = jac_scale ? jac_scale + s * ldj : NULL;
+        int rc = jac_one(m, T[s], P[s], Ys, Jt, NULL, f0, s0);
+        for (int col = 0; col < N + 1; ++col) {
+            if (col == N) {
+                for (int row = 0; row < N + 1; ++row) {
+                    Jo[(size_t)row * (N + 1) + col] = 0.0;
+                    if (Jso) Jso[(size_t)row * (N + 1) + col] = 0.0;
+                }
+                continue;
+            }
+            const double h = fd_increment(col, T[s], Ys);
+            double Tp = T[s];
+            for (int k = 0; k < N; ++k) Yp[k] = Ys[k];
+            if (col == 0) Tp = T[s] + h;
+            else { Yp[col - 1] = Ys[col - 1] + h; Yp[N - 1] = Ys[N - 1] - h; }
+            rc |= jac_one(m, Tp, P[s], Yp, Jt, NULL, f1, s1);
+            for (int row = 0; row < N + 1; ++row) {
+                Jo[(size_t)row * (N + 1) + col] = (f1[row] - f0[row]) / h;
+                if (Jso) Jso[(size_t)row * (N + 1) + col] = (s1[row] + s0[row]) / h;
+            }
+        }
+        free(buf);
+        if (rc) err = 1;
+    }
+    return err ? PJO_ENOMEM : PJO_OK;
+}
+
 /* Complex-step Jacobian of the templated source terms: column 0 from T + i h, column j from
  * Y_j + i h, Y_N - i h (j = 1..N-1); column N is zero. Exact to rounding for analytic f. */
 int pjo_jacobian_complex_step(const pjo_mech *m, int64_t n, const double *T, const double *P, const double *Y,

@@ -418,3 +418,49 @@ def test_load_rejects_corrupt_and_truncated_models():
         oracle.load_model(b"NOTAMODEL" + blob[9:])
     with pytest.raises(ValueError):
         oracle.load_model(blob + b"\0")
+
+
+# ---------------------------------------------------------------------------------------------
+# forward-difference Jacobian (the paper's finite-difference comparison)
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_forward_difference_within_its_rounding_bound_of_complex_step(cfg):
+    """The first-order forward difference converges to the exact (complex-step) Jacobian: every
+    entry lies within the rounding bound 64 eps S / h that the oracle reports for it plus a
+    truncation allowance of 1e-5 |J|. Perturbing Y_j without the opposite step in Y_N, a wrong
+    increment or a shifted column gives errors of order |J| instead."""
+    model = synth.config_model(cfg)
+    om = _om(model)
+    T, P, Y = synth.config_states(cfg, 6, seed_offset=77)
+    Jfd, Jsc = om.jacobian_fd(T, P, Y, with_scale=True)
+    Jcs = om.jacobian_complex_step(T, P, Y)
+    err = np.abs(Jfd - Jcs)
+    assert np.all(err <= 64 * EPS * Jsc + 1e-5 * np.abs(Jcs) + 1e-300)
+    assert np.all(Jfd[:, :, -1] == 0.0)
+    # the typical entry is accurate to far better than the allowance
+    big = np.abs(Jcs) > 1e-6 * np.abs(Jcs).max()
+    assert np.median(err[big] / np.abs(Jcs[big])) < 1e-5
+
+
+def test_forward_difference_increment_rule():
+    """Column c is (f(y + h_c d_c) - f(y)) / h_c with h_c = 2^-26 max(|y_c|, a_c), a = 1 K for T
+    and 1e-10 for mass fractions, d_c = e_T or e_Yj - e_YN; checked on the source terms directly."""
+    model = synth.config_model(0)
+    om = _om(model)
+    T, P, Y = synth.config_states(0, 1, seed_offset=5)
+    Y = Y.copy()
+    Y[0, 3] = 0.0                                              # takes the 1e-10 floor
+    N = model.n_species
+    Jfd, Jsc = om.jacobian_fd(T, P, Y, with_scale=True)
+    f0 = om.dydt(T, P, Y)[0]
+    for c in (0, 1, 4, N - 1):
+        Tp, Yp = T.copy(), Y.copy()
+        if c == 0:
+            h = 2.0 ** -26 * max(abs(T[0]), 1.0)
+            Tp[0] += h
+        else:
+            h = 2.0 ** -26 * max(abs(Y[0, c - 1]), 1e-10)
+            Yp[0, c - 1] += h
+            Yp[0, N - 1] -= h
+        col = (om.dydt(Tp, P, Yp)[0] - f0) / h
+        assert np.all(np.abs(col - Jfd[0, :, c]) <= 64 * EPS * Jsc[0, :, c] + 1e-300)
