@@ -394,6 +394,50 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     return res, (g, model, T, P, Y, Td, Pd, Yd)
 
 
+FD_WORKSPACE_BYTES = 4 << 30
+
+
+def fd_form(per_config: dict, steps: int, warmup: int):
+    """The paper's finite-difference comparison on this GPU (Section 5.2): first-order forward-
+    difference Jacobians from the library's source-term kernel, timed like the analytical ones on
+    the same states; reports FD time / analytical time per model (the paper's Table of GPU
+    ratios)."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    out = {}
+    for cfg in (0, 1, 2, 3):
+        name = synth.CONFIGS[cfg]["name"]
+        if name not in per_config:
+            continue
+        model = synth.config_model(cfg)
+        n = per_config[name]["n_states"]
+        T, P, Y = synth.config_states(cfg, n)
+        g = pj.Model(synth.to_bytes(model))
+        Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+        N = model.n_species
+        J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
+        ws = torch.empty(min(g.fd_workspace_bytes(n), FD_WORKSPACE_BYTES), dtype=torch.uint8, device="cuda")
+        for _ in range(warmup):
+            g.eval_jacobian_fd(Td, Pd, Yd, out=J, workspace=ws)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            g.eval_jacobian_fd(Td, Pd, Yd, out=J, workspace=ws)
+            e.record()
+            torch.cuda.synchronize()
+            ms.append(s.elapsed_time(e))
+        fd_ms = float(np.median(ms))
+        an_ms = per_config[name]["ms_median"]
+        out[name] = {"n_states": n, "fd_ms": fd_ms, "fd_jacobians_per_s": n / (fd_ms * 1e-3),
+                     "analytic_ms": an_ms, "fd_over_analytic": fd_ms / an_ms,
+                     "workspace_bytes": ws.numel()}
+        del J, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 BATCH_MIX = ((0, 16384), (1, 65536), (2, 32768), (3, 2048))
 
 
@@ -608,6 +652,8 @@ def run_ours(args):
                                                                         "fp64_dfma_equiv_per_jacobian")}
             torch.cuda.empty_cache()
     batched = batched_form(max(3, args.steps // 2), args.warmup) if not args.headline_only else None
+    fd = fd_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), 3, 1) \
+        if not (args.headline_only or args.no_fd) else None
     serving = serving_form() if not (args.headline_only or args.no_serving) else None
     per_config[synth.CONFIGS[HEADLINE_CFG]["name"]] = {k: res[k] for k in ("n_states", "ms_per_step",
                                                                             "ms_median", "ms_min",
@@ -639,6 +685,7 @@ def run_ours(args):
         "calibration": cal,
         "per_config": per_config,
         "batched_form": batched,
+        "fd_form": fd,
         "serving_form": serving,
     }
     if not args.no_cpu_baseline:
@@ -731,6 +778,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
+    ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference comparison")
     ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS]", help="one small profiling case (for ncu)")
     args = ap.parse_args()
     if args.profile:

@@ -120,6 +120,25 @@ PJ_API int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const 
 PJ_API int pj_eval_jacobian_host(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
                           int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, int64_t chunk_states);
 
+/*
+ * First-order forward-difference Jacobian: the finite-difference comparison of Section 5.2
+ * (Performance analysis; a first-order forward difference adapted from CVODE), evaluated with the
+ * library's source-term kernel. Column c of a state's Jacobian is (f(y + h_c d_c) - f(y)) / h_c:
+ * d_0 moves T; d_c (c = 1..N-1) moves Y_c by +h_c and Y_N by -h_c, the directions of the
+ * analytical columns; column N is zero. h_c = 2^-26 max(|y_c|, a_c), a_0 = 1 K, a_c = 1e-10 for
+ * mass fractions (CVODE's relative increment sqrt(unit roundoff) |y_c| with a fixed floor in place
+ * of its error-weight term). Same layout, pointer and error rules as pj_eval_jacobian (no dydt
+ * output). workspace: device memory of workspace_bytes, owned by the caller, for the perturbed
+ * states and their source terms; the states are processed in chunks of as many states as it holds
+ * (pj_fd_workspace_bytes gives the size for n states in one pass). PJ_EINVAL if it holds less than
+ * one state or is not 8-byte aligned. Asynchronous on stream; overlapping calls must not share a
+ * workspace.
+ */
+PJ_API int pj_fd_workspace_bytes(const pj_mech *m, int64_t n, size_t *bytes);
+PJ_API int pj_eval_jacobian_fd(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
+                               int64_t ldy, double *jac, int64_t ldj, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
 /* Launch shape of the evaluation kernels for one model (which: 0 = Jacobian, 1 = source terms).
  * warps_per_state in {1, 2, 4, 8, 16}: warps that cooperate on one state; states_per_cta: states
  * a CTA evaluates concurrently (CTA size = warps_per_state * 32 * states_per_cta <= 512; at most

@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
             "pj_mech_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(sz)], i32),
             "pj_eval_dydt": ([vp, i64, vp, vp, vp, i64, vp, i64, vp], i32),
             "pj_eval_jacobian": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
+            "pj_fd_workspace_bytes": ([vp, i64, ctypes.POINTER(sz)], i32),
+            "pj_eval_jacobian_fd": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, sz, vp], i32),
             "pj_eval_jacobian_host": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, i64], i32),
             "pj_set_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
             "pj_get_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
@@ -220,6 +222,27 @@ class Model:
         _check(library().pj_eval_jacobian(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out), ldj,
                                           _ptr(f), f.stride(0) if f is not None else 0, _stream_handle(stream)))
         return (out, f) if f is not None else out
+
+    def fd_workspace_bytes(self, n: int) -> int:
+        """Device workspace (bytes) of eval_jacobian_fd for n states in one pass."""
+        b = ctypes.c_size_t()
+        _check(library().pj_fd_workspace_bytes(self._h, int(n), ctypes.byref(b)))
+        return b.value
+
+    def eval_jacobian_fd(self, T, P, Y, out=None, workspace=None, stream=None):
+        """First-order forward-difference Jacobian (n, N+1, N+1) (the paper's finite-difference
+        comparison), from the library's source-term kernel. workspace: a CUDA uint8 tensor; a
+        smaller one than fd_workspace_bytes(n) makes the library process the states in chunks."""
+        torch = _torch()
+        T, P, Y, n = self._inputs(T, P, Y)
+        N = self.n_species
+        if out is None:
+            out = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device=self.device)
+        if workspace is None:
+            workspace = torch.empty(max(8, self.fd_workspace_bytes(n)), dtype=torch.uint8, device=self.device)
+        _check(library().pj_eval_jacobian_fd(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out),
+                                             out.stride(0), _ptr(workspace), workspace.numel(), _stream_handle(stream)))
+        return out
 
     # -- evaluation on host buffers (end to end) -----------------------------------------------
     def eval_jacobian_host(self, T, P, Y, jac, dydt=None, chunk_states: int = 0):

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
-SOURCES = ["pj_model.cu", "pj_kernels.cu", "pj_api.cu", "pj_host.cu", "pj_batch.cu"]
+SOURCES = ["pj_model.cu", "pj_kernels.cu", "pj_api.cu", "pj_host.cu", "pj_batch.cu", "pj_fd.cu"]
 HEADERS = ["pj_internal.h", "pj_fastmath.cuh"]
 LIB = os.path.join(HERE, "libpyjacb300.so")
 CALIB_SRC = "pj_calib.cu"

@@ -325,6 +325,50 @@ int pj_eval_dydt(const pj_mech *m, int64_t n, const double *T, const double *P, 
     return launch(m, false, n, T, P, Y, ldy, nullptr, 0, dydt, ldd, static_cast<cudaStream_t>(stream));
 }
 
+// Doubles of forward-difference workspace per state: the N perturbed states (T, P, Y[N]), their
+// source terms (N x (N+1)) and the state's own source terms (N+1).
+static size_t fd_doubles_per_state(int N) { return size_t(N) * (N + 2) + size_t(N) * (N + 1) + size_t(N + 1); }
+
+int pj_fd_workspace_bytes(const pj_mech *m, int64_t n, size_t *bytes) {
+    if (!m || n < 0 || !bytes) return fail(PJ_EINVAL, "pj_fd_workspace_bytes: bad argument");
+    *bytes = size_t(n) * fd_doubles_per_state(m->N) * sizeof(double);
+    return PJ_OK;
+}
+
+int pj_eval_jacobian_fd(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
+                        int64_t ldy, double *jac, int64_t ldj, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+    if (!m) return fail(PJ_EINVAL, "pj_eval_jacobian_fd: null model");
+    if (n < 0) return fail(PJ_EINVAL, "pj_eval_jacobian_fd: n < 0");
+    if (ldy < m->N) return fail(PJ_EINVAL, "pj_eval_jacobian_fd: ldy < number of species");
+    const int N = m->N;
+    if (ldj < int64_t(N + 1) * (N + 1)) return fail(PJ_EINVAL, "pj_eval_jacobian_fd: ldj < (number of species + 1)^2");
+    if (n == 0) return PJ_OK;
+    const size_t per = fd_doubles_per_state(N);
+    const int64_t chunk = int64_t(std::min<size_t>(size_t(n), workspace_bytes / (per * sizeof(double))));
+    if (chunk < 1) return fail(PJ_EINVAL, "pj_eval_jacobian_fd: workspace smaller than one state needs");
+    if (reinterpret_cast<uintptr_t>(workspace) & 7) return fail(PJ_EINVAL, "pj_eval_jacobian_fd: workspace not 8-byte aligned");
+    int rc;
+    if ((rc = check_model_device(m)) || (rc = check_device_ptr(T, m->device, "T")) ||
+        (rc = check_device_ptr(P, m->device, "P")) || (rc = check_device_ptr(Y, m->device, "Y")) ||
+        (rc = check_device_ptr(jac, m->device, "jac")) || (rc = check_device_ptr(workspace, m->device, "workspace")))
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int64_t s0 = 0; s0 < n; s0 += chunk) {
+        const int64_t cs = std::min(chunk, n - s0);
+        double *Tp = static_cast<double *>(workspace), *Pp = Tp + cs * N, *Yp = Pp + cs * N;
+        double *Fp = Yp + cs * N * N, *F0 = Fp + cs * N * (N + 1);
+        const double *Ts = T + s0, *Ps = P + s0, *Ys = Y + s0 * ldy;
+        if ((rc = launch(m, false, cs, Ts, Ps, Ys, ldy, nullptr, 0, F0, N + 1, st))) return rc;
+        cudaError_t e = pj::launch_fd_perturb(N, cs, Ts, Ps, Ys, ldy, Tp, Pp, Yp, st);
+        if (e != cudaSuccess) return cuda_fail(e, "finite-difference perturbation kernel");
+        if ((rc = launch(m, false, cs * N, Tp, Pp, Yp, N, nullptr, 0, Fp, N + 1, st))) return rc;
+        e = pj::launch_fd_difference(N, cs, Ts, Ys, ldy, F0, Fp, jac + s0 * ldj, ldj, st);
+        if (e != cudaSuccess) return cuda_fail(e, "finite-difference column kernel");
+    }
+    return PJ_OK;
+}
+
 int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
                      int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream) {
     if (!m) return fail(PJ_EINVAL, "pj_eval_jacobian: null model");

@@ -187,6 +187,11 @@ int shared_const_doubles(int N);
 cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream);
 cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem);
 cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads, size_t smem, cudaStream_t stream);
+// Forward-difference Jacobian kernels (pj_fd.cu).
+cudaError_t launch_fd_perturb(int N, long long ns, const double *T, const double *P, const double *Y, long long ldy,
+                              double *Tp, double *Pp, double *Yp, cudaStream_t st);
+cudaError_t launch_fd_difference(int N, long long ns, const double *T, const double *Y, long long ldy,
+                                 const double *F0, const double *Fp, double *jac, long long ldj, cudaStream_t st);
 int set_error(int code, const std::string &msg);   // records the calling thread's last error, returns code
 
 }  // namespace pj

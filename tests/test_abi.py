@@ -71,3 +71,14 @@ def test_oversized_stoichiometry_is_unsupported(lib):
     buf = ctypes.create_string_buffer(blob, len(blob))
     h = ctypes.c_void_p()
     assert lib.pj_mech_load(buf, len(blob), ctypes.byref(h)) == -6          # PJ_EUNSUPPORTED
+
+
+def test_fd_entry_points_reject_null_model(lib):
+    lib.pj_eval_jacobian_fd.restype = ctypes.c_int
+    lib.pj_eval_jacobian_fd.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 3 + \
+        [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert lib.pj_eval_jacobian_fd(None, 4, None, None, None, 13, None, 196, None, 0, None) == -1
+    lib.pj_fd_workspace_bytes.restype = ctypes.c_int
+    lib.pj_fd_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+    b = ctypes.c_size_t()
+    assert lib.pj_fd_workspace_bytes(None, 4, ctypes.byref(b)) == -1
