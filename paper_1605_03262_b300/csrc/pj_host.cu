@@ -76,7 +76,8 @@ extern "C" int pj_eval_jacobian_host(const pj_mech *cm, int64_t n, const double 
     if (dydt && ldd < N + 1) return host_fail(PJ_EINVAL, "pj_eval_jacobian_host: ldd < number of species + 1");
     if (n == 0) return PJ_OK;
     if (!T || !P || !Y || !jac) return host_fail(PJ_EINVAL, "pj_eval_jacobian_host: null pointer");
-    int64_t chunk = chunk_states > 0 ? chunk_states : std::max<int64_t>(1024, (256ll << 20) / (nn * 8));
+    // 64 MB of Jacobians per chunk: the copy stream waits only for the first chunk's kernel
+    int64_t chunk = chunk_states > 0 ? chunk_states : std::max<int64_t>(1024, (64ll << 20) / (nn * 8));
     chunk = std::min(chunk, n);
     int rc = ensure_staging(m, chunk);
     if (rc) return rc;
@@ -87,15 +88,18 @@ extern "C" int pj_eval_jacobian_host(const pj_mech *cm, int64_t n, const double 
         const int64_t cn = std::min(chunk, n - c0);
         cudaStream_t st = s->st[b];
         cudaError_t e;
+        // strided host rows go by 2D copies, contiguous ones by plain copies
         if ((e = cudaMemcpyAsync(s->T[b], T + c0, cn * d, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(s->P[b], P + c0, cn * d, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = cudaMemcpy2DAsync(s->Y[b], N * d, Y + c0 * ldy, ldy * d, N * d, cn, cudaMemcpyHostToDevice, st)) !=
-                cudaSuccess)
+            (e = ldy == N ? cudaMemcpyAsync(s->Y[b], Y + c0 * ldy, cn * N * d, cudaMemcpyHostToDevice, st)
+                          : cudaMemcpy2DAsync(s->Y[b], N * d, Y + c0 * ldy, ldy * d, N * d, cn,
+                                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_err(e, "host-to-device copy");
         rc = pj_eval_jacobian(m, cn, s->T[b], s->P[b], s->Y[b], N, s->J[b], nn, dydt ? s->F[b] : nullptr, N + 1, st);
         if (rc) return rc;
-        if ((e = cudaMemcpy2DAsync(jac + c0 * ldj, ldj * d, s->J[b], nn * d, nn * d, cn, cudaMemcpyDeviceToHost, st)) !=
-            cudaSuccess)
+        if ((e = ldj == nn ? cudaMemcpyAsync(jac + c0 * ldj, s->J[b], cn * nn * d, cudaMemcpyDeviceToHost, st)
+                           : cudaMemcpy2DAsync(jac + c0 * ldj, ldj * d, s->J[b], nn * d, nn * d, cn,
+                                               cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return cuda_err(e, "device-to-host copy");
         if (dydt && (e = cudaMemcpy2DAsync(dydt + c0 * ldd, ldd * d, s->F[b], (N + 1) * d, (N + 1) * d, cn,
                                            cudaMemcpyDeviceToHost, st)) != cudaSuccess)
