@@ -195,3 +195,25 @@ def test_host_buffer_path_equals_device_path():
     torch.cuda.synchronize()
     assert torch.equal(Jh, ref.cpu())
     assert torch.equal(fh, fref.cpu())
+
+
+def test_host_buffer_path_with_strided_rows():
+    """Host rows with padding (ldy > N, ldj > (N+1)^2) take the pitched copies; the padding stays
+    untouched and the values equal the device path's."""
+    model = synth.config_model(0)
+    T, P, Y = synth.config_states(0, 900)
+    g = _gpu_model(model)
+    N = model.n_species
+    nn = (N + 1) ** 2
+    Yp = torch.full((900, N + 3), 7.0, dtype=torch.float64).pin_memory()
+    Yp[:, :N] = torch.from_numpy(Y)
+    Jp = torch.full((900, nn + 5), -3.0, dtype=torch.float64).pin_memory()
+    Th, Ph = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (T, P))
+    import paper_1605_03262_b300 as pj
+    from paper_1605_03262_b300 import _check, library
+    _check(library().pj_eval_jacobian_host(g.handle, 900, Th.data_ptr(), Ph.data_ptr(), Yp.data_ptr(), N + 3,
+                                           Jp.data_ptr(), nn + 5, None, 0, 256))
+    Td, Pd, Yd = _dev(T, P, Y)
+    ref = g.eval_jacobian(Td, Pd, Yd).cpu().reshape(900, nn)
+    assert torch.equal(Jp[:, :nn], ref)
+    assert torch.all(Jp[:, nn:] == -3.0)
