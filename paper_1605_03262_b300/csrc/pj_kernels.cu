@@ -51,6 +51,37 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Two and four sums at once, each with exactly the addition tree of warp_sum (offsets 16, 8, 4, 2,
+// 1; a + b is commutative, so each result has the same bits): in the first steps a lane keeps only
+// the sums its half (quarter) of the warp finishes and trades the others with its partner, so the
+// four sums cost 6 FP64 adds instead of 20. Every lane gets every sum.
+__device__ __forceinline__ void warp_sum2(double &a, double &b) {
+    const int lane = threadIdx.x & 31;
+    const bool lo = lane < 16;
+    double v = (lo ? a : b) + __shfl_xor_sync(0xffffffffu, lo ? b : a, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    a = __shfl_sync(0xffffffffu, v, 0);
+    b = __shfl_sync(0xffffffffu, v, 16);
+}
+
+__device__ __forceinline__ void warp_sum4(double &a, double &b, double &c, double &d) {
+    const int lane = threadIdx.x & 31;
+    const bool lo = lane < 16;
+    // step 16: lanes 0-15 keep (a, b), lanes 16-31 keep (c, d)
+    double x = (lo ? a : c) + __shfl_xor_sync(0xffffffffu, lo ? c : a, 16);
+    double y = (lo ? b : d) + __shfl_xor_sync(0xffffffffu, lo ? d : b, 16);
+    // step 8: in each half, lanes with bit 3 clear keep the first, the others the second
+    const bool first = (lane & 8) == 0;
+    double v = (first ? x : y) + __shfl_xor_sync(0xffffffffu, first ? y : x, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    a = __shfl_sync(0xffffffffu, v, 0);
+    b = __shfl_sync(0xffffffffu, v, 8);
+    c = __shfl_sync(0xffffffffu, v, 16);
+    d = __shfl_sync(0xffffffffu, v, 24);
+}
+
 // The threads that evaluate one state: group index in the CTA, thread index in the group, lane,
 // warp in the group, warps per group (WPS template argument, or runtime when it is 0).
 struct Grp {
@@ -597,16 +628,32 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
             r2 = fma(y, scp[k], r2);
             if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
         }
-        sYW = warp_sum(r1);
-        cp = warp_sum(r2);
-        dcpdT = JAC ? warp_sum(r3) : 0.0;
+        double r4 = 0.0;
+        warp_sum4(r1, r2, r3, r4);
+        sYW = r1;
+        cp = r2;
+        dcpdT = JAC ? r3 : 0.0;
     } else {
-        for (int q = wg; q < (JAC ? 3 : 2); q += NW) {
-            const double *xs = q == 0 ? sInvW : q == 1 ? scp : sJk0;
-            double r = 0.0;
-            for (int k = lane; k < N; k += 32) r = fma(sY[k], xs[k], r);
-            r = warp_sum(r);
-            if (lane == 0) sred[q] = r;
+        if (JAC && NW == 2 && wg == 0) {                // warp 0: sums 0 and 2, reduced together
+            double r = 0.0, u = 0.0;
+            for (int k = lane; k < N; k += 32) {
+                const double y = sY[k];
+                r = fma(y, sInvW[k], r);
+                u = fma(y, sJk0[k], u);
+            }
+            warp_sum2(r, u);
+            if (lane == 0) {
+                sred[0] = r;
+                sred[2] = u;
+            }
+        } else {
+            for (int q = wg; q < (JAC ? 3 : 2); q += NW) {
+                const double *xs = q == 0 ? sInvW : q == 1 ? scp : sJk0;
+                double r = 0.0;
+                for (int k = lane; k < N; k += 32) r = fma(sY[k], xs[k], r);
+                r = warp_sum(r);
+                if (lane == 0) sred[q] = r;
+            }
         }
         group_sync<WPS>(g);
         sYW = sred[0];
@@ -786,20 +833,36 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                 x3 = fma(hk, sJk0[k], x3);
                 x4 = fma(scp[k], sf[k], x4);
             }
-            HA = warp_sum(x1);
-            Hf = warp_sum(x2);
-            HJ0 = warp_sum(x3);
-            CF = warp_sum(x4);
+            warp_sum4(x1, x2, x3, x4);
+            HA = x1;
+            Hf = x2;
+            HJ0 = x3;
+            CF = x4;
         } else {
-            for (int q = wg; q < 4; q += NW) {
-                const double *v = q == 0 ? sA : q == 2 ? sJk0 : sf;
-                double x = 0.0;
+            if (NW == 2) {                              // warp w: sums w and w + 2, reduced together
+                const double *v0 = wg == 0 ? sA : sf, *v1 = wg == 0 ? sJk0 : sf;
+                double x = 0.0, y = 0.0;
                 for (int k = lane; k < N; k += 32) {
-                    const double uk = q == 3 ? scp[k] : sH[k] * sInvW[k];
-                    x = fma(uk, v[k], x);
+                    const double hk = sH[k] * sInvW[k];
+                    x = fma(hk, v0[k], x);
+                    y = fma(wg == 0 ? hk : scp[k], v1[k], y);
                 }
-                x = warp_sum(x);
-                if (lane == 0) sred[4 + q] = x;
+                warp_sum2(x, y);
+                if (lane == 0) {
+                    sred[4 + wg] = x;
+                    sred[6 + wg] = y;
+                }
+            } else {
+                for (int q = wg; q < 4; q += NW) {
+                    const double *v = q == 0 ? sA : q == 2 ? sJk0 : sf;
+                    double x = 0.0;
+                    for (int k = lane; k < N; k += 32) {
+                        const double uk = q == 3 ? scp[k] : sH[k] * sInvW[k];
+                        x = fma(uk, v[k], x);
+                    }
+                    x = warp_sum(x);
+                    if (lane == 0) sred[4 + q] = x;
+                }
             }
             group_sync<WPS>(g);
             HA = sred[4];
