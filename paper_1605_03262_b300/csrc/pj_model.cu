@@ -332,11 +332,12 @@ std::vector<Task> cut_pieces(const std::vector<Task> &tasks, size_t piece_len, s
     return out;
 }
 
-// Piece length that lets the gather lists spread over n_warps warps of 32 lanes.
+// Piece length that lets the gather lists spread over n_warps warps of 32 lanes (at least 2
+// items, so that a piece is never shorter than the combine step it adds).
 size_t piece_length(const std::vector<Task> &tasks, int n_warps) {
     size_t total = 0;
     for (auto &t : tasks) total += t.idx.size();
-    return std::max<size_t>(8, (total + 32 * size_t(n_warps) - 1) / (32 * size_t(n_warps)));
+    return std::max<size_t>(2, (total + 32 * size_t(n_warps) - 1) / (32 * size_t(n_warps)));
 }
 
 int nu_code(double nu) {
