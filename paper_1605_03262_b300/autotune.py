@@ -47,18 +47,21 @@ def _store_cache(cache: Dict[str, list]) -> None:
 
 
 def candidate_shapes(model, which: str = "jacobian") -> List[Shape]:
-    """Every (warps per state, states per CTA, 1) the library accepts for this model."""
+    """Every (warps per state, states per CTA, CTAs per SM) the library accepts for this model:
+    one CTA per SM of up to 512 threads, or two of up to 256 threads (the register file holds
+    512 threads at the kernels' 128 registers)."""
     out = []
-    for wps in (1, 2, 4, 8, 16):
-        for groups in range(1, 17):
-            if wps * 32 * groups > 512 or (wps > 1 and groups > 15):
-                continue
-            try:
-                model.launch_smem_bytes(wps, groups, 1, which=which)
-                model.set_launch(wps, groups, 1, which=which)
-            except Exception:
-                continue
-            out.append((wps, groups, 1))
+    for ctas in (1, 2):
+        for wps in (1, 2, 4, 8, 16):
+            for groups in range(1, 17):
+                if wps * 32 * groups > 512 // ctas or (wps > 1 and groups > 15):
+                    continue
+                try:
+                    model.launch_smem_bytes(wps, groups, ctas, which=which)
+                    model.set_launch(wps, groups, ctas, which=which)
+                except Exception:
+                    continue
+                out.append((wps, groups, ctas))
     return out
 
 
