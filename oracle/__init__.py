@@ -78,6 +78,10 @@ def _bind(lib):
     lib.pjo_jacobian_complex_step.restype = i32
     lib.pjo_jacobian_fd.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
     lib.pjo_jacobian_fd.restype = i32
+    lib.pjo_eval_dydt_cv.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64]
+    lib.pjo_eval_dydt_cv.restype = i32
+    lib.pjo_jacobian_cv.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
+    lib.pjo_jacobian_cv.restype = i32
     lib.pjo_reaction_rates.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
     lib.pjo_reaction_rates.restype = i32
     lib.pjo_species_thermo.argtypes = [vp, ctypes.c_double, dp, dp, dp, dp]
@@ -175,6 +179,28 @@ class OracleModel:
         rc = self._lib.pjo_jacobian_fd(self._h, n, _ptr(T), _ptr(P), _ptr(Y), N, _ptr(J), (N + 1) ** 2, _ptr(Js))
         if rc:
             raise RuntimeError("oracle finite-difference jacobian failed (%d)" % rc)
+        return (J, Js) if with_scale else J
+
+    def dydt_cv(self, T, rho, Y):
+        """Constant-volume source terms {dT/dt, dY_k/dt} of states (T, rho, Y): (n, N+1)."""
+        T, rho, Y = _f64(T).ravel(), _f64(rho).ravel(), _f64(Y)
+        n, N = Y.shape
+        out = np.empty((n, N + 1))
+        rc = self._lib.pjo_eval_dydt_cv(self._h, n, _ptr(T), _ptr(rho), _ptr(Y), N, _ptr(out), N + 1)
+        if rc:
+            raise RuntimeError("oracle constant-volume dydt failed (%d)" % rc)
+        return out
+
+    def jacobian_cv(self, T, rho, Y, with_scale: bool = False):
+        """Constant-volume Jacobian (n, N+1, N+1) by complex-step differentiation of the
+        constant-volume source terms; with_scale also returns the per-entry rounding scale."""
+        T, rho, Y = _f64(T).ravel(), _f64(rho).ravel(), _f64(Y)
+        n, N = Y.shape
+        J = np.empty((n, N + 1, N + 1))
+        Js = np.empty_like(J) if with_scale else None
+        rc = self._lib.pjo_jacobian_cv(self._h, n, _ptr(T), _ptr(rho), _ptr(Y), N, _ptr(J), (N + 1) ** 2, _ptr(Js))
+        if rc:
+            raise RuntimeError("oracle constant-volume jacobian failed (%d)" % rc)
         return (J, Js) if with_scale else J
 
     # -- single-state introspection ------------------------------------------------------------

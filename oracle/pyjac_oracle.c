@@ -731,6 +731,106 @@ int pjo_jacobian_fd(const pjo_mech *m, int64_t n, const double *T, const double 
     return err ? PJO_ENOMEM : PJO_OK;
 }
 
+/* ---------------------------------------------------------------------------------------------
+ * Constant volume (Section 3.3): source terms of the state (T, rho, Y), and their Jacobian by the
+ * plain definition, d f / d y along the analytical columns (T; Y_j with Y_N = 1 - sum of the
+ * others; column N zero), evaluated by complex-step differentiation of the source terms. The
+ * optional per-entry scale bounds the rounding of an entry: (W_k/rho) sum_i |nu_ki| (|d(c R_f)_i|
+ * + |d(c R_r)_i|) for species rows, and for the energy row the same sums weighted by |u_k W_k|
+ * plus |du_k W_k omega_k| and |f_0 dc_v|, over rho c_v. */
+int pjo_eval_dydt_cv(const pjo_mech *m, int64_t n, const double *T, const double *rho, const double *Y, int64_t ldy,
+                     double *dydt, int64_t ldd)
+{
+    if (!m || n < 0 || ldy < m->ns || ldd < m->ns + 1) return PJO_EINVAL;
+    if (n == 0) return PJO_OK;
+    if (!T || !rho || !Y || !dydt) return PJO_EINVAL;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(pjo_max_threads())
+    for (int64_t s = 0; s < n; ++s) {
+        double *wk = malloc((6 * (size_t)m->ns + 2 * (size_t)m->nr + 8) * sizeof(double));
+        if (!wk) { err = 1; continue; }
+        source_terms_cv_d(m, T[s], rho[s], Y + s * ldy, dydt + s * ldd, NULL, NULL, wk);
+        free(wk);
+    }
+    return err ? PJO_ENOMEM : PJO_OK;
+}
+
+int pjo_jacobian_cv(const pjo_mech *m, int64_t n, const double *T, const double *rho, const double *Y, int64_t ldy,
+                    double *jac, int64_t ldj, double *jac_scale)
+{
+    if (!m || n < 0 || ldy < m->ns) return PJO_EINVAL;
+    const int N = m->ns, R = m->nr;
+    if (ldj < (int64_t)(N + 1) * (N + 1)) return PJO_EINVAL;
+    if (n == 0) return PJO_OK;
+    if (!T || !rho || !Y || !jac) return PJO_EINVAL;
+    const double h = 1e-30;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(pjo_max_threads())
+    for (int64_t s = 0; s < n; ++s) {
+        size_t nz = (size_t)N + (N + 1) + 2 * (size_t)R + 6 * (size_t)N + 2 * (size_t)R + 8;
+        size_t nd = (size_t)(N + 1) + 2 * (size_t)R + 6 * (size_t)N + 2 * (size_t)R + 8 + 3 * (size_t)N;
+        double complex *Yz = malloc(nz * sizeof(double complex));
+        double *bd = malloc(nd * sizeof(double));
+        if (!Yz || !bd) { free(Yz); free(bd); err = 1; continue; }
+        double complex *fz = Yz + N, *qfz = fz + N + 1, *qrz = qfz + R, *wkz = qrz + R;
+        double *f = bd, *qf = f + N + 1, *qr = qf + R, *wk = qr + R, *cvk = wk + 6 * (size_t)N + 2 * (size_t)R + 8,
+               *uk = cvk + N, *dcvk = uk + N;
+        const double *Ys = Y + s * ldy;
+        const double r0 = rho[s];
+        double *Jo = jac + s * ldj, *Jso = jac_scale ? jac_scale + s * ldj : NULL;
+        source_terms_cv_d(m, T[s], r0, Ys, f, qf, qr, wk);
+        /* base-state thermo for the energy-row scale: c_v,k, u_k and dc_v,k/dT (complex step) */
+        double cv = 0.0;
+        for (int k = 0; k < N; ++k) {
+            double complex cpR, HRT, SR;
+            nasa7_z(m, k, T[s] + I * h, &cpR, &HRT, &SR);
+            cvk[k] = (creal(cpR) - 1.0) * PJO_R / m->W[k];
+            uk[k] = (creal(HRT) - 1.0) * PJO_R * T[s] / m->W[k];
+            dcvk[k] = cimag(cpR) / h * PJO_R / m->W[k];
+            cv += Ys[k] * cvk[k];
+        }
+        for (int col = 0; col < N + 1; ++col) {
+            if (col == N) {
+                for (int row = 0; row < N + 1; ++row) {
+                    Jo[(size_t)row * (N + 1) + col] = 0.0;
+                    if (Jso) Jso[(size_t)row * (N + 1) + col] = 0.0;
+                }
+                continue;
+            }
+            double complex Tz = T[s];
+            for (int k = 0; k < N; ++k) Yz[k] = Ys[k];
+            if (col == 0) Tz += I * h;
+            else { Yz[col - 1] += I * h; Yz[N - 1] -= I * h; }
+            source_terms_cv_z(m, Tz, r0, Yz, fz, qfz, qrz, wkz);
+            for (int row = 0; row < N + 1; ++row) Jo[(size_t)row * (N + 1) + col] = cimag(fz[row]) / h;
+            if (!Jso) continue;
+            /* scales: sum_i |nu_ki| (|d qf_i| + |d qr_i|) per species */
+            double *sk = wk;                                       /* reuse: N entries */
+            for (int k = 0; k < N; ++k) sk[k] = 0.0;
+            for (int i = 0; i < R; ++i) {
+                const pjo_rxn *r = &m->rx[i];
+                const double d = fabs(cimag(qfz[i]) / h) + fabs(cimag(qrz[i]) / h);
+                for (int q = 0; q < r->nnet; ++q) sk[r->netsp[q]] += fabs(r->netnu[q]) * d;
+            }
+            double e0 = 0.0;
+            for (int k = 0; k < N; ++k) {
+                Jso[(size_t)(1 + k) * (N + 1) + col] = m->W[k] / r0 * sk[k];
+                const double omk = f[1 + k] * r0 / m->W[k];
+                e0 += fabs(uk[k] * m->W[k]) * sk[k] + (col == 0 ? fabs(cvk[k] * m->W[k] * omk) : 0.0);
+            }
+            double dcv = 0.0;
+            if (col == 0)
+                for (int k = 0; k < N; ++k) dcv += Ys[k] * dcvk[k];
+            else
+                dcv = cvk[col - 1] - cvk[N - 1];
+            Jso[col] = e0 / (r0 * cv) + fabs(f[0] * dcv) / cv;
+        }
+        free(Yz);
+        free(bd);
+    }
+    return err ? PJO_ENOMEM : PJO_OK;
+}
+
 /* Complex-step Jacobian of the templated source terms: column 0 from T + i h, column j from
  * Y_j + i h, Y_N - i h (j = 1..N-1); column N is zero. Exact to rounding for analytic f. */
 int pjo_jacobian_complex_step(const pjo_mech *m, int64_t n, const double *T, const double *P, const double *Y,

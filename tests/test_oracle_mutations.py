@@ -32,7 +32,7 @@ MUTANTS = [
     ("source_terms.inc", "a[2] / 6.0", "a[2] / 3.0"),
     ("source_terms.inc", "(log(P) - log(a[0])) / (log(b[0]) - log(a[0]))",
      "(log(P) - log(b[0])) / (log(b[0]) - log(a[0]))"),
-    ("source_terms.inc", "FN(chebT)(i, Tt) * FN(chebT)(j, (SCALAR)pt)", "FN(chebT)(j, Tt) * FN(chebT)(i, (SCALAR)pt)"),
+    ("source_terms.inc", "FN(chebT)(i, Tt) * FN(chebT)(j, pt)", "FN(chebT)(j, Tt) * FN(chebT)(i, pt)"),
     ("pyjac_oracle.c", "-(cpk[j] - cpk[L]) / (rho * cp) * HWO", "-(cpk[j] - cpk[0]) / (rho * cp) * HWO"),
     ("pyjac_oracle.c", "dkr = (dkf * Kc - dKc * kf) / (Kc * Kc);", "dkr = (dkf * Kc + dKc * kf) / (Kc * Kc);"),
     ("pyjac_oracle.c", "acc_d(&row[1 + j], &cmp[1 + j], om[k] * Wm * Dl[j]);",
@@ -42,13 +42,17 @@ MUTANTS = [
     ("pyjac_oracle.c", "*dFdT_Pr = Fv * (e / T + X", "*dFdT_Pr = Fv * (e * T + X"),
     ("pyjac_oracle.c", "else                        dcdY = c * (-1.0 / (1.0 + Pr) * dPrdY + dFdY / Fv);",
      "else                        dcdY = c * (1.0 / (1.0 + Pr) * dPrdY + dFdY / Fv);"),
-    ("source_terms.inc", "f[1 + k] = m->W[k] * w / rho;", "f[1 + k] = w / rho;"),
+    ("source_terms.inc", "f[1 + k] = m->W[k] * w / rho;\n        FN(acc)(&hs", "f[1 + k] = w / rho;\n        FN(acc)(&hs"),
     ("source_terms.inc", "pow(PJO_PATM / PJO_R, (double)dn)", "pow(PJO_R / PJO_PATM, (double)dn)"),
     ("source_terms.inc", "for (int s = 0; s < r->np; ++s) Prr *= FN(ipow)(C[r->psp[s]], r->pnu[s]);",
      "for (int s = 0; s < r->np; ++s) Prr *= C[r->psp[s]];"),
     ("pyjac_oracle.c", "cs_add(&s, hk[k] * J[(size_t)(1 + k) * ld + 0]);", "cs_add(&s, hk[k] * J[(size_t)(1 + k) * ld + 1]);"),
     ("source_terms.inc", "c = Pr / (1.0 + Pr) * F; kf = ki;", "c = Pr / (1.0 + Pr) * F; kf = k0;"),
     ("pyjac_oracle.c", "return kf / T * (r->kinf[1] + r->kinf[2] / T);", "return kf / T * (r->k0[1] + r->k0[2] / T);"),
+    ("source_terms.inc", "cv_k[k] = (cpR - 1.0) * PJO_R / m->W[k];", "cv_k[k] = cpR * PJO_R / m->W[k];"),
+    ("source_terms.inc", "u_k[k] = (HRT - 1.0) * PJO_R * T / m->W[k];", "u_k[k] = HRT * PJO_R * T / m->W[k];"),
+    ("source_terms.inc", "SCALAR P = rho * (sYW + sYWc) * PJO_R * T;", "SCALAR P = rho * PJO_R * T;"),
+    ("pyjac_oracle.c", "else { Yz[col - 1] += I * h; Yz[N - 1] -= I * h; }", "else { Yz[col - 1] += I * h; }"),
 ]
 
 EPS = 2.0 ** -52
@@ -125,6 +129,45 @@ def _pins(lib) -> list:
     kf = om2.reaction_rates(Tq, Pq, np.array([0.3, 0.3, 0.4]))["kf"][0]
     if abs(math.log10(kf) - np.polynomial.chebyshev.chebval2d(Tt, pt, eta)) > 1e-12:
         failed.append("chebyshev")
+    # 5. constant volume at the density of the same states: equal species rates, the energy
+    #    identity c_v f0 + sum_k u_k f_k = 0, and two Jacobian columns against central differences
+    #    (the rates on a model with every reaction type, so that pressure-dependent ones see p)
+    mixed = mechs.mixed_model(seed=3, n_species=9, n_reactions=30)
+    omm = oracle.load_model(synth.to_bytes(mixed), lib=lib)
+    Tm, Pm, Ym = synth.generate_states(mixed.n_species, 6, seed=13)
+    rm = Pm / (R_GAS * Tm * (Ym / np.array([s.W for s in mixed.species])).sum(axis=1))
+    fcp, fcvm = omm.dydt(Tm, Pm, Ym), omm.dydt_cv(Tm, rm, Ym)
+    if not np.all(np.abs(fcvm[:, 1:] - fcp[:, 1:]) <= 1e-13 * np.abs(fcp[:, 1:]).max(axis=1, keepdims=True)):
+        failed.append("cv rates")
+    Wk = np.array([s.W for s in model.species])
+    rho = P / (R_GAS * T * (Y / Wk).sum(axis=1))
+    fcv = om.dydt_cv(T, rho, Y)
+    for s in range(2):
+        a = [(sp.a_low if T[s] < sp.T_mid else sp.a_high) for sp in model.species]
+        u = np.array([R_GAS / sp.W * (_H_quad(a[i], T[s]) - T[s]) for i, sp in enumerate(model.species)])
+        cvk = np.array([R_GAS / sp.W * (np.polynomial.polynomial.polyval(T[s], a[i][:5]) - 1.0)
+                        for i, sp in enumerate(model.species)])
+        if abs(np.sum(u * fcv[s, 1:]) + (Y[s] @ cvk) * fcv[s, 0]) > 1e-11 * np.abs(u * fcv[s, 1:]).sum():
+            failed.append("cv energy")
+            break
+    Jcv = om.jacobian_cv(T[:1], rho[:1], Y[:1])[0]
+    N = model.n_species
+    for col in (0, 1):
+        h = 1e-3 * (T[0] if col == 0 else min(Y[0, 0], Y[0, N - 1]))
+        fd = []
+        for st in (-2, -1, 1, 2):
+            Tp, Yp = T[:1].copy(), Y[:1].copy()
+            if col == 0:
+                Tp += st * h
+            else:
+                Yp[0, 0] += st * h
+                Yp[0, N - 1] -= st * h
+            fd.append(om.dydt_cv(Tp, rho[:1], Yp)[0])
+        d = (fd[0] - 8 * fd[1] + 8 * fd[2] - fd[3]) / (12 * h)
+        big = np.abs(Jcv[:, col]) > 1e-3 * np.abs(Jcv[:, col]).max()
+        if not np.all(np.abs(d - Jcv[:, col])[big] <= 1e-5 * np.abs(Jcv[big, col])):
+            failed.append("cv jacobian")
+            break
     return failed
 
 

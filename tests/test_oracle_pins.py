@@ -339,7 +339,7 @@ def test_jacobian_matches_central_differences():
         fT = [om.dydt([T[s] + a * hT], [P[s]], Y[s][None])[0] for a in (-2, -1, 1, 2)]
         Jfd[:, 0] = (fT[0] - 8 * fT[1] + 8 * fT[2] - fT[3]) / (12 * hT)
         for j in range(N - 1):
-            h = 1e-4 * min(Y[s, j], Y[s, N - 1])
+            h = 1e-3 * min(Y[s, j], Y[s, N - 1])
             fs_ = []
             for a in (-2, -1, 1, 2):
                 Yp = Y[s].copy()
@@ -464,3 +464,101 @@ def test_forward_difference_increment_rule():
             Yp[0, N - 1] -= h
         col = (om.dydt(Tp, P, Yp)[0] - f0) / h
         assert np.all(np.abs(col - Jfd[0, :, c]) <= 64 * EPS * Jsc[0, :, c] + 1e-300)
+
+
+# ---------------------------------------------------------------------------------------------
+# constant volume (Section 3.3)
+
+def _rho(model, T, P, Y):
+    W = 1.0 / (Y / np.array([s.W for s in model.species])).sum(axis=1)
+    return P * W / (R_GAS * T)
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_constant_volume_species_rates_equal_constant_pressure_rates(cfg):
+    """At the density of the same state, dY_k/dt does not depend on which variable is held fixed
+    (both are W_k omega_k / rho); the temperature rates are tied by c_p - c_v = R/W per species:
+    c_v f0_cv + sum_k u_k f_k = 0 and c_p f0_cp + sum_k h_k f_k = 0 with h_k = u_k + R T / W_k."""
+    model = synth.config_model(cfg)
+    om = _om(model)
+    T, P, Y = synth.config_states(cfg, 6, seed_offset=3)
+    rho = _rho(model, T, P, Y)
+    fcv, fcp = om.dydt_cv(T, rho, Y), om.dydt(T, P, Y)
+    scale = np.abs(fcp[:, 1:]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(fcv[:, 1:] - fcp[:, 1:]) <= 1e-13 * scale)
+    W = np.array([s.W for s in model.species])
+    for s in range(len(T)):
+        cpk = np.array([np.polynomial.polynomial.polyval(T[s], _coeffs(sp, T[s])[:5]) for sp in model.species]) * R_GAS / W
+        cvk = cpk - R_GAS / W
+        cp, cv = (Y[s] * cpk).sum(), (Y[s] * cvk).sum()
+        sum_hf = -cp * fcp[s, 0]                                   # sum_k h_k f_k
+        sum_uf = sum_hf - R_GAS * T[s] * (fcp[s, 1:] / W).sum()    # sum_k u_k f_k
+        assert abs(cv * fcv[s, 0] + sum_uf) <= 1e-9 * (abs(sum_hf) + abs(cv * fcv[s, 0]))
+
+
+def test_constant_volume_jacobian_matches_central_differences():
+    """The complex-step constant-volume Jacobian against fourth-order central differences of the
+    constant-volume source terms, on the entries the differences resolve: well-conditioned ones
+    whose difference-quotient rounding (~30 eps S_f / h, S_f the source-term scale of the row,
+    equal at constant pressure) is below 1e-7 |J|. There the two agree to ~1e-12 typically; a
+    dropped or mis-signed term shows up as an O(1) relative error."""
+    model = mechs.mixed_model(seed=33)
+    om = _om(model)
+    T, P, Y = synth.generate_states(model.n_species, 5, seed=34)
+    T = np.where(np.abs(T - 1000.0) < 50.0, T + 120.0, T)
+    rho = _rho(model, T, P, Y)
+    J, Js = om.jacobian_cv(T, rho, Y, with_scale=True)
+    _, _, _, fs = om.jacobian(T, P, Y, with_scale=True)
+    N = model.n_species
+    for s in range(len(T)):
+        Jfd = np.zeros((N + 1, N + 1))
+        steps = np.empty(N + 1)
+        hT = 1e-3 * T[s]
+        steps[0] = hT
+        fT = [om.dydt_cv([T[s] + a * hT], [rho[s]], Y[s][None])[0] for a in (-2, -1, 1, 2)]
+        Jfd[:, 0] = (fT[0] - 8 * fT[1] + 8 * fT[2] - fT[3]) / (12 * hT)
+        for j in range(N - 1):
+            h = 1e-3 * min(Y[s, j], Y[s, N - 1])
+            steps[1 + j] = h
+            fs_ = []
+            for a in (-2, -1, 1, 2):
+                Yp = Y[s].copy()
+                Yp[j] += a * h
+                Yp[N - 1] -= a * h
+                fs_.append(om.dydt_cv([T[s]], [rho[s]], Yp[None])[0])
+            Jfd[:, 1 + j] = (fs_[0] - 8 * fs_[1] + 8 * fs_[2] - fs_[3]) / (12 * h)
+        steps[N] = np.inf
+        fd_round = 30 * EPS * fs[s][:, None] / steps[None, :]
+        well = (Js[s] <= 100.0 * np.abs(J[s])) & (np.abs(J[s]) > 1e-12 * np.abs(J[s]).max()) & \
+            (fd_round <= 1e-7 * np.abs(J[s]))
+        rel = np.abs(J[s] - Jfd)[well] / np.abs(J[s])[well]
+        assert well.sum() >= 10 and well[:, 0].any() and well[0, :].any() and well[1:, 1:].any()
+        assert np.median(rel) < 1e-10
+        assert rel.max() < 1e-7
+    assert np.all(J[:, :, -1] == 0.0)
+    assert np.all(np.abs(J[:, 1:, :].sum(axis=1)) <= 1e-12 * np.abs(J[:, 1:, :]).sum(axis=1) + 1e-300)
+
+
+def test_constant_volume_jacobian_is_sparse_for_elementary_reactions():
+    """Section 3.3: with the density fixed, a species row k has entries only in the columns of the
+    species it reacts with directly (columns move Y_j against Y_N, so those of N's partners too);
+    the constant-pressure Jacobian of the same model is dense through d rho / d Y_j."""
+    model = mechs.typed_model("elementary", seed=35, n_species=10, n_reactions=6, rev_modes=(1,))
+    om = _om(model)
+    N = model.n_species
+    T, P, Y = synth.generate_states(N, 3, seed=36)
+    Jcv = om.jacobian_cv(T, _rho(model, T, P, Y), Y)
+    Jcp, _ = om.jacobian(T, P, Y)
+    partners = [set() for _ in range(N)]
+    for r in model.reactions:
+        sps = {s for s, _ in r.reac} | {s for s, _ in r.prod}
+        for k in sps:
+            partners[k] |= sps
+    zero = 0
+    for k in range(N):
+        for j in range(N - 1):
+            if j not in partners[k] and (N - 1) not in partners[k]:
+                assert np.all(Jcv[:, 1 + k, 1 + j] == 0.0)
+                assert np.all(Jcp[:, 1 + k, 1 + j] != 0.0) or not any(partners[k])
+                zero += 1
+    assert zero > 0
