@@ -109,6 +109,22 @@ PJ_API int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const 
                      int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream);
 
 /*
+ * Constant-volume form (Section 3.3: the density is held fixed instead of the pressure). State
+ * (T, rho, Y): rho[n] in kg/m^3 replaces P[n]; p = rho R T / W follows from the ideal-gas law
+ * (Eq. e:state) for the pressure-dependent rates, and [X_k] = rho Y_k / W_k. Source terms:
+ * dY_k/dt = W_k omega_k / rho as at constant pressure, and dT/dt = -sum_k u_k W_k omega_k / (rho c_v)
+ * with the mass-specific internal energies u_k = h_k - R T / W_k and c_v = sum_k Y_k (c_p,k - R/W_k).
+ * The Jacobian is d(T, Y_1..Y_N)/dt with respect to (T, Y_1..Y_N) at fixed rho, in the same layout
+ * and column convention as pj_eval_jacobian (columns j move Y_j against Y_N; column N is zero).
+ * Same argument, pointer and error rules as pj_eval_dydt / pj_eval_jacobian, with the same launch
+ * shapes (pj_set_launch applies to both forms).
+ */
+PJ_API int pj_eval_dydt_cv(const pj_mech *m, int64_t n, const double *T, const double *rho, const double *Y,
+                           int64_t ldy, double *dydt, int64_t ldd, void *stream);
+PJ_API int pj_eval_jacobian_cv(const pj_mech *m, int64_t n, const double *T, const double *rho, const double *Y,
+                               int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream);
+
+/*
  * End-to-end variant of pj_eval_jacobian on HOST buffers (pinned host memory gives full copy
  * bandwidth; pageable memory works but is slower). The states are processed in chunks of
  * chunk_states (<= 0: the library picks); each chunk is copied to the device, evaluated and copied

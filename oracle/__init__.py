@@ -78,7 +78,7 @@ def _bind(lib):
     lib.pjo_jacobian_complex_step.restype = i32
     lib.pjo_jacobian_fd.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
     lib.pjo_jacobian_fd.restype = i32
-    lib.pjo_eval_dydt_cv.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64]
+    lib.pjo_eval_dydt_cv.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
     lib.pjo_eval_dydt_cv.restype = i32
     lib.pjo_jacobian_cv.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
     lib.pjo_jacobian_cv.restype = i32
@@ -181,15 +181,17 @@ class OracleModel:
             raise RuntimeError("oracle finite-difference jacobian failed (%d)" % rc)
         return (J, Js) if with_scale else J
 
-    def dydt_cv(self, T, rho, Y):
-        """Constant-volume source terms {dT/dt, dY_k/dt} of states (T, rho, Y): (n, N+1)."""
+    def dydt_cv(self, T, rho, Y, with_scale: bool = False):
+        """Constant-volume source terms {dT/dt, dY_k/dt} of states (T, rho, Y): (n, N+1); with
+        with_scale also the per-entry sum of the absolute values of the terms."""
         T, rho, Y = _f64(T).ravel(), _f64(rho).ravel(), _f64(Y)
         n, N = Y.shape
         out = np.empty((n, N + 1))
-        rc = self._lib.pjo_eval_dydt_cv(self._h, n, _ptr(T), _ptr(rho), _ptr(Y), N, _ptr(out), N + 1)
+        sc = np.empty_like(out) if with_scale else None
+        rc = self._lib.pjo_eval_dydt_cv(self._h, n, _ptr(T), _ptr(rho), _ptr(Y), N, _ptr(out), N + 1, _ptr(sc))
         if rc:
             raise RuntimeError("oracle constant-volume dydt failed (%d)" % rc)
-        return out
+        return (out, sc) if with_scale else out
 
     def jacobian_cv(self, T, rho, Y, with_scale: bool = False):
         """Constant-volume Jacobian (n, N+1, N+1) by complex-step differentiation of the

@@ -734,22 +734,47 @@ int pjo_jacobian_fd(const pjo_mech *m, int64_t n, const double *T, const double 
 /* ---------------------------------------------------------------------------------------------
  * Constant volume (Section 3.3): source terms of the state (T, rho, Y), and their Jacobian by the
  * plain definition, d f / d y along the analytical columns (T; Y_j with Y_N = 1 - sum of the
- * others; column N zero), evaluated by complex-step differentiation of the source terms. The
- * optional per-entry scale bounds the rounding of an entry: (W_k/rho) sum_i |nu_ki| (|d(c R_f)_i|
- * + |d(c R_r)_i|) for species rows, and for the energy row the same sums weighted by |u_k W_k|
- * plus |du_k W_k omega_k| and |f_0 dc_v|, over rho c_v. */
+ * others; column N zero), evaluated by complex-step differentiation of the source terms. A species
+ * column is the difference of two one-species directional derivatives, d f / d Y_j - d f / d Y_N
+ * (the same linear map as one step along Y_j - Y_N); the optional per-entry scale bounds the
+ * rounding of an entry: (W_k/rho) sum_i |nu_ki| (|d(c R_f)_i| + |d(c R_r)_i|) summed over the
+ * column's directions (T alone, or Y_j and Y_N separately, so that an entry formed from two large
+ * and nearly equal contributions, e.g. through 1/W_j - 1/W_N for W_j close to W_N, carries their
+ * size), and for the energy row the same sums weighted by |u_k W_k| plus |du_k W_k omega_k| and
+ * |f_0 dc_v|, over rho c_v. */
 int pjo_eval_dydt_cv(const pjo_mech *m, int64_t n, const double *T, const double *rho, const double *Y, int64_t ldy,
-                     double *dydt, int64_t ldd)
+                     double *dydt, int64_t ldd, double *dydt_scale)
 {
     if (!m || n < 0 || ldy < m->ns || ldd < m->ns + 1) return PJO_EINVAL;
     if (n == 0) return PJO_OK;
     if (!T || !rho || !Y || !dydt) return PJO_EINVAL;
+    const int N = m->ns, R = m->nr;
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 4) num_threads(pjo_max_threads())
     for (int64_t s = 0; s < n; ++s) {
-        double *wk = malloc((6 * (size_t)m->ns + 2 * (size_t)m->nr + 8) * sizeof(double));
+        double *wk = malloc((6 * (size_t)N + 2 * (size_t)R + 8 + 2 * (size_t)R + N) * sizeof(double));
         if (!wk) { err = 1; continue; }
-        source_terms_cv_d(m, T[s], rho[s], Y + s * ldy, dydt + s * ldd, NULL, NULL, wk);
+        double *qf = wk + 6 * (size_t)N + 2 * (size_t)R + 8, *qr = qf + R, *sk = qr + R;
+        const double *Ys = Y + s * ldy;
+        source_terms_cv_d(m, T[s], rho[s], Ys, dydt + s * ldd, qf, qr, wk);
+        if (dydt_scale) {
+            /* per entry: the sum of the absolute values of its terms, sum_i |nu_ki| (|c R_f| + |c R_r|)
+             * for species k (times W_k / rho), and sum_k |u_k W_k| of those over rho c_v for T;
+             * c_v,k and u_k are left in wk by the source terms */
+            const double *cvk = wk + 2 * (size_t)N, *uk = wk + 3 * (size_t)N;
+            double cv = 0.0;
+            for (int k = 0; k < N; ++k) { sk[k] = 0.0; cv += Ys[k] * cvk[k]; }
+            for (int i = 0; i < R; ++i) {
+                const pjo_rxn *r = &m->rx[i];
+                for (int q = 0; q < r->nnet; ++q) sk[r->netsp[q]] += fabs(r->netnu[q]) * (fabs(qf[i]) + fabs(qr[i]));
+            }
+            double *sc = dydt_scale + s * ldd, e0 = 0.0;
+            for (int k = 0; k < N; ++k) {
+                sc[1 + k] = m->W[k] / rho[s] * sk[k];
+                e0 += fabs(uk[k] * m->W[k]) * sk[k];
+            }
+            sc[0] = e0 / (rho[s] * cv);
+        }
         free(wk);
     }
     return err ? PJO_ENOMEM : PJO_OK;
@@ -767,14 +792,16 @@ int pjo_jacobian_cv(const pjo_mech *m, int64_t n, const double *T, const double 
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(pjo_max_threads())
     for (int64_t s = 0; s < n; ++s) {
-        size_t nz = (size_t)N + (N + 1) + 2 * (size_t)R + 6 * (size_t)N + 2 * (size_t)R + 8;
-        size_t nd = (size_t)(N + 1) + 2 * (size_t)R + 6 * (size_t)N + 2 * (size_t)R + 8 + 3 * (size_t)N;
+        const size_t nwk = 6 * (size_t)N + 2 * (size_t)R + 8;
+        size_t nz = (size_t)N + (N + 1) + 2 * (size_t)R + nwk;
+        /* f, qf, qr, wk; c_v,k, u_k, dc_v,k/dT; the Y_N direction: d f, |d(cR_f)|, |d(cR_r)|; sk */
+        size_t nd = (size_t)(N + 1) + 2 * (size_t)R + nwk + 3 * (size_t)N + (size_t)(N + 1) + 2 * (size_t)R + N;
         double complex *Yz = malloc(nz * sizeof(double complex));
         double *bd = malloc(nd * sizeof(double));
         if (!Yz || !bd) { free(Yz); free(bd); err = 1; continue; }
         double complex *fz = Yz + N, *qfz = fz + N + 1, *qrz = qfz + R, *wkz = qrz + R;
-        double *f = bd, *qf = f + N + 1, *qr = qf + R, *wk = qr + R, *cvk = wk + 6 * (size_t)N + 2 * (size_t)R + 8,
-               *uk = cvk + N, *dcvk = uk + N;
+        double *f = bd, *qf = f + N + 1, *qr = qf + R, *wk = qr + R, *cvk = wk + nwk, *uk = cvk + N, *dcvk = uk + N;
+        double *dfN = dcvk + N, *aqfN = dfN + N + 1, *aqrN = aqfN + R, *sk = aqrN + R;
         const double *Ys = Y + s * ldy;
         const double r0 = rho[s];
         double *Jo = jac + s * ldj, *Jso = jac_scale ? jac_scale + s * ldj : NULL;
@@ -789,6 +816,15 @@ int pjo_jacobian_cv(const pjo_mech *m, int64_t n, const double *T, const double 
             dcvk[k] = cimag(cpR) / h * PJO_R / m->W[k];
             cv += Ys[k] * cvk[k];
         }
+        /* one step along Y_N: its derivative enters every species column */
+        for (int k = 0; k < N; ++k) Yz[k] = Ys[k];
+        Yz[N - 1] += I * h;
+        source_terms_cv_z(m, T[s], r0, Yz, fz, qfz, qrz, wkz);
+        for (int row = 0; row < N + 1; ++row) dfN[row] = cimag(fz[row]) / h;
+        for (int i = 0; i < R; ++i) {
+            aqfN[i] = fabs(cimag(qfz[i]) / h);
+            aqrN[i] = fabs(cimag(qrz[i]) / h);
+        }
         for (int col = 0; col < N + 1; ++col) {
             if (col == N) {
                 for (int row = 0; row < N + 1; ++row) {
@@ -800,16 +836,17 @@ int pjo_jacobian_cv(const pjo_mech *m, int64_t n, const double *T, const double 
             double complex Tz = T[s];
             for (int k = 0; k < N; ++k) Yz[k] = Ys[k];
             if (col == 0) Tz += I * h;
-            else { Yz[col - 1] += I * h; Yz[N - 1] -= I * h; }
+            else Yz[col - 1] += I * h;
             source_terms_cv_z(m, Tz, r0, Yz, fz, qfz, qrz, wkz);
-            for (int row = 0; row < N + 1; ++row) Jo[(size_t)row * (N + 1) + col] = cimag(fz[row]) / h;
+            for (int row = 0; row < N + 1; ++row)
+                Jo[(size_t)row * (N + 1) + col] = cimag(fz[row]) / h - (col == 0 ? 0.0 : dfN[row]);
             if (!Jso) continue;
-            /* scales: sum_i |nu_ki| (|d qf_i| + |d qr_i|) per species */
-            double *sk = wk;                                       /* reuse: N entries */
+            /* scales: sum_i |nu_ki| (|d qf_i| + |d qr_i|) per species, over the column's directions */
             for (int k = 0; k < N; ++k) sk[k] = 0.0;
             for (int i = 0; i < R; ++i) {
                 const pjo_rxn *r = &m->rx[i];
-                const double d = fabs(cimag(qfz[i]) / h) + fabs(cimag(qrz[i]) / h);
+                double d = fabs(cimag(qfz[i]) / h) + fabs(cimag(qrz[i]) / h);
+                if (col > 0) d += aqfN[i] + aqrN[i];
                 for (int q = 0; q < r->nnet; ++q) sk[r->netsp[q]] += fabs(r->netnu[q]) * d;
             }
             double e0 = 0.0;
@@ -820,10 +857,10 @@ int pjo_jacobian_cv(const pjo_mech *m, int64_t n, const double *T, const double 
             }
             double dcv = 0.0;
             if (col == 0)
-                for (int k = 0; k < N; ++k) dcv += Ys[k] * dcvk[k];
+                for (int k = 0; k < N; ++k) dcv += fabs(Ys[k] * dcvk[k]);
             else
-                dcv = cvk[col - 1] - cvk[N - 1];
-            Jso[col] = e0 / (r0 * cv) + fabs(f[0] * dcv) / cv;
+                dcv = fabs(cvk[col - 1]) + fabs(cvk[N - 1]);
+            Jso[col] = e0 / (r0 * cv) + fabs(f[0]) * dcv / cv;
         }
         free(Yz);
         free(bd);

@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
             "pj_mech_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(sz)], i32),
             "pj_eval_dydt": ([vp, i64, vp, vp, vp, i64, vp, i64, vp], i32),
             "pj_eval_jacobian": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
+            "pj_eval_dydt_cv": ([vp, i64, vp, vp, vp, i64, vp, i64, vp], i32),
+            "pj_eval_jacobian_cv": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
             "pj_fd_workspace_bytes": ([vp, i64, ctypes.POINTER(sz)], i32),
             "pj_eval_jacobian_fd": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, sz, vp], i32),
             "pj_eval_jacobian_host": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, i64], i32),
@@ -199,17 +201,30 @@ class Model:
 
     def eval_dydt(self, T, P, Y, out=None, stream=None):
         """Source terms {dT/dt, dY_1/dt..dY_N/dt} for every state: (n, N+1) float64 CUDA tensor."""
+        return self._dydt(library().pj_eval_dydt, T, P, Y, out, stream)
+
+    def eval_jacobian(self, T, P, Y, out=None, dydt: bool = False, dydt_out=None, stream=None):
+        """Analytical Jacobian (n, N+1, N+1) [, dydt (n, N+1)] as float64 CUDA tensors."""
+        return self._jacobian(library().pj_eval_jacobian, T, P, Y, out, dydt, dydt_out, stream)
+
+    def eval_dydt_cv(self, T, rho, Y, out=None, stream=None):
+        """Constant-volume source terms (states given by T, density rho, Y): (n, N+1) float64."""
+        return self._dydt(library().pj_eval_dydt_cv, T, rho, Y, out, stream)
+
+    def eval_jacobian_cv(self, T, rho, Y, out=None, dydt: bool = False, dydt_out=None, stream=None):
+        """Constant-volume analytical Jacobian (n, N+1, N+1) [, dydt (n, N+1)] at fixed density."""
+        return self._jacobian(library().pj_eval_jacobian_cv, T, rho, Y, out, dydt, dydt_out, stream)
+
+    def _dydt(self, fn, T, P, Y, out, stream):
         torch = _torch()
         T, P, Y, n = self._inputs(T, P, Y)
         N = self.n_species
         if out is None:
             out = torch.empty((n, N + 1), dtype=torch.float64, device=self.device)
-        _check(library().pj_eval_dydt(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out),
-                                      out.stride(0), _stream_handle(stream)))
+        _check(fn(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out), out.stride(0), _stream_handle(stream)))
         return out
 
-    def eval_jacobian(self, T, P, Y, out=None, dydt: bool = False, dydt_out=None, stream=None):
-        """Analytical Jacobian (n, N+1, N+1) [, dydt (n, N+1)] as float64 CUDA tensors."""
+    def _jacobian(self, fn, T, P, Y, out, dydt, dydt_out, stream):
         torch = _torch()
         T, P, Y, n = self._inputs(T, P, Y)
         N = self.n_species
@@ -219,8 +234,8 @@ class Model:
         f = None
         if dydt or dydt_out is not None:
             f = dydt_out if dydt_out is not None else torch.empty((n, N + 1), dtype=torch.float64, device=self.device)
-        _check(library().pj_eval_jacobian(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out), ldj,
-                                          _ptr(f), f.stride(0) if f is not None else 0, _stream_handle(stream)))
+        _check(fn(self._h, n, _ptr(T), _ptr(P), _ptr(Y), Y.stride(0), _ptr(out), ldj, _ptr(f),
+                  f.stride(0) if f is not None else 0, _stream_handle(stream)))
         return (out, f) if f is not None else out
 
     def fd_workspace_bytes(self, n: int) -> int:

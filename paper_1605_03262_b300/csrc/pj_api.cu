@@ -114,8 +114,9 @@ size_t push(std::vector<char> &blob, const std::vector<T> &v) {
     return off;
 }
 
-int launch(const pj_mech *m, bool jac, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
-           double *jacp, int64_t ldj, double *dydt, int64_t ldd, cudaStream_t stream) {
+// P holds pressures (constant-pressure form) or densities (cv: constant-volume form).
+int launch(const pj_mech *m, bool jac, bool cv, int64_t n, const double *T, const double *P, const double *Y,
+           int64_t ldy, double *jacp, int64_t ldj, double *dydt, int64_t ldd, cudaStream_t stream) {
     const pj::LaunchCfg &c = jac ? m->jac_cfg : m->dydt_cfg;
     if (c.groups < 1)
         return fail(PJ_EUNSUPPORTED, "one state's working set does not fit in shared memory for this model");
@@ -137,7 +138,7 @@ int launch(const pj_mech *m, bool jac, int64_t n, const double *T, const double 
     long long need = (n + c.groups - 1) / c.groups;
     int blocks = int(std::min<long long>(need, (long long)dp.sms * c.ctas_per_sm));
     size_t smem = smem_bytes(m, jac, c);
-    cudaError_t e = pj::launch_eval(p, jac, c.wps, blocks, smem, stream);
+    cudaError_t e = pj::launch_eval(p, jac, cv, c.wps, blocks, smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PJ_OK;
 }
@@ -310,19 +311,31 @@ int pj_mech_info(const pj_mech *m, int *n_species, int *n_reactions, size_t *dev
     return PJ_OK;
 }
 
-int pj_eval_dydt(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
-                 double *dydt, int64_t ldd, void *stream) {
-    if (!m) return fail(PJ_EINVAL, "pj_eval_dydt: null model");
-    if (n < 0) return fail(PJ_EINVAL, "pj_eval_dydt: n < 0");
-    if (ldy < m->N) return fail(PJ_EINVAL, "pj_eval_dydt: ldy < number of species");
-    if (ldd < m->N + 1) return fail(PJ_EINVAL, "pj_eval_dydt: ldd < number of species + 1");
+static int eval_dydt(const char *fn, bool cv, const pj_mech *m, int64_t n, const double *T, const double *P,
+                     const double *Y, int64_t ldy, double *dydt, int64_t ldd, void *stream) {
+    const std::string f(fn);
+    const char *pn = cv ? "rho" : "P";
+    if (!m) return fail(PJ_EINVAL, f + ": null model");
+    if (n < 0) return fail(PJ_EINVAL, f + ": n < 0");
+    if (ldy < m->N) return fail(PJ_EINVAL, f + ": ldy < number of species");
+    if (ldd < m->N + 1) return fail(PJ_EINVAL, f + ": ldd < number of species + 1");
     if (n == 0) return PJ_OK;
     int rc;
     if ((rc = check_model_device(m)) || (rc = check_device_ptr(T, m->device, "T")) ||
-        (rc = check_device_ptr(P, m->device, "P")) || (rc = check_device_ptr(Y, m->device, "Y")) ||
+        (rc = check_device_ptr(P, m->device, pn)) || (rc = check_device_ptr(Y, m->device, "Y")) ||
         (rc = check_device_ptr(dydt, m->device, "dydt")))
         return rc;
-    return launch(m, false, n, T, P, Y, ldy, nullptr, 0, dydt, ldd, static_cast<cudaStream_t>(stream));
+    return launch(m, false, cv, n, T, P, Y, ldy, nullptr, 0, dydt, ldd, static_cast<cudaStream_t>(stream));
+}
+
+int pj_eval_dydt(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y, int64_t ldy,
+                 double *dydt, int64_t ldd, void *stream) {
+    return eval_dydt("pj_eval_dydt", false, m, n, T, P, Y, ldy, dydt, ldd, stream);
+}
+
+int pj_eval_dydt_cv(const pj_mech *m, int64_t n, const double *T, const double *rho, const double *Y, int64_t ldy,
+                    double *dydt, int64_t ldd, void *stream) {
+    return eval_dydt("pj_eval_dydt_cv", true, m, n, T, rho, Y, ldy, dydt, ldd, stream);
 }
 
 // Doubles of forward-difference workspace per state: the N perturbed states (T, P, Y[N]), their
@@ -359,32 +372,45 @@ int pj_eval_jacobian_fd(const pj_mech *m, int64_t n, const double *T, const doub
         double *Tp = static_cast<double *>(workspace), *Pp = Tp + cs * N, *Yp = Pp + cs * N;
         double *Fp = Yp + cs * N * N, *F0 = Fp + cs * N * (N + 1);
         const double *Ts = T + s0, *Ps = P + s0, *Ys = Y + s0 * ldy;
-        if ((rc = launch(m, false, cs, Ts, Ps, Ys, ldy, nullptr, 0, F0, N + 1, st))) return rc;
+        if ((rc = launch(m, false, false, cs, Ts, Ps, Ys, ldy, nullptr, 0, F0, N + 1, st))) return rc;
         cudaError_t e = pj::launch_fd_perturb(N, cs, Ts, Ps, Ys, ldy, Tp, Pp, Yp, st);
         if (e != cudaSuccess) return cuda_fail(e, "finite-difference perturbation kernel");
-        if ((rc = launch(m, false, cs * N, Tp, Pp, Yp, N, nullptr, 0, Fp, N + 1, st))) return rc;
+        if ((rc = launch(m, false, false, cs * N, Tp, Pp, Yp, N, nullptr, 0, Fp, N + 1, st))) return rc;
         e = pj::launch_fd_difference(N, cs, Ts, Ys, ldy, F0, Fp, jac + s0 * ldj, ldj, st);
         if (e != cudaSuccess) return cuda_fail(e, "finite-difference column kernel");
     }
     return PJ_OK;
 }
 
-int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
-                     int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream) {
-    if (!m) return fail(PJ_EINVAL, "pj_eval_jacobian: null model");
-    if (n < 0) return fail(PJ_EINVAL, "pj_eval_jacobian: n < 0");
-    if (ldy < m->N) return fail(PJ_EINVAL, "pj_eval_jacobian: ldy < number of species");
+static int eval_jacobian(const char *fn, bool cv, const pj_mech *m, int64_t n, const double *T, const double *P,
+                         const double *Y, int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd,
+                         void *stream) {
+    const std::string f(fn);
+    const char *pn = cv ? "rho" : "P";
+    if (!m) return fail(PJ_EINVAL, f + ": null model");
+    if (n < 0) return fail(PJ_EINVAL, f + ": n < 0");
+    if (ldy < m->N) return fail(PJ_EINVAL, f + ": ldy < number of species");
     const int64_t nn = int64_t(m->N + 1) * (m->N + 1);
-    if (ldj < nn) return fail(PJ_EINVAL, "pj_eval_jacobian: ldj < (number of species + 1)^2");
-    if (dydt && ldd < m->N + 1) return fail(PJ_EINVAL, "pj_eval_jacobian: ldd < number of species + 1");
+    if (ldj < nn) return fail(PJ_EINVAL, f + ": ldj < (number of species + 1)^2");
+    if (dydt && ldd < m->N + 1) return fail(PJ_EINVAL, f + ": ldd < number of species + 1");
     if (n == 0) return PJ_OK;
     int rc;
     if ((rc = check_model_device(m)) || (rc = check_device_ptr(T, m->device, "T")) ||
-        (rc = check_device_ptr(P, m->device, "P")) || (rc = check_device_ptr(Y, m->device, "Y")) ||
+        (rc = check_device_ptr(P, m->device, pn)) || (rc = check_device_ptr(Y, m->device, "Y")) ||
         (rc = check_device_ptr(jac, m->device, "jac")))
         return rc;
     if (dydt && (rc = check_device_ptr(dydt, m->device, "dydt"))) return rc;
-    return launch(m, true, n, T, P, Y, ldy, jac, ldj, dydt, ldd, static_cast<cudaStream_t>(stream));
+    return launch(m, true, cv, n, T, P, Y, ldy, jac, ldj, dydt, ldd, static_cast<cudaStream_t>(stream));
+}
+
+int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const double *P, const double *Y,
+                     int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream) {
+    return eval_jacobian("pj_eval_jacobian", false, m, n, T, P, Y, ldy, jac, ldj, dydt, ldd, stream);
+}
+
+int pj_eval_jacobian_cv(const pj_mech *m, int64_t n, const double *T, const double *rho, const double *Y,
+                        int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream) {
+    return eval_jacobian("pj_eval_jacobian_cv", true, m, n, T, rho, Y, ldy, jac, ldj, dydt, ldd, stream);
 }
 
 int pj_set_launch(pj_mech *m, int which, const pj_launch *cfg) {

@@ -184,7 +184,8 @@ inline int default_wps(int N, bool jac) {
     return jac ? (N <= 24 ? 1 : N <= 96 ? 2 : N <= 200 ? 4 : 16) : (N <= 128 ? 1 : 2);
 }
 int shared_const_doubles(int N);
-cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream);
+// cv: the constant-volume form, with p.P holding the densities rho instead of pressures.
+cudaError_t launch_eval(const KParams &p, bool jac, bool cv, int wps, int blocks, size_t smem, cudaStream_t stream);
 cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem);
 cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads, size_t smem, cudaStream_t stream);
 // Forward-difference Jacobian kernels (pj_fd.cu).

@@ -312,7 +312,10 @@ __device__ __forceinline__ void side_n(int n, const int16_t *sp, const int8_t *n
 }
 
 // Reaction i: rate of progress q_i and, for the Jacobian, theta_i, a_i, dH_i and the b-slots.
-template <bool JAC>
+// CV: the constant-volume form (Section 3.3), where rho is fixed instead of p: concentrations do
+// not move with T, [M] of a mixture moves with Y through rho sum Y/W, and p = rho R T / W moves
+// with T and Y (pressure-dependent rates see d ln p / dT = 1/T and d ln p / dY_j = W Delta_j).
+template <bool JAC, bool CV = false>
 __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateScalars &s, const double *C,
                                          const double *B, const double *dB, const double *H, const double *sNu,
                                          double *sq, double *sth, double *sa, double *sdH, double *sb) {
@@ -328,6 +331,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
     const double T = s.T, invT = s.invT, lnT = s.lnT;
     double lnkf = 0.0, dlnkf = 0.0, kf = 0.0;
     double c = 1.0, dcdT = 0.0, psi = 0.0, E = 0.0;
+    double pif = 0.0;                      // d ln k_f / d ln p (PLOG, Chebyshev; constant volume)
     int rev_off = 0;
 
     if (d.kind == kElem || d.kind == kThird) {
@@ -348,7 +352,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             double M;
             third_body(m, d, C, s.Ctot, M, E);
             c = M;
-            dcdT = -M * invT;
+            dcdT = CV ? 0.0 : -M * invT;
             psi = 1.0;
         }
     } else if (d.kind == kFalloff || d.kind == kChem) {
@@ -415,13 +419,13 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             psi = F * iPr1 * (phiF / Mg - ratio * iPr1);
         }
         kf = fast_exp(lnkf, tb);
-        dcdT = c * fma(phi, dlnk0 - dlnki - invT, tauF);
+        dcdT = c * fma(phi, CV ? dlnk0 - dlnki : dlnk0 - dlnki - invT, tauF);
         rev_off = 11;
     } else if (d.kind == kPlog) {
         const int n = int(__ldg(par + 0));
         const double *t = par + 1;   // n x (p, ln p, ln A, beta, Ta)
         int lo = 0, hi = 0;
-        double fr = 0.0;
+        double fr = 0.0, idl = 0.0;
         if (s.P <= __ldg(t + 0)) {
             lo = hi = 0;
         } else if (s.P >= __ldg(t + 5 * (n - 1))) {
@@ -432,6 +436,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             hi = lo + 1;
             const double l1 = __ldg(t + 5 * lo + 1), l2 = __ldg(t + 5 * hi + 1);
             fr = (s.lnP - l1) / (l2 - l1);
+            if constexpr (CV) idl = 1.0 / (l2 - l1);
         }
         const double *a = t + 5 * lo, *b = t + 5 * hi;
         const double lk1 = fma(__ldg(a + 3), lnT, __ldg(a + 2)) - __ldg(a + 4) * invT;
@@ -440,6 +445,10 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         const double d2 = fma(__ldg(b + 4), invT, __ldg(b + 3)) * invT;
         lnkf = fma(lk2 - lk1, fr, lk1);
         dlnkf = fma(d2 - d1, fr, d1);
+        if constexpr (CV) {
+            pif = (lk2 - lk1) * idl;
+            dlnkf = fma(pif, invT, dlnkf);
+        }
         kf = fast_exp(lnkf, tb);
         rev_off = 1 + 5 * n;
     } else {   // Chebyshev, Eq. e:cheb; derivative via d T_n/dx = n U_{n-1}
@@ -447,18 +456,27 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         const double Tt = (2.0 * invT - __ldg(par + 2)) * __ldg(par + 3);
         const double pt = (2.0 * s.lnP * kInvLn10 - __ldg(par + 4)) * __ldg(par + 5);
         const double *eta = par + 6;
-        double lk = 0.0, dlk = 0.0;
+        double lk = 0.0, dlk = 0.0, lkp = 0.0;
         double Tm1 = 0.0, T0 = 1.0;        // T_{t-1}, T_t at Tt
         double Um2 = 0.0, Um1 = 0.0;       // U_{t-2}, U_{t-1}
         for (int x = 0; x < nt; ++x) {
             double ct = 0.0, pm1 = 0.0, p0 = 1.0;
+            double cpd = 0.0, um2 = 0.0, um1 = 0.0;   // sum_y eta y U_{y-1}(pt); U_{y-2}, U_{y-1}
             for (int y = 0; y < npc; ++y) {
-                ct = fma(__ldg(eta + x * npc + y), p0, ct);
+                const double e = __ldg(eta + x * npc + y);
+                ct = fma(e, p0, ct);
                 const double pn = (y == 0) ? pt : 2.0 * pt * p0 - pm1;
                 pm1 = p0;
                 p0 = pn;
+                if constexpr (CV) {
+                    cpd = fma(e * sNu[y + kNuBias], um1, cpd);
+                    const double un = (y == 0) ? 1.0 : (y == 1 ? 2.0 * pt : 2.0 * pt * um1 - um2);
+                    um2 = um1;
+                    um1 = un;
+                }
             }
             lk = fma(ct, T0, lk);
+            if constexpr (CV) lkp = fma(cpd, T0, lkp);
             dlk = fma(ct * sNu[x + kNuBias], Um1, dlk);
             const double Tn = (x == 0) ? Tt : 2.0 * Tt * T0 - Tm1;
             Tm1 = T0;
@@ -469,6 +487,10 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         }
         lnkf = lk * kLn10;
         dlnkf = kLn10 * dlk * (-2.0 * invT * invT) * __ldg(par + 3);
+        if constexpr (CV) {                // d pt / d ln p = 2 par5 / ln 10
+            pif = 2.0 * lkp * __ldg(par + 5);
+            dlnkf = fma(pif, invT, dlnkf);
+        }
         kf = fast_exp(lnkf, tb);
         rev_off = 6 + nt * npc;
     }
@@ -504,12 +526,13 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
     sq[i] = q;
     if constexpr (!JAC) return;
 
-    const double dRdT = Rf * fma(-nf, invT, dlnkf) - Rr * fma(-nb, invT, dlnkr);
+    // constant volume: [X] fixed as T moves, and no 1/rho factor moves with T or Y
+    const double dRdT = CV ? fma(Rf, dlnkf, -Rr * dlnkr) : Rf * fma(-nf, invT, dlnkf) - Rr * fma(-nb, invT, dlnkr);
     const double sigma = fma(nf, Rf, -nb * Rr);
     sdH[i] = sr.sH - sf.sH;
     if (elem) {
-        sth[i] = fma(q, invT, dRdT);
-        sa[i] = -s.W * sigma;
+        sth[i] = CV ? dRdT : fma(q, invT, dRdT);
+        sa[i] = CV ? 0.0 : -s.W * sigma;
         // b'_il = k_f dP'/d[X_l] - k_r dP''/d[X_l]
         for (int x = 0; x < d.nslot; ++x) {
             const int info = __ldg(m.slot_info + d.slot_off + x);
@@ -521,8 +544,15 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
         }
         return;
     }
-    sth[i] = fma(dcdT, Rn, fma(c, dRdT, q * invT));
-    sa[i] = -s.W * fma(c, sigma, psi * Rn * E);
+    if constexpr (CV) {
+        // a_i: d[M]/dY_j = rho Delta_j (mixture) and d ln k / dY_j = pi W Delta_j (p-dependent)
+        sth[i] = fma(dcdT, Rn, c * dRdT);
+        const double pir = kc ? pif : 0.0;
+        sa[i] = fma(psi * Rn, d.tbmode == kTbMix ? s.rho : 0.0, c * s.W * fma(Rf, pif, -Rr * pir));
+    } else {
+        sth[i] = fma(dcdT, Rn, fma(c, dRdT, q * invT));
+        sa[i] = -s.W * fma(c, sigma, psi * Rn * E);
+    }
     // b'_il = c (k_f dP'/d[X_l] - k_r dP''/d[X_l]) + psi R eps_il
     const double ckf = c * kf, ckr = c * kr, psiR = psi * Rn;
     for (int x = 0; x < d.nslot; ++x) {
@@ -586,8 +616,10 @@ struct Prep {
 };
 
 // State prep and thermodynamics (Sections 2.1-2.2): Y, c_p,k, H_k, B_k (and derivatives) of every
-// species, the mixture sums, and the concentrations. Ends with the group synchronised.
-template <bool JAC, int WPS>
+// species, the mixture sums, and the concentrations. Ends with the group synchronised. CV: the
+// input is rho instead of p, and the energy arrays hold c_v,k = c_p,k - R/W_k and the molar
+// internal energy U_k = H_k - R T (Section 3.3), so that the energy row below is the constant-volume one.
+template <bool JAC, int WPS, bool CV = false>
 __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
                                            const StateIO &io, long long st, const Grp &g) {
     const int N = m.N;
@@ -599,7 +631,8 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
     // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
     StateScalars s;
     s.T = __ldg(io.T + st);
-    s.P = __ldg(io.P + st);
+    if constexpr (CV) s.rho = __ldg(io.P + st);
+    else s.P = __ldg(io.P + st);
     s.invT = 1.0 / s.T;
     s.lnT = fast_log(s.T, m.tables);
     const double *Ys = io.Y + st * io.ldy;
@@ -607,8 +640,8 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
     for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
     for (int k = t; k < N; k += G) {
         const Thermo th = species_thermo<JAC>(m, k, s.T, s.invT, s.lnT);
-        scp[k] = kR * sInvW[k] * th.cpR;
-        sH[k] = kR * th.HR;
+        scp[k] = kR * sInvW[k] * (CV ? th.cpR - 1.0 : th.cpR);
+        sH[k] = kR * (CV ? th.HR - s.T : th.HR);
         sB[k] = th.B;
         if constexpr (JAC) {
             sdB[k] = th.dB;
@@ -661,8 +694,13 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
         dcpdT = JAC ? sred[2] : 0.0;
     }
     s.W = 1.0 / sYW;
-    s.Ctot = s.P / (kR * s.T);
-    s.rho = s.Ctot * s.W;
+    if constexpr (CV) {                                 // p = rho R T / W (Eq. e:state)
+        s.Ctot = s.rho * sYW;
+        s.P = s.Ctot * kR * s.T;
+    } else {
+        s.Ctot = s.P / (kR * s.T);
+        s.rho = s.Ctot * s.W;
+    }
     s.lnP = fast_log(s.P, m.tables);
     for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
     group_sync<WPS>(g);
@@ -673,8 +711,8 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
 // of the round's states runs over the whole CTA. All threads of the CTA call this together.
 // active = false: a thread without a state in this round (a group past the last state, or a
 // thread outside the model's groups), which takes part in the reaction stage only. gact groups
-// have states; group gg's scratch is S0 + gg * stride.
-template <bool JAC, int WPS>
+// have states; group gg's scratch is S0 + gg * stride. CV: the constant-volume form.
+template <bool JAC, int WPS, bool CV = false>
 __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
                                            const StateIO &io, long long st, const Grp &g, bool active, int gact,
                                            double *S0, int stride) {
@@ -688,7 +726,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     double *spart = S + sc.part;
     (void)sHS;
     Prep pp{};
-    if (active) pp = state_prep<JAC, WPS>(m, sc, S, smem_const, io, st, g);
+    if (active) pp = state_prep<JAC, WPS, CV>(m, sc, S, smem_const, io, st, g);
     const StateScalars s = pp.s;
     const double cp = pp.cp, dcpdT = pp.dcpdT;
     double *sred = S + sc.red;
@@ -707,7 +745,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         const double *v = Sg + sc.scal;
         StateScalars sg;
         sg.T = v[0], sg.invT = v[1], sg.lnT = v[2], sg.P = v[3], sg.lnP = v[4], sg.W = v[5], sg.rho = v[6], sg.Ctot = v[7];
-        reaction<JAC>(m, i, sg, Sg + sc.C, Sg + sc.B, Sg + sc.dB, Sg + sc.H, sNu, Sg + sc.q, Sg + sc.th, Sg + sc.a,
+        reaction<JAC, CV>(m, i, sg, Sg + sc.C, Sg + sc.B, Sg + sc.dB, Sg + sc.H, sNu, Sg + sc.q, Sg + sc.th, Sg + sc.a,
                       Sg + sc.dH, Sg + sc.b);
     }
     __syncthreads();
@@ -807,7 +845,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                 const double pre = __ldg(m.W + k) * invrho;
                 sf[k] = pre * wq;
                 sJk0[k] = pre * wt;
-                sA[k] = pre * fma(s.W, wq, wa);
+                sA[k] = CV ? pre * wa : pre * fma(s.W, wq, wa);   // rho fixed: no d(1/rho)/dY term
             } else if (item < 2 * N) {
                 const int j = item - N;
                 double hs = 0.0;
@@ -990,7 +1028,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     }
 }
 
-template <bool JAC, int WPS>
+template <bool JAC, int WPS, bool CV>
 __global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__ KParams p) {
     extern __shared__ __align__(16) double smem[];
     const DevModel &m = p.m;
@@ -1010,7 +1048,7 @@ __global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__
     for (long long base = (long long)blockIdx.x * p.groups; base < p.n; base += (long long)gridDim.x * p.groups) {
         const long long st = base + g.grp;
         const int gact = int(min((long long)p.groups, p.n - base));
-        eval_state<JAC, WPS>(m, p.sc, S, smem, io, st, g, st < p.n, gact, S0, p.sc.total);
+        eval_state<JAC, WPS, CV>(m, p.sc, S, smem, io, st, g, st < p.n, gact, S0, p.sc.total);
     }
 }
 
@@ -1130,16 +1168,16 @@ bool batch_group_shape(const pj_mech &m, bool jac, int threads, size_t budget, i
 
 int shared_const_doubles(int N) { return 128 + (((2 * N) + 1) & ~1); }
 
-template <bool JAC>
+template <bool JAC, bool CV>
 static cudaError_t launch_t(const KParams &p, int wps, int blocks, size_t smem, cudaStream_t stream) {
     const int threads = wps * 32 * p.groups;
     cudaError_t e = cudaSuccess;
 #define PJ_CASE(W)                                                                                       \
     case W:                                                                                              \
-        e = cudaFuncSetAttribute(pj_eval_kernel<JAC, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+        e = cudaFuncSetAttribute(pj_eval_kernel<JAC, W, CV>, cudaFuncAttributeMaxDynamicSharedMemorySize,\
                                  int(smem));                                                             \
         if (e != cudaSuccess) return e;                                                                  \
-        pj_eval_kernel<JAC, W><<<blocks, threads, smem, stream>>>(p);                                   \
+        pj_eval_kernel<JAC, W, CV><<<blocks, threads, smem, stream>>>(p);                               \
         return cudaGetLastError();
     switch (wps) {
         PJ_CASE(1)
@@ -1153,8 +1191,9 @@ static cudaError_t launch_t(const KParams &p, int wps, int blocks, size_t smem, 
 #undef PJ_CASE
 }
 
-cudaError_t launch_eval(const KParams &p, bool jac, int wps, int blocks, size_t smem, cudaStream_t stream) {
-    return jac ? launch_t<true>(p, wps, blocks, smem, stream) : launch_t<false>(p, wps, blocks, smem, stream);
+cudaError_t launch_eval(const KParams &p, bool jac, bool cv, int wps, int blocks, size_t smem, cudaStream_t stream) {
+    if (cv) return jac ? launch_t<true, true>(p, wps, blocks, smem, stream) : launch_t<false, true>(p, wps, blocks, smem, stream);
+    return jac ? launch_t<true, false>(p, wps, blocks, smem, stream) : launch_t<false, false>(p, wps, blocks, smem, stream);
 }
 
 cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem) {

@@ -56,3 +56,39 @@ def assert_parity(gpu, ora, scale, what=""):
     assert rep["n_bad"] == 0, (what, rep)
     assert rep["max_rel_well_conditioned"] <= REL, (what, rep)
     return rep
+
+
+def rate_exponent_condition(model, T):
+    """Largest sum of the absolute values of the terms of a rate exponent over the model's
+    reactions at the temperatures T: ln k = ln A + beta ln T - Ta/T (every Arrhenius set of a
+    reaction: k, k_0, k_inf, PLOG points, explicit reverse), ln(10) sum |eta| for Chebyshev, and
+    for K_c reverse rates also |dnu ln(p_atm/R)| + sum_k |nu_k| (the absolute terms of B_k). Two
+    correct evaluations of a rate differ by up to about this many ulps (relative), which the
+    1e-10 relative bar absorbs except in entries that are themselves cancelled sums."""
+    import math
+    from paper_1605_03262_b300.synth import P_ATM, R_GAS
+    worst = 0.0
+    for t in np.atleast_1d(np.asarray(T, dtype=np.float64)):
+        lt = math.log(t)
+        bterm = []
+        for sp in model.species:
+            a = sp.a_low if t < sp.T_mid else sp.a_high
+            bterm.append(abs((a[0] - 1.0) * lt) + abs(a[6] - a[0]) + abs(a[1] * t / 2) + abs(a[2] * t * t / 6)
+                         + abs(a[3] * t ** 3 / 12) + abs(a[4] * t ** 4 / 20) + abs(a[5] / t))
+
+        def arr(p):
+            A, b, Ta = p
+            return (abs(math.log(A)) if A > 0 else 0.0) + abs(b * lt) + abs(Ta / t)
+
+        for r in model.reactions:
+            sets = [r.arr, r.k0, r.kinf] + [g[1:] for g in r.plog]
+            c = max(arr(p) for p in sets)
+            if r.cheb_eta is not None:
+                c = max(c, math.log(10.0) * float(np.abs(r.cheb_eta).sum()))
+            if r.rev_mode == 1:
+                dnu = sum(v for _, v in r.prod) - sum(v for _, v in r.reac)
+                c += abs(dnu * math.log(P_ATM / R_GAS)) + sum(v * bterm[k] for k, v in r.reac + r.prod)
+            elif r.rev_mode == 2 and r.rev_arr is not None:
+                c = max(c, arr(r.rev_arr))
+            worst = max(worst, c)
+    return worst

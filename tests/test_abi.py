@@ -82,3 +82,15 @@ def test_fd_entry_points_reject_null_model(lib):
     lib.pj_fd_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
     b = ctypes.c_size_t()
     assert lib.pj_fd_workspace_bytes(None, 4, ctypes.byref(b)) == -1
+
+
+def test_cv_entry_points_reject_null_model(lib):
+    for name in ("pj_eval_dydt_cv", "pj_eval_jacobian_cv"):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+    lib.pj_eval_dydt_cv.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 3 + \
+        [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    lib.pj_eval_jacobian_cv.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 3 + \
+        [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.pj_eval_dydt_cv(None, 4, None, None, None, 13, None, 14, None) == -1
+    assert lib.pj_eval_jacobian_cv(None, 4, None, None, None, 13, None, 196, None, 0, None) == -1

@@ -47,12 +47,12 @@ MUTANTS = [
     ("source_terms.inc", "for (int s = 0; s < r->np; ++s) Prr *= FN(ipow)(C[r->psp[s]], r->pnu[s]);",
      "for (int s = 0; s < r->np; ++s) Prr *= C[r->psp[s]];"),
     ("pyjac_oracle.c", "cs_add(&s, hk[k] * J[(size_t)(1 + k) * ld + 0]);", "cs_add(&s, hk[k] * J[(size_t)(1 + k) * ld + 1]);"),
-    ("source_terms.inc", "c = Pr / (1.0 + Pr) * F; kf = ki;", "c = Pr / (1.0 + Pr) * F; kf = k0;"),
+    ("source_terms.inc", "c = fPr * F; kf = ki;", "c = fPr * F; kf = k0;"),
     ("pyjac_oracle.c", "return kf / T * (r->kinf[1] + r->kinf[2] / T);", "return kf / T * (r->k0[1] + r->k0[2] / T);"),
     ("source_terms.inc", "cv_k[k] = (cpR - 1.0) * PJO_R / m->W[k];", "cv_k[k] = cpR * PJO_R / m->W[k];"),
     ("source_terms.inc", "u_k[k] = (HRT - 1.0) * PJO_R * T / m->W[k];", "u_k[k] = HRT * PJO_R * T / m->W[k];"),
     ("source_terms.inc", "SCALAR P = rho * (sYW + sYWc) * PJO_R * T;", "SCALAR P = rho * PJO_R * T;"),
-    ("pyjac_oracle.c", "else { Yz[col - 1] += I * h; Yz[N - 1] -= I * h; }", "else { Yz[col - 1] += I * h; }"),
+    ("pyjac_oracle.c", "cimag(fz[row]) / h - (col == 0 ? 0.0 : dfN[row]);", "cimag(fz[row]) / h;"),
 ]
 
 EPS = 2.0 ** -52

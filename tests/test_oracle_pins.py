@@ -483,9 +483,13 @@ def test_constant_volume_species_rates_equal_constant_pressure_rates(cfg):
     om = _om(model)
     T, P, Y = synth.config_states(cfg, 6, seed_offset=3)
     rho = _rho(model, T, P, Y)
-    fcv, fcp = om.dydt_cv(T, rho, Y), om.dydt(T, P, Y)
+    (fcv, fcv_s), fcp = om.dydt_cv(T, rho, Y, with_scale=True), om.dydt(T, P, Y)
     scale = np.abs(fcp[:, 1:]).max(axis=1, keepdims=True)
     assert np.all(np.abs(fcv[:, 1:] - fcp[:, 1:]) <= 1e-13 * scale)
+    # rounding scales: bound the values; the species ones are the constant-pressure ones
+    _, _, _, fcp_s = om.jacobian(T, P, Y, with_scale=True)
+    assert np.all(np.abs(fcv) <= fcv_s * (1 + 1e-12))
+    assert np.allclose(fcv_s[:, 1:], fcp_s[:, 1:], rtol=1e-12, atol=0)
     W = np.array([s.W for s in model.species])
     for s in range(len(T)):
         cpk = np.array([np.polynomial.polynomial.polyval(T[s], _coeffs(sp, T[s])[:5]) for sp in model.species]) * R_GAS / W
