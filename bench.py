@@ -438,6 +438,51 @@ def fd_form(per_config: dict, steps: int, warmup: int):
     return out
 
 
+def cv_form(per_config: dict, steps: int, warmup: int):
+    """The constant-volume form (Section 3.3) on the same states at their densities, in the same
+    launch shape as the constant-pressure Jacobian, timed like it (L2 flushed before each step)."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    for cfg in (0, 1, 2, 3):
+        name = synth.CONFIGS[cfg]["name"]
+        if name not in per_config:
+            continue
+        model = synth.config_model(cfg)
+        n = per_config[name]["n_states"]
+        T, P, Y = synth.config_states(cfg, n)
+        W = np.array([s.W for s in model.species])
+        rho = P / (synth.R_GAS * T * (Y / W).sum(axis=1))
+        g = pj.Model(synth.to_bytes(model))
+        lc = per_config[name]["launch"]
+        g.set_launch(lc["warps_per_state"], lc["states_per_cta"], lc["ctas_per_sm"])
+        Td, rd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, rho, Y))
+        N = model.n_species
+        J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            flush.zero_()
+            g.eval_jacobian_cv(Td, rd, Yd, out=J)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            g.eval_jacobian_cv(Td, rd, Yd, out=J)
+            e.record()
+            torch.cuda.synchronize()
+            ms.append(s.elapsed_time(e))
+        cv_ms = float(np.median(ms))
+        cp_ms = per_config[name]["ms_median"]
+        out[name] = {"n_states": n, "cv_ms": cv_ms, "cv_jacobians_per_s": n / (cv_ms * 1e-3),
+                     "constant_pressure_ms": cp_ms, "cv_over_constant_pressure": cv_ms / cp_ms}
+        del J
+        torch.cuda.empty_cache()
+    del flush
+    return out
+
+
 BATCH_MIX = ((0, 16384), (1, 65536), (2, 32768), (3, 2048))
 
 
@@ -654,6 +699,8 @@ def run_ours(args):
     batched = batched_form(max(3, args.steps // 2), args.warmup) if not args.headline_only else None
     fd = fd_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), 3, 1) \
         if not (args.headline_only or args.no_fd) else None
+    cvf = cv_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
+                  args.warmup) if not args.headline_only else None
     serving = serving_form() if not (args.headline_only or args.no_serving) else None
     per_config[synth.CONFIGS[HEADLINE_CFG]["name"]] = {k: res[k] for k in ("n_states", "ms_per_step",
                                                                             "ms_median", "ms_min",
@@ -686,6 +733,7 @@ def run_ours(args):
         "per_config": per_config,
         "batched_form": batched,
         "fd_form": fd,
+        "cv_form": cvf,
         "serving_form": serving,
     }
     if not args.no_cpu_baseline:
