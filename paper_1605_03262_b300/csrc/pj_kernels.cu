@@ -733,20 +733,32 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     // ---- reaction stage, all of the round's states together ----
     // Item k = (reaction i, group gg), reactions in code-path order and groups fastest: a warp's
     // lanes run a few reactions for several states, so a warp mostly takes one code path even for
-    // small reaction classes. The arithmetic of a reaction does not depend on who evaluates it.
+    // small reaction classes. Warps take runs of 32 items from a shared counter, the costliest
+    // families first, so warps that drew falloff items take fewer of the rest and the stage ends
+    // balanced. The arithmetic of a reaction does not depend on who evaluates it.
+    __shared__ int s_next_item;
     if (active && t == 0) {
         double *o = S + sc.scal;
         o[0] = s.T, o[1] = s.invT, o[2] = s.lnT, o[3] = s.P, o[4] = s.lnP, o[5] = s.W, o[6] = s.rho, o[7] = s.Ctot;
     }
+    if (threadIdx.x == 0) s_next_item = blockDim.x;     // every warp's first run is its own
     __syncthreads();
-    for (int k = threadIdx.x; k < R * gact; k += blockDim.x) {
-        const int i = k / gact, gg = k - i * gact;
-        double *Sg = S0 + size_t(gg) * stride;
-        const double *v = Sg + sc.scal;
-        StateScalars sg;
-        sg.T = v[0], sg.invT = v[1], sg.lnT = v[2], sg.P = v[3], sg.lnP = v[4], sg.W = v[5], sg.rho = v[6], sg.Ctot = v[7];
-        reaction<JAC, CV>(m, i, sg, Sg + sc.C, Sg + sc.B, Sg + sc.dB, Sg + sc.H, sNu, Sg + sc.q, Sg + sc.th, Sg + sc.a,
-                      Sg + sc.dH, Sg + sc.b);
+    const int nitems = R * gact;
+    for (int base = threadIdx.x & ~31; base < nitems;) {
+        const int k = base + (threadIdx.x & 31);
+        int nb = 0;
+        if ((threadIdx.x & 31) == 0) nb = atomicAdd(&s_next_item, 32);
+        base = __shfl_sync(0xffffffffu, nb, 0);
+        if (k < nitems) {
+            const int i = k / gact, gg = k - i * gact;
+            double *Sg = S0 + size_t(gg) * stride;
+            const double *v = Sg + sc.scal;
+            StateScalars sg;
+            sg.T = v[0], sg.invT = v[1], sg.lnT = v[2], sg.P = v[3], sg.lnP = v[4], sg.W = v[5], sg.rho = v[6];
+            sg.Ctot = v[7];
+            reaction<JAC, CV>(m, i, sg, Sg + sc.C, Sg + sc.B, Sg + sc.dB, Sg + sc.H, sNu, Sg + sc.q, Sg + sc.th,
+                              Sg + sc.a, Sg + sc.dH, Sg + sc.b);
+        }
     }
     __syncthreads();
     if (!active) return;
