@@ -374,6 +374,10 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
     J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    # the data-driven kernel, then the kernel specialised for this model and shape (NVRTC), which
+    # the result reports: same bits, sizes and offsets compiled in
+    ms_dd = time_device(g, Td, Pd, Yd, J, max(3, steps // 2), warmup, flush)
+    spec = g.specialize()
     ms = time_device(g, Td, Pd, Yd, J, steps, warmup, flush)
     work = work_model(model)
     dfe = dfma_equivalents(work, cal["ratios"])
@@ -389,6 +393,10 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
         "hbm_write_gbs": n * (N + 1) ** 2 * 8 / (ms_mean * 1e-3) / 1e9,
         "launch": {"warps_per_state": launch[0], "states_per_cta": launch[1], "ctas_per_sm": launch[2],
                    "chosen_by": "autotuner (%d probe states)" % tune.get("n_probe", 0)},
+        "kernel": "specialised for the model at run time (NVRTC, pj_mech_specialize)",
+        "specialisation": {"compile_s": spec["compile_seconds"], "cubin_bytes": spec["cubin_bytes"],
+                           "data_driven_ms_median": float(np.median(ms_dd)),
+                           "specialised_over_data_driven": float(np.median(ms)) / float(np.median(ms_dd))},
     }
     del J, flush
     return res, (g, model, T, P, Y, Td, Pd, Yd)
@@ -440,7 +448,8 @@ def fd_form(per_config: dict, steps: int, warmup: int):
 
 def cv_form(per_config: dict, steps: int, warmup: int):
     """The constant-volume form (Section 3.3) on the same states at their densities, in the same
-    launch shape as the constant-pressure Jacobian, timed like it (L2 flushed before each step)."""
+    launch shape and kernel kind (specialised) as the constant-pressure Jacobian, timed like it (L2
+    flushed before each step)."""
     import torch
     import paper_1605_03262_b300 as pj
     out = {}
@@ -457,6 +466,7 @@ def cv_form(per_config: dict, steps: int, warmup: int):
         g = pj.Model(synth.to_bytes(model))
         lc = per_config[name]["launch"]
         g.set_launch(lc["warps_per_state"], lc["states_per_cta"], lc["ctas_per_sm"])
+        g.specialize()
         Td, rd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, rho, Y))
         N = model.n_species
         J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
@@ -694,7 +704,8 @@ def run_ours(args):
             per_config[synth.CONFIGS[cfg]["name"]] = {k: r[k] for k in ("n_states", "ms_per_step", "ms_median",
                                                                         "ms_min", "jacobians_per_s",
                                                                         "roofline", "hbm_write_gbs", "launch",
-                                                                        "fp64_dfma_equiv_per_jacobian")}
+                                                                        "fp64_dfma_equiv_per_jacobian",
+                                                                        "kernel", "specialisation")}
             torch.cuda.empty_cache()
     batched = batched_form(max(3, args.steps // 2), args.warmup) if not args.headline_only else None
     fd = fd_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), 3, 1) \
@@ -706,7 +717,8 @@ def run_ours(args):
                                                                             "ms_median", "ms_min",
                                                                             "jacobians_per_s", "roofline",
                                                                             "hbm_write_gbs", "launch",
-                                                                            "fp64_dfma_equiv_per_jacobian")}
+                                                                            "fp64_dfma_equiv_per_jacobian",
+                                                                            "kernel", "specialisation")}
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
@@ -788,10 +800,11 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_profile_case(spec: str, warmup: int):
+def run_profile_case(spec: str, warmup: int, data_driven: bool = False):
     """--profile CFG:N[:WPS,GROUPS] -- a small case for ncu: warm-up launches, then one Jacobian
     launch of the first N states of configuration CFG (inputs larger than L2 once N is a few
-    thousand), at the given launch shape or else the autotuner's. The autotuner's own probe
+    thousand), at the given launch shape or else the autotuner's, with the kernel specialised for
+    the model (the one the benchmark times; --data-driven for the other). The autotuner's own probe
     launches use a separate kernel instance count, so with an explicit shape the only launches
     are the warm-ups and the profiled one."""
     import torch
@@ -808,6 +821,8 @@ def run_profile_case(spec: str, warmup: int):
         g.set_launch(shape[0], shape[1], 1)
     else:
         autotune.autotune(g, blob, use_cache=False)
+    if not data_driven:
+        g.specialize()
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
     J = torch.empty((n, model.n_species + 1, model.n_species + 1), dtype=torch.float64, device="cuda")
     for _ in range(warmup + 1):
@@ -828,9 +843,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference comparison")
     ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS]", help="one small profiling case (for ncu)")
+    ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
     args = ap.parse_args()
     if args.profile:
-        return run_profile_case(args.profile, args.warmup)
+        return run_profile_case(args.profile, args.warmup, args.data_driven)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -155,6 +155,24 @@ PJ_API int pj_eval_jacobian_fd(const pj_mech *m, int64_t n, const double *T, con
                                int64_t ldy, double *jac, int64_t ldj, void *workspace, size_t workspace_bytes,
                                void *stream);
 
+/*
+ * Per-model specialised kernels (the paper's per-mechanism code generation, Sections 4 and 6:
+ * source generated for one mechanism and compiled for it), built at run time with NVRTC. enable != 0
+ * compiles the library's evaluation kernels with every size and shared-memory offset of this model
+ * and its current launch shapes (pj_set_launch) as compile-time constants, loads them on the current
+ * device, and makes pj_eval_dydt / pj_eval_jacobian and the constant-volume calls use them while
+ * the launch shape stays the one they were compiled for (another shape uses the data-driven kernels;
+ * call again to specialise for it). The results are bitwise those of the data-driven kernels.
+ * enable == 0 releases them. Takes a few seconds. Errors: PJ_EINVAL, PJ_EUNSUPPORTED (NVRTC not
+ * loadable, or a working set that does not fit in shared memory), PJ_ECUDA (compilation or loading
+ * failed; the message holds the compiler log). pj_mech_spec_info reports whether the Jacobian and
+ * source-term calls currently run specialised kernels, and the compile time and code size; any
+ * output pointer may be NULL.
+ */
+PJ_API int pj_mech_specialize(pj_mech *m, int enable);
+PJ_API int pj_mech_spec_info(const pj_mech *m, int *active_jacobian, int *active_dydt, double *compile_seconds,
+                             size_t *cubin_bytes);
+
 /* Launch shape of the evaluation kernels for one model (which: 0 = Jacobian, 1 = source terms).
  * warps_per_state in {1, 2, 4, 8, 16}: warps that cooperate on one state; states_per_cta: states
  * a CTA evaluates concurrently (CTA size = warps_per_state * 32 * states_per_cta <= 512; at most

@@ -78,6 +78,9 @@ def load_library(path: str = LIB_PATH):
             "pj_fd_workspace_bytes": ([vp, i64, ctypes.POINTER(sz)], i32),
             "pj_eval_jacobian_fd": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, sz, vp], i32),
             "pj_eval_jacobian_host": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, i64], i32),
+            "pj_mech_specialize": ([vp, i32], i32),
+            "pj_mech_spec_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(sz)], i32),
             "pj_set_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
             "pj_get_launch": ([vp, i32, ctypes.POINTER(pj_launch)], i32),
             "pj_launch_smem_bytes": ([vp, i32, ctypes.POINTER(pj_launch), ctypes.POINTER(sz)], i32),
@@ -178,6 +181,19 @@ class Model:
                    which: str = "jacobian") -> None:
         c = pj_launch(warps_per_state, states_per_cta, ctas_per_sm)
         _check(library().pj_set_launch(self._h, 0 if which == "jacobian" else 1, ctypes.byref(c)))
+
+    def specialize(self, enable: bool = True) -> dict:
+        """Compile (NVRTC) and use kernels specialised for this model and its current launch shapes;
+        enable=False returns to the data-driven kernels. Returns spec_info()."""
+        _check(library().pj_mech_specialize(self._h, 1 if enable else 0))
+        return self.spec_info()
+
+    def spec_info(self) -> dict:
+        j, d, sec, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_size_t()
+        _check(library().pj_mech_spec_info(self._h, ctypes.byref(j), ctypes.byref(d), ctypes.byref(sec),
+                                           ctypes.byref(nb)))
+        return {"jacobian": bool(j.value), "dydt": bool(d.value), "compile_seconds": sec.value,
+                "cubin_bytes": nb.value}
 
     def launch_smem_bytes(self, warps_per_state: int, states_per_cta: int, ctas_per_sm: int = 1,
                           which: str = "jacobian") -> int:

@@ -138,7 +138,14 @@ int launch(const pj_mech *m, bool jac, bool cv, int64_t n, const double *T, cons
     long long need = (n + c.groups - 1) / c.groups;
     int blocks = int(std::min<long long>(need, (long long)dp.sms * c.ctas_per_sm));
     size_t smem = smem_bytes(m, jac, c);
-    cudaError_t e = pj::launch_eval(p, jac, cv, c.wps, blocks, smem, stream);
+    cudaError_t e;
+    if (const void *sk = pj::spec_kernel(m, jac, cv, c)) {      // the model's specialised kernel
+        e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        void *args[] = {&p};
+        if (e == cudaSuccess) e = cudaLaunchKernel(sk, dim3(blocks), dim3(c.wps * 32 * c.groups), args, smem, stream);
+    } else {
+        e = pj::launch_eval(p, jac, cv, c.wps, blocks, smem, stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PJ_OK;
 }
@@ -300,6 +307,7 @@ void pj_mech_free(pj_mech *m) {
     if (!m) return;
     if (m->dev_blob) cudaFree(m->dev_blob);
     pj_host_staging_release(m);
+    pj::spec_release(m);
     delete m;
 }
 
@@ -423,6 +431,29 @@ int pj_set_launch(pj_mech *m, int which, const pj_launch *cfg) {
     if (smem_bytes(m, which == 0, c) > size_t(device_props(m->device).smem_optin))
         return fail(PJ_EINVAL, "pj_set_launch: shape needs more shared memory than one CTA can have");
     (which == 0 ? m->jac_cfg : m->dydt_cfg) = c;
+    return PJ_OK;
+}
+
+int pj_mech_specialize(pj_mech *m, int enable) {
+    if (!m) return fail(PJ_EINVAL, "pj_mech_specialize: null model");
+    if (!enable) {
+        pj::spec_release(m);
+        return PJ_OK;
+    }
+    int rc = check_model_device(m);
+    if (rc) return rc;
+    std::string err;
+    rc = pj::specialize(m, &err);
+    return rc ? fail(rc, "pj_mech_specialize: " + err) : PJ_OK;
+}
+
+int pj_mech_spec_info(const pj_mech *m, int *active_jacobian, int *active_dydt, double *compile_seconds,
+                      size_t *cubin_bytes) {
+    if (!m) return fail(PJ_EINVAL, "pj_mech_spec_info: null model");
+    if (active_jacobian) *active_jacobian = pj::spec_kernel(m, true, false, m->jac_cfg) != nullptr;
+    if (active_dydt) *active_dydt = pj::spec_kernel(m, false, false, m->dydt_cfg) != nullptr;
+    if (compile_seconds) *compile_seconds = m->spec ? m->spec->compile_seconds : 0.0;
+    if (cubin_bytes) *cubin_bytes = m->spec ? m->spec->cubin_bytes : 0;
     return PJ_OK;
 }
 

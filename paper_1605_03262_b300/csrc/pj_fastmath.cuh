@@ -14,8 +14,10 @@
 // the test suite.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cmath>
 #include <cstdint>
+#endif
 
 namespace pj {
 
@@ -35,6 +37,7 @@ struct MathTables {
     double pad;
 };
 
+#ifndef __CUDACC_RTC__
 inline void build_math_tables(MathTables &t) {
     const long double ln2 = logl(2.0L);
     for (int j = 0; j < kExpTableSize; ++j) t.exp2j[j] = double(exp2l((long double)j / 256.0L));
@@ -58,6 +61,7 @@ inline void build_math_tables(MathTables &t) {
     t.ln2_lo = double(ln2 - h);
     t.pad = 0.0;
 }
+#endif
 
 #ifdef __CUDACC__
 

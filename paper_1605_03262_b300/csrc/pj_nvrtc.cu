@@ -1,0 +1,199 @@
+// Per-model specialised evaluation kernels, compiled at run time with NVRTC: the paper's
+// code-generation approach (per-mechanism source, compiled for the mechanism) applied to this
+// library's kernels. The device code is the library's own (pj_device_kernels.cuh, embedded at
+// build time); what is specialised is every model size and shared-memory offset the data-driven
+// kernel reads from its parameter block (species, reactions, b-slots, schedule and chunk counts,
+// scratch layout, states per CTA), which become compile-time constants, so that index arithmetic
+// and loop bounds fold. The arithmetic and its order are unchanged: a specialised kernel returns the
+// same bits as the data-driven one.
+//
+// NVRTC is loaded on first use (dlopen), so the library itself does not depend on it.
+#include <dlfcn.h>
+
+#include <chrono>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <nvrtc.h>
+
+#include "../../include/pyjac_b300.h"
+#include "pj_internal.h"
+
+namespace pj {
+namespace {
+
+#include "pj_embedded_src.inc"   // kSrcFastmath, kSrcDevice, kSrcDeviceKernels (written by build.py)
+
+struct NvrtcApi {
+    bool ok = false;
+    std::string why;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+
+const NvrtcApi &nvrtc_api() {
+    static NvrtcApi api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *h = nullptr;
+        for (const char *name : {"libnvrtc.so.13", "libnvrtc.so"})
+            if ((h = dlopen(name, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
+        if (!h) {
+            api.why = "NVRTC (libnvrtc.so.13) could not be loaded";
+            return;
+        }
+        api.create = reinterpret_cast<decltype(api.create)>(dlsym(h, "nvrtcCreateProgram"));
+        api.compile = reinterpret_cast<decltype(api.compile)>(dlsym(h, "nvrtcCompileProgram"));
+        api.log_size = reinterpret_cast<decltype(api.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+        api.log = reinterpret_cast<decltype(api.log)>(dlsym(h, "nvrtcGetProgramLog"));
+        api.cubin_size = reinterpret_cast<decltype(api.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+        api.cubin = reinterpret_cast<decltype(api.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+        api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        api.ok = api.create && api.compile && api.log_size && api.log && api.cubin_size && api.cubin && api.destroy;
+        if (!api.ok) api.why = "NVRTC lacks an expected entry point";
+    });
+    return api;
+}
+
+// Exact text of a double (hexadecimal floating literal).
+std::string hex_double(double v) {
+    char b[64];
+    std::snprintf(b, sizeof b, "%a", v);
+    return b;
+}
+
+void emit_model(std::string &s, const DevModel &d) {
+    s += "__device__ __forceinline__ void spec_model(pj::DevModel &m) {\n";
+    auto f = [&](const char *name, long long v) { s += "    m." + std::string(name) + " = " + std::to_string(v) + ";\n"; };
+    f("N", d.N), f("R", d.R), f("nslot", d.nslot), f("nnz", d.nnz), f("ncontrib", d.ncontrib);
+    f("ncolent", d.ncolent), f("rpc", d.rpc), f("n_row_chunks", d.n_row_chunks), f("ng", d.ng), f("nh", d.nh);
+    f("ncc", d.ncc), f("ngp", d.ngp), f("nhp", d.nhp), f("ncp", d.ncp), f("s_npart", d.s_npart);
+    s += "    m.lnPatmR = " + hex_double(d.lnPatmR) + ";\n}\n";
+}
+
+void emit_scratch(std::string &s, const char *fn, const Scratch &c) {
+    s += "__device__ __forceinline__ void " + std::string(fn) + "(pj::Scratch &c) {\n";
+    auto f = [&](const char *name, int v) { s += "    c." + std::string(name) + " = " + std::to_string(v) + ";\n"; };
+    f("C", c.C), f("B", c.B), f("dB", c.dB), f("H", c.H), f("cpk", c.cpk), f("Jk0", c.Jk0), f("A", c.A);
+    f("Ck", c.Ck), f("f", c.f), f("HS", c.HS), f("red", c.red), f("scal", c.scal), f("q", c.q), f("th", c.th);
+    f("a", c.a), f("dH", c.dH), f("b", c.b), f("rows", c.rows), f("part", c.part), f("total", c.total);
+    f("rows_per_chunk", c.rows_per_chunk);
+    s += "}\n";
+}
+
+// Kernel names: index = jac * 2 + cv.
+const char *const kSpecNames[4] = {"pj_spec_dydt_cp", "pj_spec_dydt_cv", "pj_spec_jac_cp", "pj_spec_jac_cv"};
+
+std::string spec_source(const pj_mech &m, const LaunchCfg &cj, const LaunchCfg &cd) {
+    std::string s = "#include \"pj_device_kernels.cuh\"\nnamespace {\n";
+    emit_model(s, m.dev);
+    emit_scratch(s, "spec_scratch_jac", make_scratch(m.dev, true, cj.wps));
+    emit_scratch(s, "spec_scratch_dydt", make_scratch(m.dev, false, cd.wps));
+    s += "}  // namespace\n";
+    const int sconst = shared_const_doubles(m.N);
+    for (int k = 0; k < 4; ++k) {
+        const bool jac = k >= 2, cv = k & 1;
+        const LaunchCfg &c = jac ? cj : cd;
+        s += "extern \"C\" __global__ void __launch_bounds__(512, 1) " + std::string(kSpecNames[k]) +
+             "(const __grid_constant__ pj::KParams p) {\n"
+             "    pj::KParams q = p;\n"
+             "    spec_model(q.m);\n"
+             "    " + std::string(jac ? "spec_scratch_jac" : "spec_scratch_dydt") + "(q.sc);\n"
+             "    q.groups = " + std::to_string(c.groups) + ";\n"
+             "    q.shared_const = " + std::to_string(sconst) + ";\n"
+             "    pj::eval_kernel_body<" + (jac ? "true" : "false") + ", " + std::to_string(c.wps) + ", " +
+             (cv ? "true" : "false") + ">(q);\n}\n";
+    }
+    return s;
+}
+
+}  // namespace
+
+// Compiles and loads the specialised kernels of a model for its current launch shapes.
+int specialize(pj_mech *m, std::string *err) {
+    const NvrtcApi &api = nvrtc_api();
+    if (!api.ok) {
+        *err = api.why;
+        return PJ_EUNSUPPORTED;
+    }
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        *err = "no CUDA device";
+        return PJ_ECUDA;
+    }
+    if (m->jac_cfg.groups < 1 || m->dydt_cfg.groups < 1) {
+        *err = "the model's working set does not fit in shared memory";
+        return PJ_EUNSUPPORTED;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    const std::string src = spec_source(*m, m->jac_cfg, m->dydt_cfg);
+    const char *hdr_src[3] = {kSrcFastmath, kSrcDevice, kSrcDeviceKernels};
+    const char *hdr_name[3] = {"pj_fastmath.cuh", "pj_device.h", "pj_device_kernels.cuh"};
+    nvrtcProgram prog = nullptr;
+    if (api.create(&prog, src.c_str(), "pj_spec.cu", 3, hdr_src, hdr_name) != NVRTC_SUCCESS) {
+        *err = "nvrtcCreateProgram failed";
+        return PJ_ECUDA;
+    }
+    const std::string arch = "-arch=sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a";
+    const char *opts[] = {arch.c_str(), "-std=c++17", "-default-device"};
+    const nvrtcResult rc = api.compile(prog, 3, opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t n = 0;
+        api.log_size(prog, &n);
+        std::string log(n, '\0');
+        if (n) api.log(prog, &log[0]);
+        api.destroy(&prog);
+        *err = "NVRTC compilation failed: " + log.substr(0, 2000);
+        return PJ_ECUDA;
+    }
+    size_t nbin = 0;
+    api.cubin_size(prog, &nbin);
+    std::vector<char> bin(nbin);
+    api.cubin(prog, bin.data());
+    api.destroy(&prog);
+    const double seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+
+    pj_spec *sp = new pj_spec();
+    cudaError_t e = cudaLibraryLoadData(&sp->lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaLibraryGetKernel(&sp->kern[k], sp->lib, kSpecNames[k]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (sp->lib) cudaLibraryUnload(sp->lib);
+        delete sp;
+        *err = std::string("loading the specialised kernels failed: ") + cudaGetErrorString(e);
+        return PJ_ECUDA;
+    }
+    sp->jac_cfg = m->jac_cfg;
+    sp->dydt_cfg = m->dydt_cfg;
+    sp->compile_seconds = seconds;
+    sp->cubin_bytes = nbin;
+    spec_release(m);
+    m->spec = sp;
+    return PJ_OK;
+}
+
+void spec_release(pj_mech *m) {
+    if (!m->spec) return;
+    if (m->spec->lib) cudaLibraryUnload(m->spec->lib);
+    delete m->spec;
+    m->spec = nullptr;
+}
+
+const void *spec_kernel(const pj_mech *m, bool jac, bool cv, const LaunchCfg &c) {
+    const pj_spec *sp = m->spec;
+    if (!sp) return nullptr;
+    const LaunchCfg &sc = jac ? sp->jac_cfg : sp->dydt_cfg;
+    if (sc.wps != c.wps || sc.groups != c.groups) return nullptr;
+    return reinterpret_cast<const void *>(sp->kern[(jac ? 2 : 0) + (cv ? 1 : 0)]);
+}
+
+}  // namespace pj
