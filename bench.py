@@ -52,9 +52,13 @@ def _distinct(side):
 
 def _side_ops(nus, kc: bool) -> int:
     """FP64 operations of one side of a reaction: powers [X]^nu and their derivatives (none for
-    nu = 1), the product and its partial derivatives, and the sums nu*B, nu*dB/dT (K_c only), nu*H."""
+    nu = 1), the product and its partial derivatives (without the factors d[X]^nu/d[X] = 1 when every
+    coefficient is 1), and the sums nu*B, nu*dB/dT (K_c only), nu*H."""
     ops = sum({1: 0, 2: 2, 3: 3}.get(v, 4) for v in nus)
-    ops += {1: 0, 2: 3, 3: 7}.get(len(nus), 11)
+    if all(v == 1 for v in nus):
+        ops += {1: 0, 2: 1, 3: 4}.get(len(nus), 7)
+    else:
+        ops += {1: 0, 2: 3, 3: 7}.get(len(nus), 11)
     return ops + len(nus) * (3 if kc else 1)
 
 

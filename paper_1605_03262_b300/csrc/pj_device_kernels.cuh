@@ -240,34 +240,43 @@ struct Side {
     double P, S[kMaxSlots], sB, sdB, sH;
 };
 
-template <int NS, bool JAC>
+template <int NS, bool JAC, bool UNIT>
 __device__ __forceinline__ void side(const int16_t *sp, const int8_t *nu, const double *C, const double *B,
                                      const double *dB, const double *H, const double *sNu, bool kc, Side &o) {
+    // UNIT: every coefficient of the side is 1 (flagged at load), so [X]^nu = [X] and its derivative
+    // is 1: the products and partial derivatives below skip the factors d (multiplications by 1.0,
+    // exact) and the per-species power branch
     double p[NS], d[NS];
     o.sB = 0.0;
     o.sdB = 0.0;
     o.sH = 0.0;
 #pragma unroll
     for (int x = 0; x < NS; ++x) {
-        const int k = sp[x], v = nu[x];
+        const int k = sp[x];
         const double c = C[k];
-        if (v == 1) {
+        if constexpr (UNIT) {
             p[x] = c;
             d[x] = 1.0;
         } else {
-            const double c2 = c * c;
-            if (v == 2) {
-                p[x] = c2;
-                d[x] = 2.0 * c;
-            } else if (v == 3) {
-                p[x] = c2 * c;
-                d[x] = 3.0 * c2;
+            const int v = nu[x];
+            if (v == 1) {
+                p[x] = c;
+                d[x] = 1.0;
             } else {
-                p[x] = c2 * c2;
-                d[x] = 4.0 * c2 * c;
+                const double c2 = c * c;
+                if (v == 2) {
+                    p[x] = c2;
+                    d[x] = 2.0 * c;
+                } else if (v == 3) {
+                    p[x] = c2 * c;
+                    d[x] = 3.0 * c2;
+                } else {
+                    p[x] = c2 * c2;
+                    d[x] = 4.0 * c2 * c;
+                }
             }
         }
-        const double vd = sNu[v + kNuBias];
+        const double vd = UNIT ? 1.0 : sNu[nu[x] + kNuBias];
         if (kc) {
             o.sB = fma(vd, B[k], o.sB);
             if constexpr (JAC) o.sdB = fma(vd, dB[k], o.sdB);
@@ -279,32 +288,42 @@ __device__ __forceinline__ void side(const int16_t *sp, const int8_t *nu, const 
         o.S[0] = d[0];
     } else if constexpr (NS == 2) {
         o.P = p[0] * p[1];
-        o.S[0] = d[0] * p[1];
-        o.S[1] = d[1] * p[0];
+        o.S[0] = UNIT ? p[1] : d[0] * p[1];
+        o.S[1] = UNIT ? p[0] : d[1] * p[0];
     } else if constexpr (NS == 3) {
         const double p01 = p[0] * p[1];
         o.P = p01 * p[2];
-        o.S[0] = d[0] * (p[1] * p[2]);
-        o.S[1] = d[1] * (p[0] * p[2]);
-        o.S[2] = d[2] * p01;
+        o.S[0] = UNIT ? p[1] * p[2] : d[0] * (p[1] * p[2]);
+        o.S[1] = UNIT ? p[0] * p[2] : d[1] * (p[0] * p[2]);
+        o.S[2] = UNIT ? p01 : d[2] * p01;
     } else {
         const double p01 = p[0] * p[1], p23 = p[2] * p[3];
         o.P = p01 * p23;
-        o.S[0] = d[0] * (p[1] * p23);
-        o.S[1] = d[1] * (p[0] * p23);
-        o.S[2] = d[2] * (p[3] * p01);
-        o.S[3] = d[3] * (p[2] * p01);
+        o.S[0] = UNIT ? p[1] * p23 : d[0] * (p[1] * p23);
+        o.S[1] = UNIT ? p[0] * p23 : d[1] * (p[0] * p23);
+        o.S[2] = UNIT ? p[3] * p01 : d[2] * (p[3] * p01);
+        o.S[3] = UNIT ? p[2] * p01 : d[3] * (p[2] * p01);
     }
 }
 
 template <bool JAC>
-__device__ __forceinline__ void side_n(int n, const int16_t *sp, const int8_t *nu, const double *C, const double *B,
-                                       const double *dB, const double *H, const double *sNu, bool kc, Side &o) {
+__device__ __forceinline__ void side_n(int n, bool unit, const int16_t *sp, const int8_t *nu, const double *C,
+                                       const double *B, const double *dB, const double *H, const double *sNu, bool kc,
+                                       Side &o) {
+    if (unit) {
+        switch (n) {
+        case 1: side<1, JAC, true>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+        case 2: side<2, JAC, true>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+        case 3: side<3, JAC, true>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+        default: side<4, JAC, true>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+        }
+        return;
+    }
     switch (n) {
-    case 1: side<1, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
-    case 2: side<2, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
-    case 3: side<3, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
-    default: side<4, JAC>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    case 1: side<1, JAC, false>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    case 2: side<2, JAC, false>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    case 3: side<3, JAC, false>(sp, nu, C, B, dB, H, sNu, kc, o); break;
+    default: side<4, JAC, false>(sp, nu, C, B, dB, H, sNu, kc, o); break;
     }
 }
 
@@ -495,8 +514,8 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
     // concentration products, their partial derivatives, and the equilibrium-constant sums
     const bool kc = d.rev == kRevKc;
     Side sf, sr;
-    side_n<JAC>(d.nr, d.rsp, d.rnu, C, B, dB, H, sNu, kc, sf);
-    side_n<JAC>(d.np, d.psp, d.pnu, C, B, dB, H, sNu, kc, sr);
+    side_n<JAC>(d.nr, d.flags & 2, d.rsp, d.rnu, C, B, dB, H, sNu, kc, sf);
+    side_n<JAC>(d.np, d.flags & 4, d.psp, d.pnu, C, B, dB, H, sNu, kc, sr);
     int inf = 0, inb = 0;
 #pragma unroll
     for (int x = 0; x < kMaxSlots; ++x) {
