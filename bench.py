@@ -374,8 +374,11 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     n, N = Y.shape
     blob = synth.to_bytes(model)
     g = pj.Model(blob)
-    tune = autotune.autotune(g, blob, use_cache=False)
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+    # tune on the workload itself when its output fits a 2 GB probe (a small batch wants another
+    # shape than a large one), else on the tuner's synthetic batch
+    own = n * (N + 1) ** 2 * 8 <= (2 << 30)
+    tune = autotune.autotune(g, blob, use_cache=False, probe=(Td, Pd, Yd) if own else None)
     J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
     # the data-driven kernel, then the kernel specialised for this model and shape (NVRTC), which
