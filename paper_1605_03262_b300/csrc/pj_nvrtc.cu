@@ -101,7 +101,11 @@ std::string spec_source(const pj_mech &m, const LaunchCfg &cj, const LaunchCfg &
     for (int k = 0; k < 4; ++k) {
         const bool jac = k >= 2, cv = k & 1;
         const LaunchCfg &c = jac ? cj : cd;
-        s += "extern \"C\" __global__ void __launch_bounds__(512, 1) " + std::string(kSpecNames[k]) +
+        // launch bounds of the compiled shape: a CTA of fewer than 512 threads leaves each thread
+        // more than 128 registers
+        const int threads = c.wps * 32 * c.groups, ctas = c.ctas_per_sm > 0 ? c.ctas_per_sm : 1;
+        s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(threads) + ", " + std::to_string(ctas) +
+             ") " + std::string(kSpecNames[k]) +
              "(const __grid_constant__ pj::KParams p) {\n"
              "    pj::KParams q = p;\n"
              "    spec_model(q.m);\n"
