@@ -312,8 +312,10 @@ typedef struct { double s, c; } csum;
 static void cs_add(csum *a, double x) { acc_d(&a->s, &a->c, x); }
 static double cs_val(const csum *a) { return a->s + a->c; }
 
-/* Troe F and its partial derivatives dF/dFcent, dF/dP_r and Fcent, dFcent/dT (Section 3.1). */
-static void troe_parts(const pjo_rxn *r, double T, double Pr, double *F, double *dFdT_Pr, double *dFdPr)
+/* Troe F and its partial derivatives dF/dFcent, dF/dP_r and Fcent, dFcent/dT (Section 3.1); dFdlnPr
+ * receives P_r dF/dP_r, which stays finite at P_r = 0. */
+static void troe_parts(const pjo_rxn *r, double T, double Pr, double *F, double *dFdT_Pr, double *dFdPr,
+                       double *dFdlnPr)
 {
     double a = r->fp[0], T3 = r->fp[1], T1 = r->fp[2], T2 = r->fp[3];
     double Fc = (1.0 - a) * exp(-T / T3) + a * exp(-T / T1) + (r->has_T2 ? exp(-T2 / T) : 0.0);
@@ -328,12 +330,15 @@ static void troe_parts(const pjo_rxn *r, double T, double Pr, double *F, double 
     double dAdPr = 1.0 / (Pr * M_LN10), dBdPr = -0.14 / (Pr * M_LN10);
     double dFdFc = Fv * (1.0 / (Fc * g) - log(Fc) * 2.0 * At / (Bt * Bt * Bt) * (dAdFc * Bt - At * dBdFc) / (g * g));
     *dFdPr = -Fv * log(Fc) * 2.0 * At / (Bt * Bt * Bt) * (dAdPr * Bt - At * dBdPr) / (g * g);
+    *dFdlnPr = -Fv * log(Fc) * 2.0 * At / (Bt * Bt * Bt) * (1.0 / M_LN10 * Bt - At * (-0.14 / M_LN10)) / (g * g);
+    if (Pr < 1e-300) *dFdPr = *dFdlnPr = 0.0;   /* F is constant below the clamp */
     *F = Fv;
     *dFdT_Pr = dFdFc * dFc;   /* explicit temperature dependence at fixed P_r */
 }
 
-/* SRI F, its explicit T-derivative at fixed P_r and dF/dP_r (Section 3.1). */
-static void sri_parts(const pjo_rxn *r, double T, double Pr, double *F, double *dFdT_Pr, double *dFdPr)
+/* SRI F, its explicit T-derivative at fixed P_r, dF/dP_r and P_r dF/dP_r (Section 3.1). */
+static void sri_parts(const pjo_rxn *r, double T, double Pr, double *F, double *dFdT_Pr, double *dFdPr,
+                      double *dFdlnPr)
 {
     double a = r->fp[0], b = r->fp[1], c = r->fp[2], d = r->fp[3], e = r->fp[4];
     double Prc = Pr < 1e-300 ? 1e-300 : Pr;
@@ -345,6 +350,8 @@ static void sri_parts(const pjo_rxn *r, double T, double Pr, double *F, double *
     *F = Fv;
     *dFdT_Pr = Fv * (e / T + X * (a * b / (T * T) * exp(-b / T) - exp(-T / c) / c) / base);
     *dFdPr = Fv * dXdPr * log(base);
+    *dFdlnPr = Fv * (-X * X * 2.0 * lPr / M_LN10) * log(base);
+    if (Pr < 1e-300) *dFdPr = *dFdlnPr = 0.0;   /* F is constant below the clamp */
 }
 
 /* Chebyshev polynomial of the second kind U_n(x) by its recurrence (U_0 = 1, U_1 = 2x). */
@@ -470,7 +477,7 @@ static int jac_one(const pjo_mech *m, double T, double P, const double *Y,
 
         /* pressure modifier derivatives */
         double dcdT = 0.0, dcdTabs = 0.0;
-        double Pr = 0.0, ratio = 0.0, Fv = 1.0, dFdPr = 0.0, M = 0.0;
+        double Pr = 0.0, ratio = 0.0, Fv = 1.0, dFdPr = 0.0, dFdlnPr = 0.0, M = 0.0;
         if (r->kind == PJO_THIRD) {
             dcdT = -c / T;
             dcdTabs = fabs(dcdT);
@@ -483,13 +490,21 @@ static int jac_one(const pjo_mech *m, double T, double P, const double *Y,
             /* Eq. E:dPridT */
             double dPrdT = Pr / T * (r->k0[1] - r->kinf[1] + (r->k0[2] - r->kinf[2]) / T - 1.0);
             double dFdT = 0.0, dFdT_Pr = 0.0;
-            if (r->ftype == PJO_TROE) troe_parts(r, T, Pr, &Fv, &dFdT_Pr, &dFdPr);
-            else if (r->ftype == PJO_SRI) sri_parts(r, T, Pr, &Fv, &dFdT_Pr, &dFdPr);
-            dFdT = dFdT_Pr + dFdPr * dPrdT;
-            if (r->kind == PJO_FALLOFF) dcdT = c * (1.0 / (Pr * (1.0 + Pr)) * dPrdT + dFdT / Fv);
-            else                        dcdT = c * (-1.0 / (1.0 + Pr) * dPrdT + dFdT / Fv);
-            dcdTabs = fabs(c) * (fabs(dPrdT / (Pr * (1.0 + Pr))) + fabs(dPrdT / (1.0 + Pr)) + fabs(dFdT_Pr / Fv) +
-                                 fabs(dFdPr * dPrdT / Fv));
+            if (r->ftype == PJO_TROE) troe_parts(r, T, Pr, &Fv, &dFdT_Pr, &dFdPr, &dFdlnPr);
+            else if (r->ftype == PJO_SRI) sri_parts(r, T, Pr, &Fv, &dFdT_Pr, &dFdPr, &dFdlnPr);
+            if (Pr < 1e-300 && r->kind == PJO_FALLOFF) {
+                /* P_r = 0 (a single third-body species that is absent): c = 0 and P_r ~ [M], so the
+                 * limit of Eq. dCidT is 0; the 1/P_r form would be 0 * inf */
+                dcdT = 0.0;
+                dcdTabs = 0.0;
+            } else {
+                dFdT = dFdT_Pr + dFdPr * dPrdT;
+                if (r->kind == PJO_FALLOFF) dcdT = c * (1.0 / (Pr * (1.0 + Pr)) * dPrdT + dFdT / Fv);
+                else                        dcdT = c * (-1.0 / (1.0 + Pr) * dPrdT + dFdT / Fv);
+                /* the scale counts the terms of the kind's own form (the falloff one alone has 1/P_r) */
+                const double tPr = r->kind == PJO_FALLOFF ? fabs(dPrdT / (Pr * (1.0 + Pr))) : fabs(dPrdT / (1.0 + Pr));
+                dcdTabs = fabs(c) * (tPr + fabs(dFdT_Pr / Fv) + fabs(dFdPr * dPrdT / Fv));
+            }
         }
         dqT[i] = dcdT * Rn + c * dRdT;
         dqTabs[i] = dcdTabs * Rabs[i] + fabs(c) * dRdTabs;
@@ -541,9 +556,17 @@ static int jac_one(const pjo_mech *m, double T, double P, const double *Y,
                     dPrdYabs = fabs(Pr * Wm * Dl[j]) + ratio * rho / m->W[ms] * fabs(dl);
                 }
                 double dFdY = dFdPr * dPrdY;
-                if (r->kind == PJO_FALLOFF) dcdY = c * (1.0 / (Pr * (1.0 + Pr)) * dPrdY + dFdY / Fv);   /* Eq. dCidY_falloff */
-                else                        dcdY = c * (-1.0 / (1.0 + Pr) * dPrdY + dFdY / Fv);         /* Eq. dCidY_chem */
-                dcdYabs = fabs(c) * (fabs(1.0 / (Pr * (1.0 + Pr))) + 1.0 / (1.0 + Pr) + fabs(dFdPr / Fv)) * dPrdYabs;
+                if (Pr < 1e-300 && r->kind == PJO_FALLOFF) {
+                    /* the limit of Eq. dCidY_falloff at P_r = 0, from c / P_r = F / (1 + P_r) and
+                     * c dF/dP_r / F = P_r dF/dP_r / (1 + P_r): dc/dY = (F + P_r dF/dP_r) dP_r/dY */
+                    dcdY = (Fv + dFdlnPr) * dPrdY;
+                    dcdYabs = (fabs(Fv) + fabs(dFdlnPr)) * dPrdYabs;
+                } else {
+                    if (r->kind == PJO_FALLOFF) dcdY = c * (1.0 / (Pr * (1.0 + Pr)) * dPrdY + dFdY / Fv);   /* Eq. dCidY_falloff */
+                    else                        dcdY = c * (-1.0 / (1.0 + Pr) * dPrdY + dFdY / Fv);         /* Eq. dCidY_chem */
+                    const double tPr = r->kind == PJO_FALLOFF ? fabs(1.0 / (Pr * (1.0 + Pr))) : 1.0 / (1.0 + Pr);
+                    dcdYabs = fabs(c) * (tPr + fabs(dFdPr / Fv)) * dPrdYabs;
+                }
             }
             dqY[(size_t)i * Nj + j] = dcdY * Rn + c * dRdY;
             dqYabs[(size_t)i * Nj + j] = dcdYabs * Rabs[i] + fabs(c) * dRdYabs;

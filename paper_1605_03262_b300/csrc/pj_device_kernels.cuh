@@ -400,7 +400,8 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             F = fast_exp(lnFc * g, tb);
             if constexpr (JAC) {
                 const double g2r = -2.0 * g * g * r * iB;
-                phiF = lnFc * g2r * fma(0.14, r, 1.0) * kInvLn10;
+                // below the P_r clamp F is constant, so its P_r derivative is zero there
+                phiF = Pr < 1e-300 ? 0.0 : lnFc * g2r * fma(0.14, r, 1.0) * kInvLn10;
                 const double dg_dlFc = g2r * fma(1.1762, r, -0.67);
                 tauF = fma(lnFc * kInvLn10, dg_dlFc, g) * dFc / Fc;
             }
@@ -414,7 +415,7 @@ __device__ __forceinline__ void reaction(const DevModel &m, int i, const StateSc
             const double lnb = fast_log(base, tb);
             F = fast_exp(fma(X, lnb, fma(e, lnT, lnd)), tb);
             if constexpr (JAC) {
-                phiF = -2.0 * X * X * lPr * lnb * kInvLn10;
+                phiF = Pr < 1e-300 ? 0.0 : -2.0 * X * X * lPr * lnb * kInvLn10;
                 tauF = fma(X * fma(a * b * invT * invT, e1, -ic * e2), 1.0 / base, e * invT);
             }
         }

@@ -566,3 +566,55 @@ def test_constant_volume_jacobian_is_sparse_for_elementary_reactions():
                 assert np.all(Jcp[:, 1 + k, 1 + j] != 0.0) or not any(partners[k])
                 zero += 1
     assert zero > 0
+
+
+@pytest.mark.parametrize("ftype", ["lindemann", "troe", "sri"])
+def test_falloff_with_absent_third_body_species(ftype):
+    """A falloff reaction whose single third-body species m is absent has P_r = 0, where the forms of
+    dc/dT and dc/dY with 1/P_r are 0 * inf. With F constant below the P_r clamp (reading of the
+    clamp), c = P_r F(clamp) / (1 + P_r) has dc/d[X_m] = (k_0/k_inf) F(clamp) and dc/dT = 0 there,
+    so the only nonzero entries of the reaction's columns are
+    d(dY_k/dt)/dY_m = (W_k / rho) nu_k (k_0/k_inf) F (rho / W_m) R, computed here independently.
+    (The complex step is no check at this point: the sign of an O(h^2) real part of P_r decides
+    whether its perturbed log P_r is clamped.)"""
+    import math
+    model = mechs.typed_model(ftype, seed=81, n_species=8, n_reactions=6, species_tb_fraction=1.0,
+                              chem_fraction=0.0)
+    N = model.n_species
+    r = next(x for x in model.reactions if x.tb_species >= 0 and x.tb_species != N - 1)
+    import copy
+    sub = copy.deepcopy(model)
+    sub.reactions = [r]
+    om = _om(sub)
+    T, P, Y = synth.generate_states(N, 3, seed=82)
+    m = r.tb_species
+    Y[:, m] = 0.0
+    Y /= Y.sum(axis=1, keepdims=True)
+    J, f = om.jacobian(T, P, Y)
+    assert np.all(np.isfinite(J))
+    W = np.array([sp.W for sp in model.species])
+    for s in range(len(T)):
+        t = T[s]
+        rho = P[s] / (R_GAS * t * (Y[s] / W).sum())
+        k0 = r.k0[0] * t ** r.k0[1] * math.exp(-r.k0[2] / t)
+        ki = r.kinf[0] * t ** r.kinf[1] * math.exp(-r.kinf[2] / t)
+        if ftype == "lindemann":
+            F = 1.0
+        elif ftype == "troe":
+            a, T3, T1, T2 = r.fparams[:4]
+            Fc = (1 - a) * math.exp(-t / T3) + a * math.exp(-t / T1) + (math.exp(-T2 / t) if r.troe_has_T2 else 0.0)
+            lFc = math.log10(Fc)
+            At, Bt = -300.0 - 0.67 * lFc - 0.4, 0.806 - 1.1762 * lFc + 0.14 * 300.0
+            F = Fc ** (1.0 / (1.0 + (At / Bt) ** 2))
+        else:
+            a, b, c, d, e = r.fparams[:5]
+            F = d * t ** e * (a * math.exp(-b / t) + math.exp(-t / c)) ** (1.0 / (1.0 + 300.0 ** 2))
+        rates = om.reaction_rates(t, P[s], Y[s])
+        R = rates["Rf"][0] - rates["Rr"][0]
+        assert rates["c"][0] == 0.0
+        dq = k0 / ki * F * rho / W[m] * R
+        for k in range(N):
+            nu = sum(v for x, v in r.prod if x == k) - sum(v for x, v in r.reac if x == k)
+            want = W[k] / rho * nu * dq
+            assert abs(J[s, 1 + k, 1 + m] - want) <= 1e-12 * abs(dq * W.max() / rho) + 1e-300
+        assert np.all(J[s, 1:, 0] == 0.0)              # dc/dT = 0 and c = 0: no temperature column
