@@ -94,3 +94,28 @@ def test_cv_entry_points_reject_null_model(lib):
         [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     assert lib.pj_eval_dydt_cv(None, 4, None, None, None, 13, None, 14, None) == -1
     assert lib.pj_eval_jacobian_cv(None, 4, None, None, None, 13, None, 196, None, 0, None) == -1
+
+
+def test_header_and_library_work_from_plain_c(tmp_path):
+    """The ABI is C: the header compiles as C99 with warnings as errors, and a C program linked
+    against the library gets the documented status codes and error text (no GPU needed)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_1605_03262_b300 import build
+    src = tmp_path / "t.c"
+    src.write_text(
+        '#include <string.h>\n#include "pyjac_b300.h"\n'
+        "int main(void) {\n"
+        "    if (pj_version() <= 0) return 1;\n"
+        "    if (pj_eval_jacobian(NULL, 4, NULL, NULL, NULL, 13, NULL, 196, NULL, 0, NULL) != PJ_EINVAL) return 2;\n"
+        "    if (strlen(pj_last_error()) == 0) return 3;\n"
+        "    if (pj_eval_jacobian_cv(NULL, 4, NULL, NULL, NULL, 13, NULL, 196, NULL, 0, NULL) != PJ_EINVAL) return 4;\n"
+        "    if (pj_mech_specialize(NULL, 1) != PJ_EINVAL) return 5;\n"
+        "    return 0;\n}\n")
+    exe = tmp_path / "t"
+    libdir = os.path.dirname(build.LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(build.ROOT, "include"),
+                    str(src), "-L", libdir, "-lpyjacb300", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    assert subprocess.run([str(exe)]).returncode == 0
