@@ -100,7 +100,7 @@ struct DevModel {
 };
 
 // Doubles of one warp's row stage: rpc staged rows and the partial slots of split entries.
-__host__ __device__ inline int row_stride(const DevModel &m) { return (m.rpc * (m.N + 1) + m.s_npart + 1) & ~1; }
+__host__ __device__ inline int row_stride(const DevModel &m) { return (m.rpc * (m.N + 1) + m.s_npart + 2) & ~1; }
 
 // Offsets (in doubles) of one state's scratch in shared memory.
 struct Scratch {

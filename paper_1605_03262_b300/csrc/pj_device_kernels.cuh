@@ -945,8 +945,11 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
         //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
         const int ld = N + 1, RPC = m.rpc;
-        double *stage = S + sc.rows + wg * row_stride(m);
-        double *pbuf = stage + RPC * ld;          // partial sums of split entries
+        // the chunk's rows sit one element in when their global start is 8 mod 16, so that the
+        // bulk copy to global memory has both ends 16-byte aligned
+        double *const stage0 = S + sc.rows + wg * row_stride(m);
+        double *stage = stage0;
+        double *pbuf = stage0 + RPC * ld + 1;     // partial sums of split entries
         double *Jout = io.jac + st * io.ldj;
         constexpr int kDense = 4;
         double acc = 0.0;
@@ -955,6 +958,9 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         walk<SB, true, true>(m.s_chunk, m.n_row_chunks, wg, NW, m.s_rec, lane,
              [&](int c) {                               // dense part of chunk c
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
+                 if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                 __syncwarp();                          // the previous chunk's bulk copy has read the stage
+                 stage = stage0 + ((reinterpret_cast<uintptr_t>(Jout + (long long)r0 * ld) & 15) ? 1 : 0);
                  comb = __ldg(m.s_comb_chunk + c);     // split entries of this chunk
                  if (RPC == 1 && r0 > 0) {              // one species row: its constants once
                      const int k = r0 - 1;
@@ -1045,10 +1051,34 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                      for (int q = 0; q < cr.z; ++q) v += pbuf[cr.y + q];
                      stage[cr.x] = v;
                  }
+                 // the finished rows go out as one bulk copy (TMA engine) of their 16-byte aligned
+                 // middle, issued by lane 0 after the warp's shared-memory writes are fenced for the
+                 // async proxy; the odd first and last elements are plain stores
+                 // (one-row chunks keep the warp's own 16-byte stores: their copy would have to be read
+                 // before the next row's dense fill, measured slower)
+                 if (RPC == 1) {
+                     __syncwarp();
+                     store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
+                     __syncwarp();
+                     return;
+                 }
+                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                  __syncwarp();
-                 store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
-                 __syncwarp();
+                 if (lane == 0) {
+                     double *gdst = Jout + (long long)r0 * ld;
+                     const int head = int(stage - stage0), body = (nel - head) & ~1;
+                     if (head) __stcs(gdst, stage[0]);
+                     if (body > 0) {
+                         const unsigned saddr = unsigned(__cvta_generic_to_shared(stage + head));
+                         asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                                      :: "l"(gdst + head), "r"(saddr), "r"(body * 8) : "memory");
+                         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                     }
+                     if (head + body < nel) __stcs(gdst + nel - 1, stage[nel - 1]);
+                 }
              });
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();                                   // the stage may be reused (gather partials)
         if (io.dydt) {
             double *out = io.dydt + st * io.ldd;
             for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -Hf * invcp : sf[k - 1];
