@@ -564,7 +564,46 @@ def batched_form(steps: int, warmup: int):
            "batched_persistent": {"ms": t_batch, "jacobians_per_s": total / (t_batch * 1e-3), "launches": 1,
                                   "tiles": plan.n_tiles, "threads_per_cta": plan.threads_per_cta},
            "batched_graph": {"ms": t_graph, "jacobians_per_s": total / (t_graph * 1e-3), "launches": 1}}
-    del items, flush, plan, graph
+    del plan, graph
+
+    # many small batches (the form's use: 64 requests of 16-1,024 states over the four models), one
+    # persistent launch against 64 launches, plain or replayed from a graph
+    rng = np.random.default_rng(17)
+    small, stotal = [], 0
+    for x in range(64):
+        g = items[x % 4][0]
+        n = int(np.exp(rng.uniform(np.log(16), np.log(1024))))
+        N = g.n_species
+        T, P, Y = synth.generate_states(N, n, seed=3000 + x)
+        Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+        small.append((g, Td, Pd, Yd, torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")))
+        stotal += n
+
+    def plain_small():
+        for g, Td, Pd, Yd, J in small:
+            g.eval_jacobian(Td, Pd, Yd, out=J)
+
+    plain_graph = torch.cuda.CUDAGraph()
+    s_cap = torch.cuda.Stream()
+    s_cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_cap):
+        plain_small()                      # warm-up outside the capture
+        torch.cuda.synchronize()
+        with torch.cuda.graph(plain_graph, stream=s_cap):
+            for g, Td, Pd, Yd, J in small:
+                g.eval_jacobian(Td, Pd, Yd, out=J, stream=s_cap)
+    torch.cuda.current_stream().wait_stream(s_cap)
+    splan = pj.BatchPlan(small)
+    sgraph = splan.capture()
+    ts_plain, ts_pgraph = timed(plain_small), timed(plain_graph.replay)
+    ts_batch, ts_graph = timed(splan.run), timed(sgraph.replay)
+    out["many_small"] = {
+        "requests": len(small), "total_states": stotal,
+        "plain_sequential": {"ms": ts_plain, "launches": len(small)},
+        "plain_graph": {"ms": ts_pgraph, "launches": len(small)},
+        "batched_persistent": {"ms": ts_batch, "launches": 1, "tiles": splan.n_tiles},
+        "batched_graph": {"ms": ts_graph, "launches": 1}}
+    del items, small, flush, splan, sgraph, plain_graph
     torch.cuda.empty_cache()
     return out
 
