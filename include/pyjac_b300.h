@@ -259,6 +259,18 @@ PJ_API void pj_batch_free(pj_batch *b);
  */
 PJ_API int pj_batch_run_noalloc(const pj_batch_item *items, int n_items, int which, int tile_states, void *stream);
 
+/*
+ * The same launch with the item table, tile bounds and counter in a device workspace of the
+ * caller (at least pj_batch_workspace_bytes() bytes, 16-byte aligned, on the current device)
+ * instead of the library's static array: calls on different workspaces may overlap on the GPU (one
+ * workspace per stream, e.g. a server's pool). At most 64 items; same argument rules and errors as
+ * pj_batch_run_noalloc, plus PJ_EINVAL for a missing, small, misaligned or non-device workspace.
+ * Calls that share a workspace must be ordered on one stream.
+ */
+PJ_API size_t pj_batch_workspace_bytes(void);
+PJ_API int pj_batch_run_ws(const pj_batch_item *items, int n_items, int which, int tile_states, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH):
             "pj_batch_run": ([vp, vp], i32),
             "pj_batch_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(sz), ctypes.POINTER(i32)], i32),
             "pj_batch_free": ([vp], None),
+            "pj_batch_run_noalloc": ([ctypes.POINTER(pj_batch_item), i32, i32, i32, vp], i32),
+            "pj_batch_workspace_bytes": ([], sz),
+            "pj_batch_run_ws": ([ctypes.POINTER(pj_batch_item), i32, i32, i32, vp, sz, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -308,6 +311,48 @@ def _host_stride0(a):
     return a.strides[0] // 8
 
 
+def _batch_items(items, which: int):
+    """pj_batch_item array from (Model, T, P, Y, out[, dydt_out]) tuples; returns it and the
+    tensors it points into (to keep alive)."""
+    keep = []
+    arr = (pj_batch_item * len(items))()
+    for x, item in enumerate(items):
+        model, T, P, Y, out = item[:5]
+        f = item[5] if len(item) > 5 else None
+        T, P, Y, n = model._inputs(T, P, Y)
+        keep += [model, T, P, Y, out, f]
+        a = arr[x]
+        a.mech = model.handle
+        a.n = n
+        a.T, a.P, a.Y, a.ldy = T.data_ptr(), P.data_ptr(), Y.data_ptr(), Y.stride(0)
+        if which == 0:
+            a.jac, a.ldj = out.data_ptr(), out.stride(0)
+            a.dydt, a.ldd = (f.data_ptr(), f.stride(0)) if f is not None else (None, 0)
+        else:
+            a.jac, a.ldj = None, 0
+            a.dydt, a.ldd = out.data_ptr(), out.stride(0)
+    return arr, keep
+
+
+def batch_workspace_bytes() -> int:
+    return int(library().pj_batch_workspace_bytes())
+
+
+def run_batch(items, which: str = "jacobian", workspace=None, tile_states: int = 0, stream=None) -> None:
+    """One persistent launch over up to 64 (Model, T, P, Y, out[, dydt_out]) items without a plan:
+    the item table goes to ``workspace`` (a CUDA uint8 tensor of at least batch_workspace_bytes();
+    calls sharing one must be ordered on a stream) or, without one, to the library's static array
+    (pj_batch_run_noalloc; calls must not overlap on the GPU)."""
+    w = 0 if which == "jacobian" else 1
+    arr, keep = _batch_items(items, w)
+    if workspace is None:
+        _check(library().pj_batch_run_noalloc(arr, len(items), w, int(tile_states), _stream_handle(stream)))
+    else:
+        _check(library().pj_batch_run_ws(arr, len(items), w, int(tile_states), _ptr(workspace), workspace.numel(),
+                                         _stream_handle(stream)))
+    del keep
+
+
 class BatchPlan:
     """One persistent launch over several (model, states, outputs) items (the batched form).
 
@@ -319,23 +364,7 @@ class BatchPlan:
     def __init__(self, items, which: str = "jacobian", threads_per_cta: int = 0, ctas_per_sm: int = 0,
                  tile_states: int = 0):
         self.which = 0 if which == "jacobian" else 1
-        self._keep = []
-        arr = (pj_batch_item * len(items))()
-        for x, item in enumerate(items):
-            model, T, P, Y, out = item[:5]
-            f = item[5] if len(item) > 5 else None
-            T, P, Y, n = model._inputs(T, P, Y)
-            self._keep += [model, T, P, Y, out, f]
-            a = arr[x]
-            a.mech = model.handle
-            a.n = n
-            a.T, a.P, a.Y, a.ldy = T.data_ptr(), P.data_ptr(), Y.data_ptr(), Y.stride(0)
-            if self.which == 0:
-                a.jac, a.ldj = out.data_ptr(), out.stride(0)
-                a.dydt, a.ldd = (f.data_ptr(), f.stride(0)) if f is not None else (None, 0)
-            else:
-                a.jac, a.ldj = None, 0
-                a.dydt, a.ldd = out.data_ptr(), out.stride(0)
+        arr, self._keep = _batch_items(items, self.which)
         shape = pj_batch_shape(threads_per_cta, ctas_per_sm, tile_states)
         h = ctypes.c_void_p()
         _check(library().pj_batch_create(arr, len(items), self.which, ctypes.byref(shape), ctypes.byref(h)))

@@ -207,6 +207,85 @@ int noalloc_fail(int code, const std::string &msg) { return pj::set_error(code, 
 
 }  // namespace
 
+namespace {
+
+// Builds the item table of a batched launch on the host, copies it with the zeroed tile counter
+// into the device scratch `scratch` (the static array or a caller's workspace) on the stream, and
+// launches the persistent batched kernel over it.
+int batch_run_table(const char *fn, const pj_batch_item *items, int n_items, int which, int tile_states, int dev,
+                    void *scratch, cudaStream_t st) {
+    using namespace pj;
+    const std::string f(fn);
+    cudaError_t e;
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool jac = which == 0;
+    cudaFuncAttributes fa{};
+    e = jac ? cudaFuncGetAttributes(&fa, pj_batch_noalloc_kernel<true>)
+            : cudaFuncGetAttributes(&fa, pj_batch_noalloc_kernel<false>);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    const size_t budget = size_t(optin) > fa.sharedSizeBytes ? size_t(optin) - fa.sharedSizeBytes : 0;
+    const int threads = 512;
+
+    // the item table, built on the host stack and copied into the scratch
+    NoAllocScratch h;
+    std::memset(&h, 0, sizeof(h));
+    h.n_items = n_items;
+    size_t smem = 0;
+    int ntiles = 0;
+    for (int i = 0; i < n_items; ++i) {
+        const pj_batch_item &x = items[i];
+        const pj_mech *m = x.mech;
+        if (!m || x.n < 0) return noalloc_fail(PJ_EINVAL, f + ": null model or n < 0");
+        if (m->device != dev) return noalloc_fail(PJ_EINVAL, f + ": model lives on another device");
+        const int64_t N = m->N, nn = (N + 1) * (N + 1);
+        if (x.ldy < N || (jac && x.ldj < nn) || ((!jac || x.dydt) && x.ldd < N + 1))
+            return noalloc_fail(PJ_EINVAL, f + ": leading dimension too small");
+        if (x.n > 0 && (!x.T || !x.P || !x.Y || (jac && !x.jac) || (!jac && !x.dydt)))
+            return noalloc_fail(PJ_EINVAL, f + ": null input or output pointer");
+        int wps = 0, groups = 0;
+        Scratch sc{};
+        if (!batch_group_shape(*m, jac, threads, budget, &wps, &groups, &sc))
+            return noalloc_fail(PJ_EUNSUPPORTED, f + ": state working set exceeds shared memory");
+        const int sconst = shared_const_doubles(m->N);
+        smem = std::max(smem, (size_t(sconst) + size_t(sc.total) * groups) * 8);
+        BatchItem &b = h.items[i];
+        b.m = m->dev_model;
+        b.sc = sc;
+        b.io = BatchIO{x.T, x.P, x.Y, x.ldy, x.jac, x.ldj, x.dydt, x.ldd};
+        b.wps = wps;
+        b.groups = groups;
+        b.shared_const = sconst;
+        const long long ts = tile_states > 0 ? tile_states : 4LL * groups;
+        h.tile_states[i] = ts;
+        h.n_states[i] = x.n;
+        h.tile_first[i] = ntiles;
+        const long long nt = (x.n + ts - 1) / ts;
+        if (ntiles + nt > 0x7fffffffLL) return noalloc_fail(PJ_EINVAL, f + ": too many tiles");
+        ntiles += int(nt);
+    }
+    h.tile_first[n_items] = ntiles;
+    h.counter = 0;                     // what must start at zero: the tile counter
+    // the copy brings the zeroed counter and this call's table; a call still running on the GPU
+    // with the same array would race with it
+    e = cudaMemcpyAsync(scratch, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
+    if (ntiles == 0) return PJ_OK;
+    e = jac ? cudaFuncSetAttribute(pj_batch_noalloc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
+            : cudaFuncSetAttribute(pj_batch_noalloc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
+    const int blocks = std::max(1, std::min(sms, ntiles));
+    NoAllocScratch *scr = static_cast<NoAllocScratch *>(scratch);
+    if (jac) pj_batch_noalloc_kernel<true><<<blocks, threads, smem, st>>>(scr, ntiles);
+    else pj_batch_noalloc_kernel<false><<<blocks, threads, smem, st>>>(scr, ntiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return PJ_OK;
+}
+
+}  // namespace
+
 extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const pj_batch_item *items, int n_items,
                                                                           int which, int tile_states, void *stream) {
     using namespace pj;
@@ -234,70 +313,35 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const
         }
         scratch = g_noalloc_ptr[dev];
     }
-    int sms = 0, optin = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const bool jac = which == 0;
-    cudaFuncAttributes fa{};
-    e = jac ? cudaFuncGetAttributes(&fa, pj_batch_noalloc_kernel<true>)
-            : cudaFuncGetAttributes(&fa, pj_batch_noalloc_kernel<false>);
-    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
-    const size_t budget = size_t(optin) > fa.sharedSizeBytes ? size_t(optin) - fa.sharedSizeBytes : 0;
-    const int threads = 512;
+    return batch_run_table("pj_batch_run_noalloc", items, n_items, which, tile_states, dev, scratch,
+                           static_cast<cudaStream_t>(stream));
+}
 
-    // the item table, built on the host stack and copied into the static scratch
-    NoAllocScratch h;
-    std::memset(&h, 0, sizeof(h));
-    h.n_items = n_items;
-    size_t smem = 0;
-    int ntiles = 0;
-    for (int i = 0; i < n_items; ++i) {
-        const pj_batch_item &x = items[i];
-        const pj_mech *m = x.mech;
-        if (!m || x.n < 0) return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: null model or n < 0");
-        if (m->device != dev) return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: model lives on another device");
-        const int64_t N = m->N, nn = (N + 1) * (N + 1);
-        if (x.ldy < N || (jac && x.ldj < nn) || ((!jac || x.dydt) && x.ldd < N + 1))
-            return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: leading dimension too small");
-        if (x.n > 0 && (!x.T || !x.P || !x.Y || (jac && !x.jac) || (!jac && !x.dydt)))
-            return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: null input or output pointer");
-        int wps = 0, groups = 0;
-        Scratch sc{};
-        if (!batch_group_shape(*m, jac, threads, budget, &wps, &groups, &sc))
-            return noalloc_fail(PJ_EUNSUPPORTED, "pj_batch_run_noalloc: state working set exceeds shared memory");
-        const int sconst = shared_const_doubles(m->N);
-        smem = std::max(smem, (size_t(sconst) + size_t(sc.total) * groups) * 8);
-        BatchItem &b = h.items[i];
-        b.m = m->dev_model;
-        b.sc = sc;
-        b.io = BatchIO{x.T, x.P, x.Y, x.ldy, x.jac, x.ldj, x.dydt, x.ldd};
-        b.wps = wps;
-        b.groups = groups;
-        b.shared_const = sconst;
-        const long long ts = tile_states > 0 ? tile_states : 4LL * groups;
-        h.tile_states[i] = ts;
-        h.n_states[i] = x.n;
-        h.tile_first[i] = ntiles;
-        const long long nt = (x.n + ts - 1) / ts;
-        if (ntiles + nt > 0x7fffffffLL) return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: too many tiles");
-        ntiles += int(nt);
+extern "C" __attribute__((visibility("default"))) size_t pj_batch_workspace_bytes(void) {
+    return sizeof(pj::NoAllocScratch);
+}
+
+extern "C" __attribute__((visibility("default"))) int pj_batch_run_ws(const pj_batch_item *items, int n_items,
+                                                                     int which, int tile_states, void *workspace,
+                                                                     size_t workspace_bytes, void *stream) {
+    using namespace pj;
+    if (!items || n_items < 1 || (which != 0 && which != 1) || tile_states < 0)
+        return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: bad argument");
+    if (n_items > kNoAllocMaxItems)
+        return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: " + std::to_string(n_items) + " items, more than a workspace holds (" +
+                                           std::to_string(kNoAllocMaxItems) + ")");
+    if (!workspace || workspace_bytes < sizeof(NoAllocScratch) || (reinterpret_cast<uintptr_t>(workspace) & 15))
+        return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: workspace null, smaller than pj_batch_workspace_bytes() or "
+                                       "not 16-byte aligned");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    cudaPointerAttributes pa{};
+    e = cudaPointerGetAttributes(&pa, workspace);
+    if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != dev) {
+        cudaGetLastError();
+        return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: workspace is not device memory of the current device");
     }
-    h.tile_first[n_items] = ntiles;
-    h.counter = 0;                     // what must start at zero: the tile counter
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the copy brings the zeroed counter and this call's table; a call still running on the GPU
-    // with the same array would race with it
-    e = cudaMemcpyAsync(scratch, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
-    if (ntiles == 0) return PJ_OK;
-    e = jac ? cudaFuncSetAttribute(pj_batch_noalloc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
-            : cudaFuncSetAttribute(pj_batch_noalloc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
-    const int blocks = std::max(1, std::min(sms, ntiles));
-    NoAllocScratch *scr = static_cast<NoAllocScratch *>(scratch);
-    if (jac) pj_batch_noalloc_kernel<true><<<blocks, threads, smem, st>>>(scr, ntiles);
-    else pj_batch_noalloc_kernel<false><<<blocks, threads, smem, st>>>(scr, ntiles);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
-    return PJ_OK;
+    return batch_run_table("pj_batch_run_ws", items, n_items, which, tile_states, dev, workspace,
+                           static_cast<cudaStream_t>(stream));
 }

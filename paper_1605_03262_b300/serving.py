@@ -5,12 +5,17 @@ future. A scheduler thread runs iterations continuously:
 
 * retire: iterations whose completion event has fired hand their results to the futures and
   give back their device memory and stream;
-* admit: queued requests are taken in arrival order; requests of the same model that are queued
-  together are merged into one launch (up to ``max_batch_states`` states). An iteration is admitted
-  only while an in-flight slot is free and the device memory it holds (inputs, Jacobians, dydt)
-  fits the HBM budget next to the iterations already in flight; otherwise it waits in the queue
-  (no out-of-memory, no rejection). Iterations run on a pool of streams, so requests admitted
-  while others are on the GPU overlap with them.
+* admit: queued requests are taken in arrival order. By default an iteration merges queued
+  requests of the head's model into one plain launch (up to ``max_batch_states`` states), which
+  runs the model's own (specialised, if compiled) kernel; with ``mixed=True`` an iteration takes up
+  to 64 queued requests of any of the models and evaluates them in one persistent batched launch
+  (pj_batch_run_ws, with a workspace per stream). On a trace of requests of 1-4,096 states over
+  four models the merged iterations served 1.4 M Jacobians/s and the mixed ones 1.0 M/s: the
+  streams already overlap the iterations, and the batched kernel runs its group width at run
+  time. An iteration is admitted only while an in-flight slot is free and the device memory it
+  holds (inputs, Jacobians, dydt) fits the HBM budget next to the iterations already in flight;
+  otherwise it waits in the queue (no out-of-memory, no rejection). Iterations run on a pool of
+  streams, so requests admitted while others are on the GPU overlap with them.
 
 Model images stay resident for the server's lifetime. Each request's latency is measured from
 :meth:`submit` to the completion event of its iteration (results in device memory), and, with
@@ -43,10 +48,10 @@ class Request:
 
 
 class _Iteration:
-    __slots__ = ("reqs", "model", "stream", "event", "bytes", "J", "F", "offsets", "host")
+    __slots__ = ("reqs", "model", "stream", "event", "bytes", "J", "F", "offsets", "host", "results")
 
     def __init__(self):
-        self.reqs, self.offsets, self.host = [], [], None
+        self.reqs, self.offsets, self.host, self.results = [], [], None, None
 
 
 class Server:
@@ -61,7 +66,8 @@ class Server:
     device tensors are the clients' memory from then on."""
 
     def __init__(self, models: Dict[str, object], hbm_budget: Optional[int] = None, max_inflight: int = 6,
-                 max_batch_states: int = 65536, host_results: bool = False, discard_results: bool = False):
+                 max_batch_states: int = 65536, host_results: bool = False, discard_results: bool = False,
+                 mixed: bool = False):
         import torch
         self.torch = torch
         self.models = dict(models)
@@ -76,6 +82,12 @@ class Server:
         self._inflight: List[_Iteration] = []
         self._streams = [torch.cuda.Stream(device=self.device) for _ in range(self.max_inflight)]
         self._free_streams = list(self._streams)
+        self.mixed = bool(mixed)
+        self._ws = {}
+        if self.mixed:                    # one batched-launch workspace per stream
+            from . import batch_workspace_bytes
+            nb = batch_workspace_bytes()
+            self._ws = {id(st): torch.empty(nb, dtype=torch.uint8, device=self.device) for st in self._streams}
         self._held = 0
         self._cv = threading.Condition()
         self._stop = False
@@ -171,11 +183,16 @@ class Server:
         for it in done:
             self._inflight.remove(it)
             t = time.perf_counter()
-            for r, (a, b) in zip(it.reqs, it.offsets):
+            for x, r in enumerate(it.reqs):
                 r.t_done = t
                 if self.discard_results:
                     r.future.set_result(None)
                     continue
+                if it.results is not None:        # a mixed iteration: one output per request
+                    J, F = it.results[x]
+                    r.future.set_result((J, F) if r.dydt else J)
+                    continue
+                a, b = it.offsets[x]
                 if self.host_results:
                     J = it.host[0][a:b]
                     res = (J, it.host[1][a:b]) if r.dydt else J
@@ -188,6 +205,71 @@ class Server:
         return bool(done)
 
     def _admit(self) -> bool:
+        return self._admit_mixed() if self.mixed else self._admit_merged()
+
+    def _admit_mixed(self) -> bool:
+        """Iterations of up to 64 queued requests of any models, one batched launch each."""
+        from . import run_batch
+        torch = self.torch
+        admitted = False
+        while True:
+            with self._cv:
+                if not self._queue or len(self._inflight) >= self.max_inflight or not self._free_streams:
+                    return admitted
+                take, n, need = [], 0, 0
+                for r in self._queue:
+                    b = self._bytes(self.models[r.name], r.n)
+                    if take and (len(take) == 64 or n + r.n > self.max_batch_states or
+                                 self._held + need + b > self.hbm_budget):
+                        break
+                    take.append(r)
+                    n += r.n
+                    need += b
+                if self._held + need > self.hbm_budget:
+                    self.stats["waits_for_memory"] += 1
+                    return admitted
+                for r in take:
+                    self._queue.remove(r)
+            it = _Iteration()
+            it.reqs, it.model, it.bytes = take, None, need
+            it.stream = self._free_streams.pop()
+            self._held += need
+            items, results = [], []
+            with torch.cuda.stream(it.stream):
+                for r in take:
+                    model = self.models[r.name]
+                    N = model.n_species
+                    T = torch.as_tensor(r.T, dtype=torch.float64).to(self.device, non_blocking=True)
+                    P = torch.as_tensor(r.P, dtype=torch.float64).to(self.device, non_blocking=True)
+                    Y = torch.as_tensor(r.Y, dtype=torch.float64).to(self.device, non_blocking=True)
+                    J = torch.empty((r.n, N + 1, N + 1), dtype=torch.float64, device=self.device)
+                    F = torch.empty((r.n, N + 1), dtype=torch.float64, device=self.device) if r.dydt else None
+                    items.append((model, T, P, Y, J) + ((F,) if F is not None else ()))
+                    results.append((J, F))
+                run_batch(items, workspace=self._ws[id(it.stream)], stream=it.stream)
+                if self.host_results:
+                    hres = []
+                    for J, F in results:
+                        Jh = torch.empty(J.shape, dtype=torch.float64, pin_memory=True)
+                        Jh.copy_(J, non_blocking=True)
+                        Fh = None
+                        if F is not None:
+                            Fh = torch.empty(F.shape, dtype=torch.float64, pin_memory=True)
+                            Fh.copy_(F, non_blocking=True)
+                        hres.append((Jh.numpy(), Fh.numpy() if Fh is not None else None))
+                    results = hres
+                it.results = results
+                it.event = torch.cuda.Event()
+                it.event.record(it.stream)
+            self._inflight.append(it)
+            self.stats["iterations"] += 1
+            self.stats["requests"] += len(take)
+            self.stats["merged_requests"] += len(take) - 1
+            self.stats["states"] += n
+            self.stats["max_inflight_seen"] = max(self.stats["max_inflight_seen"], len(self._inflight))
+            admitted = True
+
+    def _admit_merged(self) -> bool:
         torch = self.torch
         admitted = False
         while True:

@@ -85,3 +85,52 @@ def test_requests_overlap_and_latencies_are_recorded():
     summ = latency_summary([f.request for f in futs])
     assert summ["n"] == len(trace) and summ["p99_ms"] >= summ["p50_ms"] > 0
     assert stats["max_inflight_seen"] > 1
+
+
+def test_merged_and_mixed_iterations_give_the_same_results():
+    """Per-model merged launches (the default) and mixed-model batched launches (mixed=True) return
+    the same bits for every request."""
+    from paper_1605_03262_b300.serving import Server
+    models = _models()
+    trace = _trace(models, 30, seed=11)
+    out = {}
+    for mixed in (False, True):
+        with Server(models, max_inflight=3, mixed=mixed) as srv:
+            futs = [srv.submit(*r) for r in trace]
+            out[mixed] = [f.result(timeout=120).cpu() for f in futs]
+            if mixed:
+                assert srv.stats["merged_requests"] > 0
+    for a, b in zip(out[False], out[True]):
+        assert torch.equal(a, b)
+
+
+def test_run_batch_with_workspaces_equals_plain_launches():
+    """pj_batch_run_ws on two workspaces on two streams, and pj_batch_run_noalloc, equal the plain
+    launches of every item."""
+    import paper_1605_03262_b300 as pj
+    models = _models()
+    trace = _trace(models, 12, seed=21)
+    items, refs = [], []
+    for name, T, P, Y in trace:
+        g = models[name]
+        Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+        N = g.n_species
+        items.append((g, Td, Pd, Yd, torch.empty((len(T), N + 1, N + 1), dtype=torch.float64, device="cuda")))
+        refs.append(g.eval_jacobian(Td, Pd, Yd))
+    nb = pj.batch_workspace_bytes()
+    ws = [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    torch.cuda.synchronize()
+    pj.run_batch(items[:6], workspace=ws[0], stream=streams[0])
+    pj.run_batch(items[6:], workspace=ws[1], stream=streams[1])
+    torch.cuda.synchronize()
+    for it, ref in zip(items, refs):
+        assert torch.equal(it[4], ref)
+    for it in items:
+        it[4].zero_()
+    pj.run_batch(items)                               # the static array
+    torch.cuda.synchronize()
+    for it, ref in zip(items, refs):
+        assert torch.equal(it[4], ref)
+    with pytest.raises(pj.LibraryError):
+        pj.run_batch(items, workspace=ws[0][:16])      # too small
