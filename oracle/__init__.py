@@ -82,6 +82,10 @@ def _bind(lib):
     lib.pjo_eval_dydt_cv.restype = i32
     lib.pjo_jacobian_cv.argtypes = [vp, i64, dp, dp, dp, i64, dp, i64, dp]
     lib.pjo_jacobian_cv.restype = i32
+    lib.pjo_eval_dydt_conc.argtypes = [vp, i64, dp, dp, dp, dp, i64, dp, i64]
+    lib.pjo_eval_dydt_conc.restype = i32
+    lib.pjo_jacobian_conc.argtypes = [vp, i64, dp, dp, dp, dp, i64, dp, i64, dp, dp, i64, dp]
+    lib.pjo_jacobian_conc.restype = i32
     lib.pjo_reaction_rates.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp, dp, dp, dp]
     lib.pjo_reaction_rates.restype = i32
     lib.pjo_species_thermo.argtypes = [vp, ctypes.c_double, dp, dp, dp, dp]
@@ -204,6 +208,39 @@ class OracleModel:
         if rc:
             raise RuntimeError("oracle constant-volume jacobian failed (%d)" % rc)
         return (J, Js) if with_scale else J
+
+    def dydt_conc(self, T, P, V, nmol):
+        """Source terms of the molar-concentration basis at constant pressure: states (T, V,
+        n_1..n_{N-1}) at pressure P, nmol of shape (n, N-1); returns (n, N+1) in state order
+        (dT/dt, dV/dt, dn_1/dt..dn_{N-1}/dt)."""
+        T, P, V, nmol = _f64(T).ravel(), _f64(P).ravel(), _f64(V).ravel(), _f64(nmol)
+        n = len(T)
+        N = self.n_species
+        nmol = nmol.reshape(n, N - 1)
+        out = np.empty((n, N + 1))
+        rc = self._lib.pjo_eval_dydt_conc(self._h, n, _ptr(T), _ptr(P), _ptr(V), _ptr(nmol), N - 1, _ptr(out),
+                                          N + 1)
+        if rc:
+            raise RuntimeError("oracle concentration-basis dydt failed (%d)" % rc)
+        return out
+
+    def jacobian_conc(self, T, P, V, nmol, with_scale: bool = False):
+        """Jacobian (n, N+1, N+1) of the molar-concentration basis at constant pressure, rows and
+        columns (T, V, n_1..n_{N-1}), by complex-step differentiation of its source terms; also the
+        source terms. with_scale: (J, f, J_scale, f_scale) with per-entry rounding scales."""
+        T, P, V, nmol = _f64(T).ravel(), _f64(P).ravel(), _f64(V).ravel(), _f64(nmol)
+        n = len(T)
+        N = self.n_species
+        nmol = nmol.reshape(n, N - 1)
+        J = np.empty((n, N + 1, N + 1))
+        f = np.empty((n, N + 1))
+        Js = np.empty_like(J) if with_scale else None
+        fs = np.empty_like(f) if with_scale else None
+        rc = self._lib.pjo_jacobian_conc(self._h, n, _ptr(T), _ptr(P), _ptr(V), _ptr(nmol), N - 1, _ptr(J),
+                                         (N + 1) ** 2, _ptr(Js), _ptr(f), N + 1, _ptr(fs))
+        if rc:
+            raise RuntimeError("oracle concentration-basis jacobian failed (%d)" % rc)
+        return (J, f, Js, fs) if with_scale else (J, f)
 
     # -- single-state introspection ------------------------------------------------------------
     def reaction_rates(self, T: float, P: float, Y):

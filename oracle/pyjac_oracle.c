@@ -921,3 +921,177 @@ int pjo_jacobian_complex_step(const pjo_mech *m, int64_t n, const double *T, con
     }
     return err ? PJO_ENOMEM : PJO_OK;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Molar-concentration basis at constant pressure (conc_rhs in source_terms.inc): the source terms
+ * f = (dT/dt, dV/dt, dn_1/dt..dn_{N-1}/dt) of states (T, V, n_1..n_{N-1}) at fixed P, and their
+ * Jacobian by the plain definition, d f / d (T, V, n_1..n_{N-1}), one complex-step derivative per
+ * column (T + i h; V (1 + i h); n_j + i h V, which moves [X_j] by i h and, through n_N, [X_N] by
+ * -i h). State-major; nmol[s * ldn + k] = n_k (k < N-1). */
+int pjo_eval_dydt_conc(const pjo_mech *m, int64_t n, const double *T, const double *P, const double *V,
+                       const double *nmol, int64_t ldn, double *dydt, int64_t ldd)
+{
+    if (!m || n < 0 || ldn < m->ns - 1 || ldd < m->ns + 1) return PJO_EINVAL;
+    if (n == 0) return PJO_OK;
+    if (!T || !P || !V || !nmol || !dydt) return PJO_EINVAL;
+    const int N = m->ns;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(pjo_max_threads())
+    for (int64_t s = 0; s < n; ++s) {
+        double *wk = malloc((9 * (size_t)N + (size_t)m->nr + 2) * sizeof(double));
+        if (!wk) { err = 1; continue; }
+        conc_rhs_d(m, T[s], P[s], V[s], nmol + s * ldn, dydt + s * ldd, NULL, wk);
+        free(wk);
+    }
+    return err ? PJO_ENOMEM : PJO_OK;
+}
+
+/* jac: (N+1) x (N+1) per state, rows and columns in state order (T, V, n_1..n_{N-1}); dydt
+ * (optional): f. The optional scales bound the rounding of each entry for an evaluation that
+ * forms it from per-reaction partial derivatives in the concentrations [X_l] (each at fixed
+ * T and fixed other [X]) and in T: per reaction a_i = |c R_f| + |c R_r|, g_il = |d(c R_f)/d[X_l]| +
+ * |d(c R_r)/d[X_l]|, t_i = |d(c R_f)/dT| + |d(c R_r)/dT| + (3 + orders + 6 [third body]) a_i / T;
+ * per species m_kl = sum_i |nu_ki| g_il; a species entry in column n_j takes m_kj + m_kN, its V
+ * entry sV_k = sum_i |nu_ki| a_i + sum_l [X_l] m_kl + [M] m_kN, its T entry
+ * V (sum_i |nu_ki| t_i + sV_k / T); the T and V rows take the same sums weighted as in their
+ * definitions (|H_k|, 1/(V rho c_p), 1/[M]), plus the magnitudes of their thermodynamic terms. */
+int pjo_jacobian_conc(const pjo_mech *m, int64_t n, const double *T, const double *P, const double *V,
+                      const double *nmol, int64_t ldn, double *jac, int64_t ldj, double *jac_scale,
+                      double *dydt, int64_t ldd, double *dydt_scale)
+{
+    if (!m || n < 0 || ldn < m->ns - 1) return PJO_EINVAL;
+    const int N = m->ns, R = m->nr;
+    if (ldj < (int64_t)(N + 1) * (N + 1)) return PJO_EINVAL;
+    if ((dydt || dydt_scale) && ldd < N + 1) return PJO_EINVAL;
+    if (n == 0) return PJO_OK;
+    if (!T || !P || !V || !nmol || !jac) return PJO_EINVAL;
+    const double h = 1e-30;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(pjo_max_threads())
+    for (int64_t s = 0; s < n; ++s) {
+        const size_t nwk = 9 * (size_t)N + (size_t)R + 2;
+        /* complex: n, f, workspace (conc_rhs and the constant-volume source terms), qf, qr, Y */
+        double complex *z = malloc(((size_t)N + (N + 1) + nwk + 2 * (size_t)R + N) * sizeof(double complex));
+        /* real: f, X, Y, H, cp, dcp, a, t, mN, ml, sV, sT, |omega|, column scales of the T row */
+        double *b = malloc(((size_t)(N + 1) + 11 * (size_t)N + 2 * (size_t)R + (size_t)(N + 1)) * sizeof(double));
+        if (!z || !b) { free(z); free(b); err = 1; continue; }
+        double complex *nz = z, *fz = nz + N, *wkz = fz + N + 1, *qfz = wkz + nwk, *qrz = qfz + R, *Yz = qrz + R;
+        double *f = b, *X = f + N + 1, *Y = X + N, *Hm = Y + N, *cpm = Hm + N, *dcpm = cpm + N, *ar = dcpm + N;
+        double *tr = ar + R, *mN = tr + R, *ml = mN + N, *sV = ml + N, *sT = sV + N, *aom = sT + N, *sTr = aom + N;
+        const double Ts = T[s], Ps = P[s], Vs = V[s], *ns_ = nmol + s * ldn;
+        double *Jo = jac + s * ldj, *Jso = jac_scale ? jac_scale + s * ldj : NULL;
+        const size_t ld = (size_t)N + 1;
+        /* f and the columns */
+        for (int k = 0; k < N - 1; ++k) nz[k] = ns_[k];
+        conc_rhs_z(m, Ts, Ps, Vs, nz, fz, NULL, wkz);
+        for (int r = 0; r <= N; ++r) f[r] = creal(fz[r]);
+        if (dydt) for (int r = 0; r <= N; ++r) dydt[s * ldd + r] = f[r];
+        for (int col = 0; col <= N; ++col) {
+            double complex Tz = Ts, Vz = Vs;
+            double dh = h;
+            for (int k = 0; k < N - 1; ++k) nz[k] = ns_[k];
+            if (col == 0) Tz += I * h;
+            else if (col == 1) { Vz += I * h * Vs; dh = h * Vs; }
+            else { nz[col - 2] += I * h * Vs; dh = h * Vs; }
+            conc_rhs_z(m, Tz, Ps, Vz, nz, fz, NULL, wkz);
+            for (int r = 0; r <= N; ++r) Jo[(size_t)r * ld + col] = cimag(fz[r]) / dh;
+        }
+        if (Jso || dydt_scale) {
+            /* concentrations, mass fractions and molar thermodynamics of the state */
+            const double M = Ps / (PJO_R * Ts);
+            double sx = 0.0, rho = 0.0;
+            for (int k = 0; k < N - 1; ++k) { X[k] = ns_[k] / Vs; sx += X[k]; }
+            X[N - 1] = M - sx;
+            for (int k = 0; k < N; ++k) rho += X[k] * m->W[k];
+            for (int k = 0; k < N; ++k) Y[k] = X[k] * m->W[k] / rho;
+            double K = 0.0, dK = 0.0;
+            for (int k = 0; k < N; ++k) {
+                double complex cpR, HRT, SR;
+                nasa7_z(m, k, Ts + I * h, &cpR, &HRT, &SR);
+                Hm[k] = creal(HRT) * PJO_R * Ts;
+                cpm[k] = creal(cpR) * PJO_R;
+                dcpm[k] = cimag(cpR) / h * PJO_R;
+                K += X[k] * cpm[k];
+                dK += fabs(X[k] * dcpm[k]);
+            }
+            /* per reaction: a_i and t_i (T-partials at fixed [X], constant-volume source terms) */
+            for (int k = 0; k < N; ++k) Yz[k] = Y[k];
+            source_terms_cv_z(m, Ts + I * h, rho, Yz, fz, qfz, qrz, wkz);
+            for (int i = 0; i < R; ++i) {
+                const pjo_rxn *r = &m->rx[i];
+                int ord = 3 + (r->kind == PJO_THIRD || r->kind == PJO_FALLOFF || r->kind == PJO_CHEM ? 6 : 0);
+                for (int q = 0; q < r->nr; ++q) ord += r->rnu[q];
+                for (int q = 0; q < r->np; ++q) ord += r->pnu[q];
+                ar[i] = fabs(creal(qfz[i])) + fabs(creal(qrz[i]));
+                tr[i] = fabs(cimag(qfz[i]) / h) + fabs(cimag(qrz[i]) / h) + ord * ar[i] / Ts;
+            }
+            for (int k = 0; k < N; ++k) { aom[k] = 0.0; sV[k] = 0.0; sT[k] = 0.0; }
+            for (int i = 0; i < R; ++i) {
+                const pjo_rxn *r = &m->rx[i];
+                for (int q = 0; q < r->nnet; ++q) {
+                    aom[r->netsp[q]] += fabs(r->netnu[q]) * ar[i];
+                    sT[r->netsp[q]] += fabs(r->netnu[q]) * tr[i];
+                }
+            }
+            /* m_kl for l = N first (every column's second direction), then l = 1..N-1 */
+            for (int l = N - 1; l >= 0; --l) {
+                double *mk = (l == N - 1) ? mN : ml;
+                for (int k = 0; k < N; ++k) Yz[k] = Y[k];
+                Yz[l] += I * h * m->W[l] / rho;                /* [X_l] + i h */
+                source_terms_cv_z(m, Ts, rho, Yz, fz, qfz, qrz, wkz);
+                for (int k = 0; k < N; ++k) mk[k] = 0.0;
+                for (int i = 0; i < R; ++i) {
+                    const pjo_rxn *r = &m->rx[i];
+                    const double g = fabs(cimag(qfz[i]) / h) + fabs(cimag(qrz[i]) / h);
+                    for (int q = 0; q < r->nnet; ++q) mk[r->netsp[q]] += fabs(r->netnu[q]) * g;
+                }
+                for (int k = 0; k < N; ++k) sV[k] += X[l] * mk[k];
+                if (l == N - 1 || !Jso) continue;
+                double sh = 0.0, sn = 0.0;                     /* column n_l: species, T and V rows */
+                for (int k = 0; k < N; ++k) {
+                    const double skj = mk[k] + mN[k];
+                    if (k < N - 1) Jso[(size_t)(2 + k) * ld + 2 + l] = skj;
+                    sh += fabs(Hm[k]) * skj;
+                    sn += skj;
+                }
+                const double sTj = (sh + fabs(f[0]) * (fabs(cpm[l]) + fabs(cpm[N - 1]))) / (Vs * K);
+                sTr[2 + l] = sTj;
+                Jso[2 + l] = sTj;
+                Jso[ld + 2 + l] = Vs / Ts * sTj + sn / M;
+            }
+            double aO = 0.0, sHV = 0.0, sHT = 0.0, sVs = 0.0, sTs = 0.0, cpo = 0.0;
+            for (int k = 0; k < N; ++k) {
+                sV[k] += aom[k] + M * mN[k];
+                sT[k] += sV[k] / Ts;                           /* per unit volume */
+                aO += aom[k];
+                sHV += fabs(Hm[k]) * sV[k];
+                sHT += fabs(Hm[k]) * sT[k];
+                sVs += sV[k];
+                sTs += sT[k];
+                cpo += fabs(cpm[k]) * aom[k];
+            }
+            if (dydt_scale) {
+                double *fs = dydt_scale + s * ldd, sh = 0.0;
+                for (int k = 0; k < N; ++k) sh += fabs(Hm[k]) * aom[k];
+                fs[0] = sh / K;
+                fs[1] = Vs * (fs[0] / Ts + aO / M);
+                for (int k = 0; k < N - 1; ++k) fs[2 + k] = Vs * aom[k];
+            }
+            if (Jso) {
+                for (int k = 0; k < N - 1; ++k) {
+                    Jso[(size_t)(2 + k) * ld + 0] = Vs * sT[k];
+                    Jso[(size_t)(2 + k) * ld + 1] = sV[k];
+                }
+                const double sTV = (sHV + fabs(f[0]) * (K + M * fabs(cpm[N - 1]))) / (Vs * K);
+                const double sTT = (cpo + sHT + fabs(f[0]) * (dK + fabs(cpm[N - 1]) * M / Ts)) / K;
+                Jso[0] = sTT;
+                Jso[1] = sTV;
+                Jso[ld + 0] = Vs * (sTT / Ts + fabs(f[0]) / (Ts * Ts) + aO / (M * Ts) + sTs / M);
+                Jso[ld + 1] = fabs(f[0]) / Ts + Vs / Ts * sTV + sVs / M;
+            }
+        }
+        free(z);
+        free(b);
+    }
+    return err ? PJO_ENOMEM : PJO_OK;
+}

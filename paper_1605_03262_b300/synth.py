@@ -524,6 +524,28 @@ def generate_states(n_species: int, n_states: int, seed: int, T_range=(800.0, 25
     return T.astype(np.float64), P.astype(np.float64), np.ascontiguousarray(Y, dtype=np.float64)
 
 
+def generate_conc_states(n_species: int, n_states: int, seed: int, T_range=(800.0, 2500.0),
+                         P_range_atm=(1.0, 50.0), alpha: float = 0.5, V_range=(1e-6, 1e-2)):
+    """States of the molar-concentration basis: T uniform, P log-uniform (Pa), V log-uniform (m^3),
+    mole fractions x ~ Dirichlet(alpha) over all species and n_k = x_k P V / (R T) for the first
+    N - 1 species (the last one is implied). Returns (T, P, V, n) with n of shape (n_states, N-1)."""
+    rng = np.random.default_rng(seed)
+    T = rng.uniform(T_range[0], T_range[1], size=n_states)
+    P = P_ATM * 10.0 ** rng.uniform(math.log10(P_range_atm[0]), math.log10(P_range_atm[1]), size=n_states)
+    V = 10.0 ** rng.uniform(math.log10(V_range[0]), math.log10(V_range[1]), size=n_states)
+    x = rng.dirichlet(np.full(n_species, alpha), size=n_states)
+    ntot = P * V / (R_GAS * T)
+    nmol = x[:, : n_species - 1] * ntot[:, None]
+    return (T.astype(np.float64), P.astype(np.float64), V.astype(np.float64),
+            np.ascontiguousarray(nmol, dtype=np.float64))
+
+
+def config_conc_states(cfg: int, n_states: Optional[int] = None, seed_offset: int = 2000):
+    c = CONFIGS[cfg]
+    n = c["n_states"] if n_states is None else n_states
+    return generate_conc_states(c["n_species"], n, seed=SEED_BASE + cfg + seed_offset)
+
+
 # ----------------------------------------------------------------------------------------------
 # the benchmark workloads (synthetic stand-ins for the paper's four kinetic models, Table T:models)
 

@@ -53,6 +53,13 @@ MUTANTS = [
     ("source_terms.inc", "u_k[k] = (HRT - 1.0) * PJO_R * T / m->W[k];", "u_k[k] = HRT * PJO_R * T / m->W[k];"),
     ("source_terms.inc", "SCALAR P = rho * (sYW + sYWc) * PJO_R * T;", "SCALAR P = rho * PJO_R * T;"),
     ("pyjac_oracle.c", "cimag(fz[row]) / h - (col == 0 ? 0.0 : dfN[row]);", "cimag(fz[row]) / h;"),
+    ("source_terms.inc", "f[1] = V * (fY[0] / T + PJO_R * T / P * (O + Oc));", "f[1] = V * (PJO_R * T / P * (O + Oc));"),
+    ("source_terms.inc", "X[N - 1] = M - (s + sc);", "X[N - 1] = M + (s + sc);"),
+    ("source_terms.inc", "for (int k = 0; k < N; ++k) Y[k] = X[k] * m->W[k] / rho;",
+     "for (int k = 0; k < N; ++k) Y[k] = X[k] / rho;"),
+    ("source_terms.inc", "if (k < N - 1) f[2 + k] = V * w;", "if (k < N - 1) f[2 + k] = w;"),
+    ("pyjac_oracle.c", "else { nz[col - 2] += I * h * Vs; dh = h * Vs; }", "else { nz[col - 2] += I * h * Vs; dh = h; }"),
+    ("pyjac_oracle.c", "else if (col == 1) { Vz += I * h * Vs; dh = h * Vs; }", "else if (col == 1) { Vz += I * h; dh = h * Vs; }"),
 ]
 
 EPS = 2.0 ** -52
@@ -167,6 +174,47 @@ def _pins(lib) -> list:
         big = np.abs(Jcv[:, col]) > 1e-3 * np.abs(Jcv[:, col]).max()
         if not np.all(np.abs(d - Jcv[:, col])[big] <= 1e-5 * np.abs(Jcv[big, col])):
             failed.append("cv jacobian")
+            break
+    # 6. molar-concentration basis: one elementary reaction A + B -> C with D inert, in closed form
+    #    (source terms, n_A and V columns); element conservation with the last species' rate implied
+    #    by the ideal-gas law; the T and first n column against central differences
+    A, beta, Ta = 3.0e5, 0.7, 4000.0
+    r = synth.Reaction(kind=synth.KIND_ELEMENTARY, rev_mode=synth.REV_IRREVERSIBLE, reac=[(0, 1), (1, 1)],
+                       prod=[(2, 1)], arr=(A, beta, Ta))
+    om3 = oracle.load_model(synth.to_bytes(mechs.one_reaction_model(r, [(1, 0), (0, 1), (1, 1), (2, 0)])), lib=lib)
+    Tc, Pc, Vc = np.array([1234.0]), np.array([3.0 * P_ATM]), np.array([2.5e-3])
+    nc = np.array([[0.2, 0.3, 0.1]]) * Pc[0] * Vc[0] / (R_GAS * Tc[0])
+    Jc, fc = om3.jacobian_conc(Tc, Pc, Vc, nc)
+    k = A * Tc[0] ** beta * math.exp(-Ta / Tc[0])
+    CA, CB = nc[0, 0] / Vc[0], nc[0, 1] / Vc[0]
+    ok = (abs(fc[0, 2] + Vc[0] * k * CA * CB) <= 1e-12 * Vc[0] * k * CA * CB
+          and abs(Jc[0, 2, 2] + k * CB) <= 1e-12 * k * CB and abs(Jc[0, 2, 1] - k * CA * CB) <= 1e-12 * k * CA * CB)
+    if not ok:
+        failed.append("conc closed form")
+    Nm = mixed.n_species
+    Tn, Pn, Vn, nn = synth.generate_conc_states(Nm, 3, seed=33, alpha=3.0)
+    Jn, fn = omm.jacobian_conc(Tn, Pn, Vn, nn)
+    Wm = np.array([sp.W for sp in mixed.species])
+    Em = np.array([sp.elem for sp in mixed.species], dtype=np.float64)
+    for s in range(3):
+        dnN = Pn[s] * fn[s, 1] / (R_GAS * Tn[s]) - Pn[s] * Vn[s] * fn[s, 0] / (R_GAS * Tn[s] ** 2) - fn[s, 2:].sum()
+        rates = np.concatenate([fn[s, 2:], [dnN]])
+        if not np.all(np.abs(rates @ Em) <= 1e-12 * (np.abs(rates) @ Em + 1e-300)):
+            failed.append("conc elements")
+            break
+    x = np.concatenate([[Tn[0], Vn[0]], nn[0]])
+    nN = Pn[0] * Vn[0] / (R_GAS * Tn[0]) - nn[0].sum()
+    for col in (0, 1, 2):
+        h = 1e-5 * (abs(x[col]) if col < 2 else min(abs(x[col]), nN))
+        d = []
+        for st in (-2, -1, 1, 2):
+            xp = x.copy()
+            xp[col] += st * h
+            d.append(omm.dydt_conc(xp[:1], Pn[:1], xp[1:2], xp[2:][None])[0])
+        fd = (d[0] - 8 * d[1] + 8 * d[2] - d[3]) / (12 * h)
+        big = np.abs(Jn[0, :, col]) > 1e-3 * np.abs(Jn[0, :, col]).max()
+        if not np.all(np.abs(fd - Jn[0, :, col])[big] <= 1e-6 * np.abs(Jn[0, big, col])):
+            failed.append("conc jacobian")
             break
     return failed
 
