@@ -938,7 +938,7 @@ int pjo_eval_dydt_conc(const pjo_mech *m, int64_t n, const double *T, const doub
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 4) num_threads(pjo_max_threads())
     for (int64_t s = 0; s < n; ++s) {
-        double *wk = malloc((9 * (size_t)N + (size_t)m->nr + 2) * sizeof(double));
+        double *wk = malloc((6 * (size_t)N + (size_t)m->nr) * sizeof(double));
         if (!wk) { err = 1; continue; }
         conc_rhs_d(m, T[s], P[s], V[s], nmol + s * ldn, dydt + s * ldd, NULL, wk);
         free(wk);

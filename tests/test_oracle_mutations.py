@@ -53,11 +53,11 @@ MUTANTS = [
     ("source_terms.inc", "u_k[k] = (HRT - 1.0) * PJO_R * T / m->W[k];", "u_k[k] = HRT * PJO_R * T / m->W[k];"),
     ("source_terms.inc", "SCALAR P = rho * (sYW + sYWc) * PJO_R * T;", "SCALAR P = rho * PJO_R * T;"),
     ("pyjac_oracle.c", "cimag(fz[row]) / h - (col == 0 ? 0.0 : dfN[row]);", "cimag(fz[row]) / h;"),
-    ("source_terms.inc", "f[1] = V * (fY[0] / T + PJO_R * T / P * (O + Oc));", "f[1] = V * (PJO_R * T / P * (O + Oc));"),
+    ("source_terms.inc", "f[1] = V * (f[0] / T + PJO_R * T / P * (O + Oc));", "f[1] = V * (PJO_R * T / P * (O + Oc));"),
     ("source_terms.inc", "X[N - 1] = M - (s + sc);", "X[N - 1] = M + (s + sc);"),
-    ("source_terms.inc", "for (int k = 0; k < N; ++k) Y[k] = X[k] * m->W[k] / rho;",
-     "for (int k = 0; k < N; ++k) Y[k] = X[k] / rho;"),
-    ("source_terms.inc", "if (k < N - 1) f[2 + k] = V * w;", "if (k < N - 1) f[2 + k] = w;"),
+    ("source_terms.inc", "H[k] = HRT * PJO_R * T;", "H[k] = HRT * PJO_R;"),
+    ("source_terms.inc", "FN(acc)(&K, &Kc, X[k] * cpR * PJO_R);", "FN(acc)(&K, &Kc, cpR * PJO_R);"),
+    ("source_terms.inc", "if (k < N - 1) f[2 + k] = V * wk_;", "if (k < N - 1) f[2 + k] = wk_;"),
     ("pyjac_oracle.c", "else { nz[col - 2] += I * h * Vs; dh = h * Vs; }", "else { nz[col - 2] += I * h * Vs; dh = h; }"),
     ("pyjac_oracle.c", "else if (col == 1) { Vz += I * h * Vs; dh = h * Vs; }", "else if (col == 1) { Vz += I * h; dh = h * Vs; }"),
 ]
@@ -201,6 +201,13 @@ def _pins(lib) -> list:
         rates = np.concatenate([fn[s, 2:], [dnN]])
         if not np.all(np.abs(rates @ Em) <= 1e-12 * (np.abs(rates) @ Em + 1e-300)):
             failed.append("conc elements")
+            break
+        a = [(sp.a_low if Tn[s] < sp.T_mid else sp.a_high) for sp in mixed.species]
+        H = np.array([R_GAS * _H_quad(a[i], Tn[s]) for i in range(Nm)])
+        cpm = np.array([R_GAS * np.polynomial.polynomial.polyval(Tn[s], a[i][:5]) for i in range(Nm)])
+        n_all = np.concatenate([nn[s], [Pn[s] * Vn[s] / (R_GAS * Tn[s]) - nn[s].sum()]])
+        if abs(rates @ H + (n_all @ cpm) * fn[s, 0]) > 1e-11 * np.abs(rates * H).sum():
+            failed.append("conc enthalpy")
             break
     x = np.concatenate([[Tn[0], Vn[0]], nn[0]])
     nN = Pn[0] * Vn[0] / (R_GAS * Tn[0]) - nn[0].sum()
