@@ -125,6 +125,34 @@ PJ_API int pj_eval_jacobian_cv(const pj_mech *m, int64_t n, const double *T, con
                                int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream);
 
 /*
+ * Molar-concentration basis at constant pressure, as a sparse Jacobian: the formulation the paper
+ * names as future work (Section 3.4, where it says the concentration basis makes the constant-
+ * pressure Jacobian far sparser, and Section 6). State (T, V, n_1..n_{N-1}) at fixed P: n_k moles of
+ * species k in the volume V (m^3); n_N = P V / (R T) - sum_{k<N} n_k by the ideal-gas law, so that
+ * [X_k] = n_k / V and [X_N] = P / (R T) - sum_{k<N} [X_k]. Source terms, in state order:
+ *   dT/dt (Eq. e:dTdt),  dV/dt = V (dT/dt / T + (R T / P) sum_k omega_k),  dn_k/dt = V omega_k,
+ * with omega_k the paper's molar production rates (Section 2). The Jacobian is
+ * d(dT/dt, dV/dt, dn_k/dt) / d(T, V, n_1..n_{N-1}), an (N+1) x (N+1) matrix in CSR form with a
+ * pattern fixed per model (pj_conc_pattern): rows T and V dense; species row k holds columns T, V and
+ * the n_j of species that share a reaction with k (as reactant, product, third-body species or
+ * non-unity efficiency), or every n_j when species N takes part in one of k's reactions.
+ *
+ * pj_conc_pattern: *nnz = the number of stored entries; row_ptr[N+2] and col_idx[nnz] (host
+ * memory, both or neither) receive the pattern, columns ascending within a row. Errors: PJ_EINVAL.
+ *
+ * pj_eval_jacobian_conc: T[n] (K), P[n] (Pa), V[n] (m^3), nmol[n][ldn >= N-1] (mol) in;
+ * jac[n][ldj >= nnz] out, the values of each state's CSR entries in pattern order; dydt (or NULL)
+ * [n][ldd >= N+1] out, the source terms in state order. Device pointers; asynchronous on stream;
+ * the launch shape is the Jacobian's (pj_set_launch which = 1). Errors: PJ_EINVAL (null model or
+ * pointer, n < 0, ldn < N-1, ldj < nnz, ldd < N+1, host pointer), PJ_EUNSUPPORTED (N < 2, or one
+ * state's working set does not fit in shared memory), PJ_ECUDA (launch failure).
+ */
+PJ_API int pj_conc_pattern(const pj_mech *m, int64_t *nnz, int32_t *row_ptr, int32_t *col_idx);
+PJ_API int pj_eval_jacobian_conc(const pj_mech *m, int64_t n, const double *T, const double *P, const double *V,
+                                 const double *nmol, int64_t ldn, double *jac, int64_t ldj, double *dydt,
+                                 int64_t ldd, void *stream);
+
+/*
  * End-to-end variant of pj_eval_jacobian on HOST buffers (pinned host memory gives full copy
  * bandwidth; pageable memory works but is slower). The states are processed in chunks of
  * chunk_states (<= 0: the library picks); each chunk is copied to the device, evaluated and copied

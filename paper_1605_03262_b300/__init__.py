@@ -75,6 +75,8 @@ def load_library(path: str = LIB_PATH):
             "pj_eval_jacobian": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
             "pj_eval_dydt_cv": ([vp, i64, vp, vp, vp, i64, vp, i64, vp], i32),
             "pj_eval_jacobian_cv": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
+            "pj_conc_pattern": ([vp, ctypes.POINTER(i64), vp, vp], i32),
+            "pj_eval_jacobian_conc": ([vp, i64, vp, vp, vp, vp, i64, vp, i64, vp, i64, vp], i32),
             "pj_fd_workspace_bytes": ([vp, i64, ctypes.POINTER(sz)], i32),
             "pj_eval_jacobian_fd": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, sz, vp], i32),
             "pj_eval_jacobian_host": ([vp, i64, vp, vp, vp, i64, vp, i64, vp, i64, i64], i32),
@@ -207,12 +209,13 @@ class Model:
         return b.value
 
     # -- evaluation on device tensors ----------------------------------------------------------
-    def _inputs(self, T, P, Y):
+    def _inputs(self, T, P, Y, width=None):
         T = _as_f64_cuda(T, "T", self.device).contiguous().reshape(-1)
         P = _as_f64_cuda(P, "P", self.device).contiguous().reshape(-1)
         Y = _as_f64_cuda(Y, "Y", self.device)
-        if Y.dim() != 2 or Y.shape[1] < self.n_species or Y.stride(1) != 1:
-            raise ValueError("Y must be (n, >= N) with unit stride along species")
+        width = self.n_species if width is None else width
+        if Y.dim() != 2 or Y.shape[1] < width or Y.stride(1) != 1:
+            raise ValueError("the per-species input must be (n, >= %d) with unit stride along species" % width)
         n = Y.shape[0]
         if T.shape[0] != n or P.shape[0] != n:
             raise ValueError("T, P and Y must describe the same number of states")
@@ -233,6 +236,40 @@ class Model:
     def eval_jacobian_cv(self, T, rho, Y, out=None, dydt: bool = False, dydt_out=None, stream=None):
         """Constant-volume analytical Jacobian (n, N+1, N+1) [, dydt (n, N+1)] at fixed density."""
         return self._jacobian(library().pj_eval_jacobian_cv, T, rho, Y, out, dydt, dydt_out, stream)
+
+    def conc_pattern(self):
+        """CSR pattern (row_ptr (N+2,), col_idx (nnz,), int32 numpy arrays) of the molar-concentration
+        basis Jacobian, rows and columns in state order (T, V, n_1..n_{N-1})."""
+        import numpy as np
+        nnz = ctypes.c_int64()
+        _check(library().pj_conc_pattern(self._h, ctypes.byref(nnz), None, None))
+        rp = np.empty(self.n_species + 2, dtype=np.int32)
+        ci = np.empty(nnz.value, dtype=np.int32)
+        _check(library().pj_conc_pattern(self._h, ctypes.byref(nnz), rp.ctypes.data_as(ctypes.c_void_p),
+                                         ci.ctypes.data_as(ctypes.c_void_p)))
+        return rp, ci
+
+    def eval_jacobian_conc(self, T, P, V, nmol, out=None, dydt: bool = False, dydt_out=None, stream=None):
+        """Sparse Jacobian of the molar-concentration basis at constant pressure for states
+        (T, V, n_1..n_{N-1}) at pressures P: the values of every state's CSR entries, (n, nnz) in the
+        order of conc_pattern() [, source terms (n, N+1) in state order]."""
+        torch = _torch()
+        N = self.n_species
+        T, P, nmol, n = self._inputs(T, P, nmol, N - 1)
+        V = _as_f64_cuda(V, "V", self.device).contiguous().reshape(-1)
+        if V.shape[0] != n:
+            raise ValueError("V must hold one volume per state")
+        nnz = ctypes.c_int64()
+        _check(library().pj_conc_pattern(self._h, ctypes.byref(nnz), None, None))
+        if out is None:
+            out = torch.empty((n, nnz.value), dtype=torch.float64, device=self.device)
+        f = None
+        if dydt or dydt_out is not None:
+            f = dydt_out if dydt_out is not None else torch.empty((n, N + 1), dtype=torch.float64, device=self.device)
+        _check(library().pj_eval_jacobian_conc(self._h, n, _ptr(T), _ptr(P), _ptr(V), _ptr(nmol), nmol.stride(0),
+                                               _ptr(out), out.stride(0), _ptr(f), f.stride(0) if f is not None else 0,
+                                               _stream_handle(stream)))
+        return (out, f) if f is not None else out
 
     def _dydt(self, fn, T, P, Y, out, stream):
         torch = _torch()

@@ -195,6 +195,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
            o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk), o_scc = push(blob, im.s_comb_chunk),
            o_scb = push(blob, im.s_comb), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst),
            o_cpf = push(blob, im.c_pfirst);
+    size_t o_ccp = push(blob, im.cc_ptr), o_ccs = push(blob, im.cc_src), o_ccc = push(blob, im.cc_col),
+           o_dnu = push(blob, im.rx_dnu);
     pj::MathTables tables;
     pj::build_math_tables(tables);
     std::vector<pj::MathTables> tvec(1, tables);
@@ -277,6 +279,11 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.s_comb_chunk = reinterpret_cast<const int2 *>(b + o_scc);
     d.s_comb = reinterpret_cast<const int4 *>(b + o_scb);
     d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
+    d.cc_nnz = int(im.cc_src.size());
+    d.cc_ptr = reinterpret_cast<const int *>(b + o_ccp);
+    d.cc_src = reinterpret_cast<const int *>(b + o_ccs);
+    d.cc_col = reinterpret_cast<const int *>(b + o_ccc);
+    d.rx_dnu = reinterpret_cast<const double *>(b + o_dnu);
     m->dev_model = reinterpret_cast<const pj::DevModel *>(b + o_dm);
     e = cudaMemcpy(b + o_dm, &d, sizeof(d), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -289,6 +296,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     m->NE = im.NE;
     m->dev_bytes = blob.size();
     m->perm = im.perm;
+    m->cc_ptr = im.cc_ptr;
+    m->cc_col = im.cc_col;
     m->jac_cfg = pick_default(m, true);
     m->dydt_cfg = pick_default(m, false);
     *out = m;
@@ -419,6 +428,73 @@ int pj_eval_jacobian(const pj_mech *m, int64_t n, const double *T, const double 
 int pj_eval_jacobian_cv(const pj_mech *m, int64_t n, const double *T, const double *rho, const double *Y,
                         int64_t ldy, double *jac, int64_t ldj, double *dydt, int64_t ldd, void *stream) {
     return eval_jacobian("pj_eval_jacobian_cv", true, m, n, T, rho, Y, ldy, jac, ldj, dydt, ldd, stream);
+}
+
+int pj_conc_pattern(const pj_mech *m, int64_t *nnz, int32_t *row_ptr, int32_t *col_idx) {
+    if (!m || !nnz) return fail(PJ_EINVAL, "pj_conc_pattern: null argument");
+    const int N = m->N;
+    const int64_t cc = m->cc_ptr.empty() ? 0 : m->cc_ptr.back();
+    *nnz = 2 * int64_t(N + 1) + 2 * int64_t(N - 1) + cc;
+    if (!row_ptr && !col_idx) return PJ_OK;
+    if (!row_ptr || !col_idx) return fail(PJ_EINVAL, "pj_conc_pattern: give both row_ptr and col_idx, or neither");
+    int64_t o = 0;
+    for (int r = 0; r < 2; ++r) {                   // T and V rows: dense
+        row_ptr[r] = int32_t(o);
+        for (int c = 0; c <= N; ++c) col_idx[o++] = c;
+    }
+    for (int k = 0; k < N - 1; ++k) {               // species rows: T, V, then the pattern
+        row_ptr[2 + k] = int32_t(o);
+        col_idx[o++] = 0;
+        col_idx[o++] = 1;
+        for (int e = m->cc_ptr[k]; e < m->cc_ptr[k + 1]; ++e) col_idx[o++] = 2 + m->cc_col[e];
+    }
+    row_ptr[N + 1] = int32_t(o);
+    return PJ_OK;
+}
+
+int pj_eval_jacobian_conc(const pj_mech *m, int64_t n, const double *T, const double *P, const double *V,
+                          const double *nmol, int64_t ldn, double *jac, int64_t ldj, double *dydt, int64_t ldd,
+                          void *stream) {
+    const std::string f("pj_eval_jacobian_conc");
+    if (!m) return fail(PJ_EINVAL, f + ": null model");
+    if (n < 0) return fail(PJ_EINVAL, f + ": n < 0");
+    if (m->N < 2) return fail(PJ_EUNSUPPORTED, f + ": the basis needs at least two species");
+    if (ldn < m->N - 1) return fail(PJ_EINVAL, f + ": ldn < number of species - 1");
+    int64_t nnz = 0;
+    pj_conc_pattern(m, &nnz, nullptr, nullptr);
+    if (ldj < nnz) return fail(PJ_EINVAL, f + ": ldj < the pattern's number of entries (pj_conc_pattern)");
+    if (dydt && ldd < m->N + 1) return fail(PJ_EINVAL, f + ": ldd < number of species + 1");
+    if (n == 0) return PJ_OK;
+    int rc;
+    if ((rc = check_model_device(m)) || (rc = check_device_ptr(T, m->device, "T")) ||
+        (rc = check_device_ptr(P, m->device, "P")) || (rc = check_device_ptr(V, m->device, "V")) ||
+        (rc = check_device_ptr(nmol, m->device, "nmol")) || (rc = check_device_ptr(jac, m->device, "jac")))
+        return rc;
+    if (dydt && (rc = check_device_ptr(dydt, m->device, "dydt"))) return rc;
+    const pj::LaunchCfg &c = m->jac_cfg;
+    if (c.groups < 1)
+        return fail(PJ_EUNSUPPORTED, "one state's working set does not fit in shared memory for this model");
+    pj::KParams p{};
+    p.m = m->dev;
+    p.sc = pj::make_scratch(m->dev, true, c.wps);
+    p.n = n;
+    p.T = T;
+    p.P = P;
+    p.Y = nmol;
+    p.ldy = ldn;
+    p.V = V;
+    p.jac = jac;
+    p.ldj = ldj;
+    p.dydt = dydt;
+    p.ldd = ldd;
+    p.groups = c.groups;
+    p.shared_const = pj::shared_const_doubles(m->N);
+    DeviceProps dp = device_props(m->device);
+    long long need = (n + c.groups - 1) / c.groups;
+    int blocks = int(std::min<long long>(need, (long long)dp.sms * c.ctas_per_sm));
+    cudaError_t e = pj::launch_conc(p, c.wps, blocks, smem_bytes(m, true, c), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return PJ_OK;
 }
 
 int pj_set_launch(pj_mech *m, int which, const pj_launch *cfg) {

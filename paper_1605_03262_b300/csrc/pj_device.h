@@ -97,6 +97,12 @@ struct DevModel {
     const int2 *s_comb_chunk; // per row chunk: offset into s_comb, number of split entries
     const int4 *s_comb;       // split row entry: staged position, first partial slot, partials, 0
     const MathTables *tables;  // exp/log tables (pj_fastmath.cuh)
+    // molar-concentration basis: per species row k < N-1, its pattern entries cc_ptr[k]..cc_ptr[k+1]
+    // (columns n_j in ascending j); cc_src = the sparse-block entry of (k, j), or -1 where the row
+    // is dense only through species N. rx_dnu: sum_k nu_ki per reaction.
+    int cc_nnz;
+    const int *cc_ptr, *cc_src, *cc_col;
+    const double *rx_dnu;
 };
 
 // Doubles of one warp's row stage: rpc staged rows and the partial slots of split entries.
@@ -120,6 +126,7 @@ struct KParams {
     long long ldd;
     int groups;               // states processed concurrently per CTA
     int shared_const;         // doubles of per-CTA constants at the start of shared memory
+    const double *V;          // volumes (molar-concentration basis only)
 };
 
 // Batched form: one entry per (model, state batch) of a plan, and tiles of consecutive states.
@@ -130,6 +137,7 @@ struct BatchIO {
     long long ldj;
     double *dydt;
     long long ldd;
+    const double *V;          // volumes (molar-concentration basis only)
 };
 
 struct BatchItem {

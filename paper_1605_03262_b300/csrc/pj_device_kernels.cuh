@@ -636,7 +636,9 @@ struct Prep {
 // species, the mixture sums, and the concentrations. Ends with the group synchronised. CV: the
 // input is rho instead of p, and the energy arrays hold c_v,k = c_p,k - R/W_k and the molar
 // internal energy U_k = H_k - R T (Section 3.3), so that the energy row below is the constant-volume one.
-template <bool JAC, int WPS, bool CV = false>
+// CONC: the molar-concentration basis at constant pressure; the input is (T, P, V, n_1..n_{N-1}),
+// [X_k] = n_k / V and [X_N] = P / (R T) - sum_{k<N} [X_k] by the ideal-gas law.
+template <bool JAC, int WPS, bool CV = false, bool CONC = false>
 __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
                                            const StateIO &io, long long st, const Grp &g) {
     const int N = m.N;
@@ -649,12 +651,29 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
     StateScalars s;
     s.T = __ldg(io.T + st);
     if constexpr (CV) s.rho = __ldg(io.P + st);
-    else s.P = __ldg(io.P + st);
+    else if constexpr (!CONC) s.P = __ldg(io.P + st);
     s.invT = 1.0 / s.T;
     s.lnT = fast_log(s.T, m.tables);
     const double *Ys = io.Y + st * io.ldy;
     double *sY = sf;   // Y parks in the f array until the concentrations exist
-    for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
+    double rho_c = 0.0;
+    if constexpr (CONC) {
+        // every warp forms the sums in the same lane order, so all hold the same bits
+        s.P = __ldg(io.P + st);
+        s.Ctot = s.P / (kR * s.T);
+        const double invV = 1.0 / __ldg(io.V + st);
+        double sx = 0.0;
+        for (int k = lane; k < N - 1; k += 32) sx += __ldg(Ys + k) * invV;
+        sx = warp_sum(sx);
+        for (int k = t; k < N; k += G) sC[k] = k < N - 1 ? __ldg(Ys + k) * invV : s.Ctot - sx;
+        group_sync<WPS>(g);
+        for (int k = lane; k < N; k += 32) rho_c = fma(sC[k], __ldg(m.W + k), rho_c);
+        rho_c = warp_sum(rho_c);
+        const double irho = 1.0 / rho_c;
+        for (int k = t; k < N; k += G) sY[k] = sC[k] * __ldg(m.W + k) * irho;
+    } else {
+        for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
+    }
     for (int k = t; k < N; k += G) {
         const Thermo th = species_thermo<JAC>(m, k, s.T, s.invT, s.lnT);
         scp[k] = kR * sInvW[k] * (CV ? th.cpR - 1.0 : th.cpR);
@@ -714,22 +733,127 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
     if constexpr (CV) {                                 // p = rho R T / W (Eq. e:state)
         s.Ctot = s.rho * sYW;
         s.P = s.Ctot * kR * s.T;
+    } else if constexpr (CONC) {
+        s.rho = rho_c;
     } else {
         s.Ctot = s.P / (kR * s.T);
         s.rho = s.Ctot * s.W;
     }
     s.lnP = fast_log(s.P, m.tables);
-    for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
+    if constexpr (!CONC)
+        for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
     group_sync<WPS>(g);
     return Prep{s, cp, dcpdT};
+}
+
+// Molar-concentration basis at constant pressure: state (T, V, n_1..n_{N-1}) at fixed P, with
+// dT/dt (Eq. e:dTdt), dV/dt = V (dT/dt / T + (R T / P) sum_k omega_k) (the ideal-gas law at fixed
+// P) and dn_k/dt = V omega_k. Its Jacobian reuses the constant-pressure reaction stage and gathers:
+// with D_kl = d omega_k / d[X_l] = sum_i nu_ki b'_il at fixed T and [M] = P / (R T),
+//   d(dn_k/dt)/dn_j = D_kj - D_kN,
+//   d(dn_k/dt)/dV   = omega_k + G_k / W + [M] D_kN   (G_k = sum_i nu_ki a_i, a_i = -W (c sigma + psi R E)),
+//   d(dn_k/dt)/dT   = V (Theta_k - (d(dn_k/dt)/dV) / T)   (Theta_k = sum_i nu_ki theta_i),
+// and the T and V rows from the column sums sum_k H_k D_kj (HS_j) and sum_k D_kj (NS_j). Rows are
+// sparse: species k's row holds T, V and the columns n_j of its pattern (the species of k's
+// reactions, or all of them when species N takes part in one), in the static order of cc_ptr /
+// cc_src; the T and V rows are dense. Output per state: the CSR values, rows in state order.
+template <int WPS>
+__device__ __noinline__ void conc_finish(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
+                                         const StateIO &io, long long st, const Grp &g, const StateScalars &s,
+                                         double cp, double J00, double HA, double Hf) {
+    const int N = m.N;
+    const int G = WPS ? WPS * 32 : g.G, NW = WPS ? WPS : g.wps;
+    const int t = g.t, lane = g.lane, wg = g.wg;
+    const double *sInvW = smem_const + 128 + N;
+    const double *scp = S + sc.cpk, *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sf = S + sc.f, *sHS = S + sc.HS;
+    const double *sb = S + sc.b;
+    double *sNS = S + sc.rows;                          // free once the gathers are combined
+    // NS_j = sum_k D_kj = sum_i dnu_i b'_ij over the column lists
+    for (int j = t; j < N; j += G) {
+        double v = 0.0;
+        for (int e = __ldg(m.col_ptr + j); e < __ldg(m.col_ptr + j + 1); ++e)
+            v = fma(__ldg(m.rx_dnu + __ldg(m.col_rxn + e)), sb[__ldg(m.col_slot + e)], v);
+        sNS[j] = v;
+    }
+    // SA = sum_k A_k / W_k, SF = sum_k f_k / W_k, SJ = sum_k J_k0 / W_k (every warp, same order)
+    double SA = 0.0, SF = 0.0, SJ = 0.0, unused = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        SA = fma(sA[k], sInvW[k], SA);
+        SF = fma(sf[k], sInvW[k], SF);
+        SJ = fma(sJk0[k], sInvW[k], SJ);
+    }
+    warp_sum4(SA, SF, SJ, unused);
+    group_sync<WPS>(g);
+    const double V = __ldg(io.V + st), invT = s.invT, M = s.Ctot, W = s.W, rho = s.rho;
+    const double invcp = 1.0 / cp, WN = __ldg(m.W + N - 1);
+    const double fT = -Hf * invcp;
+    const double HSN = sHS[N - 1], NSN = sNS[N - 1], cpN = scp[N - 1];
+    const double Z = fma(fT * WN, cpN, fma(WN, HSN, HA));
+    const double iWcp = invcp / W;
+    const double JTT = fma(Z * invT, iWcp, J00);
+    const double JTV = -Z * iWcp / V;
+    const double JVV = fT * invT + V * invT * JTV + (SA + NSN);
+    const double JVT = V * (JTT * invT - fT * invT * invT + W * SF * invT + W * SJ - (SA + NSN) * invT);
+    const double eT = -invcp / (V * rho);
+    double *out = io.jac + st * io.ldj;
+    const int ld = N + 1;
+    // T and V rows (dense, N + 1 columns each)
+    for (int x = t; x < 2 * ld; x += G) {
+        const int row = x >= ld, col = x - row * ld;
+        double v;
+        if (col < 2) {
+            v = row ? (col ? JVV : JVT) : (col ? JTV : JTT);
+        } else {
+            const int j = col - 2;
+            const double Wj = __ldg(m.W + j);
+            const double jt = eT * (fma(Wj, sHS[j], -WN * HSN) + fT * (Wj * scp[j] - WN * cpN));
+            v = row ? fma(V * invT, jt, (sNS[j] - NSN) / M) : jt;
+        }
+        __stcs(out + x, v);
+    }
+    // species rows: warp wg takes rows wg, wg + NW, ...
+    for (int k = wg; k < N - 1; k += NW) {
+        const int e0 = __ldg(m.cc_ptr + k), len = __ldg(m.cc_ptr + k + 1) - e0;
+        double *o = out + 2 * ld + 2 * k + e0;
+        double DkN = 0.0;                               // d omega_k / d[X_N]
+        const int eN = __ldg(m.colN_nnz + k);
+        if (eN >= 0)
+            for (int c = __ldg(m.nnz_cptr + eN); c < __ldg(m.nnz_cptr + eN + 1); ++c)
+                DkN = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], DkN);
+        if (lane < 2) {
+            const double iWk = sInvW[k];
+            const double JV = M * fma(iWk, sA[k], DkN);
+            __stcs(o + lane, lane ? JV : V * fma(rho * iWk, sJk0[k], -JV * invT));
+        }
+        for (int e = lane; e < len; e += 32) {
+            const int src = __ldg(m.cc_src + e0 + e);
+            double v = 0.0;
+            if (src >= 0)
+                for (int c = __ldg(m.nnz_cptr + src); c < __ldg(m.nnz_cptr + src + 1); ++c)
+                    v = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], v);
+            __stcs(o + 2 + e, v - DkN);
+        }
+    }
+    if (io.dydt) {
+        double *f = io.dydt + st * io.ldd;
+        for (int k = t; k <= N; k += G) {
+            double v;
+            if (k == 0) v = fT;
+            else if (k == 1) v = V * fma(fT, invT, W * SF);
+            else v = V * rho * sInvW[k - 2] * sf[k - 2];
+            f[k] = v;
+        }
+    }
+    group_sync<WPS>(g);
 }
 
 // One round of a CTA: each group evaluates one state (prep, gathers, rows), and the reaction stage
 // of the round's states runs over the whole CTA. All threads of the CTA call this together.
 // active = false: a thread without a state in this round (a group past the last state, or a
 // thread outside the model's groups), which takes part in the reaction stage only. gact groups
-// have states; group gg's scratch is S0 + gg * stride. CV: the constant-volume form.
-template <bool JAC, int WPS, bool CV = false>
+// have states; group gg's scratch is S0 + gg * stride. CV: the constant-volume form. CONC (with
+// JAC): the molar-concentration basis at constant pressure, written as sparse rows (below).
+template <bool JAC, int WPS, bool CV = false, bool CONC = false>
 __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
                                            const StateIO &io, long long st, const Grp &g, bool active, int gact,
                                            double *S0, int stride) {
@@ -743,7 +867,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     double *spart = S + sc.part;
     (void)sHS;
     Prep pp{};
-    if (active) pp = state_prep<JAC, WPS, CV>(m, sc, S, smem_const, io, st, g);
+    if (active) pp = state_prep<JAC, WPS, CV, CONC>(m, sc, S, smem_const, io, st, g);
     const StateScalars s = pp.s;
     const double cp = pp.cp, dcpdT = pp.dcpdT;
     double *sred = S + sc.red;
@@ -942,6 +1066,10 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         const double HSN = sHS[N - 1], cpN = scp[N - 1];
         const double e0 = Hf * invcp * invcp;
 
+        if constexpr (CONC) {
+            conc_finish<WPS>(m, sc, S, smem_const, io, st, g, s, cp, J00, HA, Hf);
+            return;
+        }
         // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
         //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
         const int ld = N + 1, RPC = m.rpc;
@@ -1089,7 +1217,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
 
 // Body of the evaluation kernel: the CTA's groups loop over rounds of p.groups states. The
 // runtime-specialised kernels call it with the model's sizes and offsets as constants.
-template <bool JAC, int WPS, bool CV>
+template <bool JAC, int WPS, bool CV, bool CONC = false>
 __device__ __forceinline__ void eval_kernel_body(const KParams &p) {
     extern __shared__ __align__(16) double smem[];
     const DevModel &m = p.m;
@@ -1104,18 +1232,18 @@ __device__ __forceinline__ void eval_kernel_body(const KParams &p) {
     double *S = smem + p.shared_const + size_t(g.grp) * p.sc.total;
     init_neutral<JAC>(m, p.sc, S, g.t);
     __syncthreads();
-    const StateIO io{p.T, p.P, p.Y, p.ldy, p.jac, p.ldj, p.dydt, p.ldd};
+    const StateIO io{p.T, p.P, p.Y, p.ldy, p.jac, p.ldj, p.dydt, p.ldd, p.V};
     double *S0 = smem + p.shared_const;
     for (long long base = (long long)blockIdx.x * p.groups; base < p.n; base += (long long)gridDim.x * p.groups) {
         const long long st = base + g.grp;
         const int gact = int(min((long long)p.groups, p.n - base));
-        eval_state<JAC, WPS, CV>(m, p.sc, S, smem, io, st, g, st < p.n, gact, S0, p.sc.total);
+        eval_state<JAC, WPS, CV, CONC>(m, p.sc, S, smem, io, st, g, st < p.n, gact, S0, p.sc.total);
     }
 }
 
-template <bool JAC, int WPS, bool CV>
+template <bool JAC, int WPS, bool CV, bool CONC = false>
 __global__ void __launch_bounds__(512, 1) pj_eval_kernel(const __grid_constant__ KParams p) {
-    eval_kernel_body<JAC, WPS, CV>(p);
+    eval_kernel_body<JAC, WPS, CV, CONC>(p);
 }
 
 // States [begin, end) of one tile of the batched form, in CTA rounds of it.groups states.

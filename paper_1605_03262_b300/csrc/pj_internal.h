@@ -42,6 +42,9 @@ struct HostImage {
     std::vector<int> g_chunk, h_chunk, c_chunk, s_chunk;   // (record offset, rows) per chunk
     int s_npart = 0;
     std::vector<int> s_comb_chunk, s_comb;                 // (offset, count) per chunk; 4 ints per entry
+    // molar-concentration basis: species-row pattern (DevModel::cc_ptr / cc_src / cc_col), sum_k nu_ki
+    std::vector<int> cc_ptr, cc_src, cc_col;
+    std::vector<double> rx_dnu;
 };
 
 
@@ -55,6 +58,7 @@ inline int default_wps(int N, bool jac) {
 int shared_const_doubles(int N);
 // cv: the constant-volume form, with p.P holding the densities rho instead of pressures.
 cudaError_t launch_eval(const KParams &p, bool jac, bool cv, int wps, int blocks, size_t smem, cudaStream_t stream);
+cudaError_t launch_conc(const KParams &p, int wps, int blocks, size_t smem, cudaStream_t stream);
 cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem);
 cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads, size_t smem, cudaStream_t stream);
 // Forward-difference Jacobian kernels (pj_fd.cu).
@@ -89,6 +93,7 @@ struct pj_mech {
     pj_host_staging *staging = nullptr;   // device buffers of pj_eval_jacobian_host (lazy)
     const pj::DevModel *dev_model = nullptr;   // device copy of dev (for batched plans)
     pj_spec *spec = nullptr;        // specialised kernels (pj_mech_specialize), or none
+    std::vector<int> cc_ptr, cc_col;   // molar-concentration basis: species-row pattern (host copy)
 };
 
 namespace pj {

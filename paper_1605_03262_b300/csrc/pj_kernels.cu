@@ -104,6 +104,28 @@ cudaError_t launch_eval(const KParams &p, bool jac, bool cv, int wps, int blocks
     return jac ? launch_t<true, false>(p, wps, blocks, smem, stream) : launch_t<false, false>(p, wps, blocks, smem, stream);
 }
 
+cudaError_t launch_conc(const KParams &p, int wps, int blocks, size_t smem, cudaStream_t stream) {
+    const int threads = wps * 32 * p.groups;
+    cudaError_t e = cudaSuccess;
+#define PJ_CASE(W)                                                                                        \
+    case W:                                                                                               \
+        e = cudaFuncSetAttribute(pj_eval_kernel<true, W, false, true>,                                    \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));                 \
+        if (e != cudaSuccess) return e;                                                                   \
+        pj_eval_kernel<true, W, false, true><<<blocks, threads, smem, stream>>>(p);                       \
+        return cudaGetLastError();
+    switch (wps) {
+        PJ_CASE(1)
+        PJ_CASE(2)
+        PJ_CASE(4)
+        PJ_CASE(8)
+        PJ_CASE(16)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef PJ_CASE
+}
+
 cudaError_t prepare_batch_kernel(bool jac, size_t dyn_smem, size_t *static_smem) {
     cudaFuncAttributes a{};
     cudaError_t e = jac ? cudaFuncGetAttributes(&a, pj_batch_kernel<true>) : cudaFuncGetAttributes(&a, pj_batch_kernel<false>);

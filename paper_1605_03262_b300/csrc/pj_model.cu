@@ -581,6 +581,27 @@ HostImage build_image(const void *buf, size_t len) {
         }
         for (int k = 0; k < N; ++k) im.row_ptr[k + 1] += im.row_ptr[k];
     }
+    // molar-concentration basis: species row k < N-1 holds the columns n_j (j < N-1) of its
+    // sparse-block entries, or every column when its row has an entry in column N (d/dn_j moves
+    // [X_N] by -1/V, so D_kN enters every column); ascending j
+    {
+        im.cc_ptr.assign(N, 0);
+        for (int k = 0; k < N - 1; ++k) {
+            const bool dense = im.colN_nnz[k] >= 0;
+            std::vector<int> at(N - 1, -1);
+            for (int e = im.row_ptr[k]; e < im.row_ptr[k + 1]; ++e)
+                if (im.nnz_col[e] < N - 1) at[im.nnz_col[e]] = e;
+            for (int j = 0; j < N - 1; ++j)
+                if (dense || at[j] >= 0) {
+                    im.cc_src.push_back(at[j]);
+                    im.cc_col.push_back(j);
+                }
+            im.cc_ptr[k + 1] = int(im.cc_src.size());
+        }
+        im.rx_dnu.assign(R, 0.0);
+        for (int i = 0; i < R; ++i)
+            for (auto &e : net[i]) im.rx_dnu[i] += e.second;
+    }
 
     // lane-balanced schedules; neutral items read the zero element appended to each array
     const unsigned zero_slot = unsigned(slot_total), zero_rxn = unsigned(R);

@@ -96,6 +96,17 @@ def test_cv_entry_points_reject_null_model(lib):
     assert lib.pj_eval_jacobian_cv(None, 4, None, None, None, 13, None, 196, None, 0, None) == -1
 
 
+def test_concentration_basis_entry_points_reject_null_model(lib):
+    lib.pj_conc_pattern.restype = ctypes.c_int
+    lib.pj_conc_pattern.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_void_p]
+    nnz = ctypes.c_int64(-7)
+    assert lib.pj_conc_pattern(None, ctypes.byref(nnz), None, None) == -1
+    lib.pj_eval_jacobian_conc.restype = ctypes.c_int
+    lib.pj_eval_jacobian_conc.argtypes = [ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 4 + \
+        [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.pj_eval_jacobian_conc(None, 4, None, None, None, None, 12, None, 300, None, 0, None) == -1
+
+
 def test_header_and_library_work_from_plain_c(tmp_path):
     """The ABI is C: the header compiles as C99 with warnings as errors, and a C program linked
     against the library gets the documented status codes and error text (no GPU needed)."""
