@@ -510,6 +510,58 @@ def cv_form(per_config: dict, steps: int, warmup: int):
     return out
 
 
+def conc_form(per_config: dict, steps: int, warmup: int):
+    """The molar-concentration basis at constant pressure (state T, V, n_1..n_{N-1}), written as a
+    sparse Jacobian: the same numbers of states as the constant-pressure Jacobian, at its launch
+    shape (the data-driven kernel: this form is not specialised), L2 flushed before each step.
+    Reports the pattern's size, the bytes written per state against the dense (N+1)^2, and the time
+    against the constant-pressure Jacobian's data-driven kernel on the same batch size."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    for cfg in (0, 1, 2, 3):
+        name = synth.CONFIGS[cfg]["name"]
+        if name not in per_config:
+            continue
+        model = synth.config_model(cfg)
+        N = model.n_species
+        n = per_config[name]["n_states"]
+        T, P, V, nmol = synth.config_conc_states(cfg, n)
+        g = pj.Model(synth.to_bytes(model))
+        lc = per_config[name]["launch"]
+        g.set_launch(lc["warps_per_state"], lc["states_per_cta"], lc["ctas_per_sm"])
+        rp, ci = g.conc_pattern()
+        nnz = len(ci)
+        Td, Pd, Vd, nd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, V, nmol))
+        vals = torch.empty((n, nnz), dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            flush.zero_()
+            g.eval_jacobian_conc(Td, Pd, Vd, nd, out=vals)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            g.eval_jacobian_conc(Td, Pd, Vd, nd, out=vals)
+            e_.record()
+            torch.cuda.synchronize()
+            ms.append(s_.elapsed_time(e_))
+        c_ms = float(np.median(ms))
+        dd_ms = per_config[name]["specialisation"]["data_driven_ms_median"]
+        out[name] = {"n_states": n, "nnz_per_state": nnz, "density": nnz / (N + 1) ** 2,
+                     "species_block_density": (nnz - 2 * (N + 1) - 2 * (N - 1)) / (N - 1) ** 2,
+                     "bytes_written_per_state": 8 * nnz, "dense_bytes_per_state": 8 * (N + 1) ** 2,
+                     "ms": c_ms, "jacobians_per_s": n / (c_ms * 1e-3),
+                     "hbm_write_gbs": n * nnz * 8 / (c_ms * 1e-3) / 1e9,
+                     "constant_pressure_data_driven_ms": dd_ms, "conc_over_constant_pressure": c_ms / dd_ms}
+        del vals
+        torch.cuda.empty_cache()
+    del flush
+    return out
+
+
 BATCH_MIX = ((0, 16384), (1, 65536), (2, 32768), (3, 2048))
 
 
@@ -774,6 +826,8 @@ def run_ours(args):
         if not (args.headline_only or args.no_fd) else None
     cvf = cv_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
                   args.warmup) if not args.headline_only else None
+    concf = conc_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
+                      args.warmup) if not args.headline_only else None
     serving = serving_form() if not (args.headline_only or args.no_serving) else None
     per_config[synth.CONFIGS[HEADLINE_CFG]["name"]] = {k: res[k] for k in ("n_states", "ms_per_step",
                                                                             "ms_median", "ms_min",
@@ -808,6 +862,7 @@ def run_ours(args):
         "batched_form": batched,
         "fd_form": fd,
         "cv_form": cvf,
+        "conc_form": concf,
         "serving_form": serving,
     }
     if not args.no_cpu_baseline:
@@ -862,13 +917,13 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_profile_case(spec: str, warmup: int, data_driven: bool = False):
+def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bool = False):
     """--profile CFG:N[:WPS,GROUPS] -- a small case for ncu: warm-up launches, then one Jacobian
     launch of the first N states of configuration CFG (inputs larger than L2 once N is a few
     thousand), at the given launch shape or else the autotuner's, with the kernel specialised for
     the model (the one the benchmark times; --data-driven for the other). The autotuner's own probe
     launches use a separate kernel instance count, so with an explicit shape the only launches
-    are the warm-ups and the profiled one."""
+    are the warm-ups and the profiled one. --conc: the molar-concentration basis kernel instead."""
     import torch
     import paper_1605_03262_b300 as pj
     parts = spec.split(":")
@@ -883,6 +938,15 @@ def run_profile_case(spec: str, warmup: int, data_driven: bool = False):
         g.set_launch(shape[0], shape[1], 1)
     else:
         autotune.autotune(g, blob, use_cache=False)
+    if conc:
+        Tc, Pc, Vc, nc = (torch.as_tensor(a, dtype=torch.float64, device="cuda")
+                          for a in synth.config_conc_states(cfg, n))
+        vals = torch.empty((n, len(g.conc_pattern()[1])), dtype=torch.float64, device="cuda")
+        for _ in range(warmup + 1):
+            g.eval_jacobian_conc(Tc, Pc, Vc, nc, out=vals)
+        torch.cuda.synchronize()
+        print("profile case done: concentration basis, cfg %d, %d states, launch %s" % (cfg, n, g.get_launch()))
+        return
     if not data_driven:
         specialise(g)
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
@@ -906,9 +970,10 @@ def main():
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference comparison")
     ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS]", help="one small profiling case (for ncu)")
     ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
+    ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
     args = ap.parse_args()
     if args.profile:
-        return run_profile_case(args.profile, args.warmup, args.data_driven)
+        return run_profile_case(args.profile, args.warmup, args.data_driven, args.conc)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
