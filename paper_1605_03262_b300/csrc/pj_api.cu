@@ -492,7 +492,17 @@ int pj_eval_jacobian_conc(const pj_mech *m, int64_t n, const double *T, const do
     DeviceProps dp = device_props(m->device);
     long long need = (n + c.groups - 1) / c.groups;
     int blocks = int(std::min<long long>(need, (long long)dp.sms * c.ctas_per_sm));
-    cudaError_t e = pj::launch_conc(p, c.wps, blocks, smem_bytes(m, true, c), static_cast<cudaStream_t>(stream));
+    const size_t smem = smem_bytes(m, true, c);
+    cudaError_t e;
+    if (const void *sk = pj::spec_conc_kernel(m, c)) {       // the model's specialised kernel
+        e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        void *args[] = {&p};
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(sk, dim3(blocks), dim3(c.wps * 32 * c.groups), args, smem,
+                                 static_cast<cudaStream_t>(stream));
+    } else {
+        e = pj::launch_conc(p, c.wps, blocks, smem, static_cast<cudaStream_t>(stream));
+    }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PJ_OK;
 }

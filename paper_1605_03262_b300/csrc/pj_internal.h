@@ -75,7 +75,8 @@ struct pj_host_staging;
 // Runtime-compiled kernels specialised for one model and its launch shapes (pj_nvrtc.cu).
 struct pj_spec {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t kern[4] = {};       // source terms / Jacobian (index 2 * jac) x constant p / v (+ cv)
+    cudaKernel_t kern[5] = {};       // source terms / Jacobian (index 2 * jac) x constant p / v (+ cv);
+                                     // 4: the molar-concentration basis Jacobian
     pj::LaunchCfg jac_cfg, dydt_cfg; // the shapes they were compiled for
     double compile_seconds = 0.0;
     size_t cubin_bytes = 0;
@@ -111,4 +112,6 @@ namespace pj {
 int specialize(pj_mech *m, std::string *err);
 void spec_release(pj_mech *m);
 const void *spec_kernel(const pj_mech *m, bool jac, bool cv, const LaunchCfg &c);
+const void *spec_conc_kernel(const pj_mech *m, const LaunchCfg &c);
+constexpr int kSpecKernels = 5;
 }  // namespace pj

@@ -88,8 +88,9 @@ void emit_scratch(std::string &s, const char *fn, const Scratch &c) {
     s += "}\n";
 }
 
-// Kernel names: index = jac * 2 + cv.
-const char *const kSpecNames[4] = {"pj_spec_dydt_cp", "pj_spec_dydt_cv", "pj_spec_jac_cp", "pj_spec_jac_cv"};
+// Kernel names: index = jac * 2 + cv; 4 = the molar-concentration basis Jacobian.
+const char *const kSpecNames[kSpecKernels] = {"pj_spec_dydt_cp", "pj_spec_dydt_cv", "pj_spec_jac_cp",
+                                              "pj_spec_jac_cv", "pj_spec_jac_conc"};
 
 std::string spec_source(const pj_mech &m, const LaunchCfg &cj, const LaunchCfg &cd) {
     std::string s = "#include \"pj_device_kernels.cuh\"\nnamespace {\n";
@@ -98,8 +99,8 @@ std::string spec_source(const pj_mech &m, const LaunchCfg &cj, const LaunchCfg &
     emit_scratch(s, "spec_scratch_dydt", make_scratch(m.dev, false, cd.wps));
     s += "}  // namespace\n";
     const int sconst = shared_const_doubles(m.N);
-    for (int k = 0; k < 4; ++k) {
-        const bool jac = k >= 2, cv = k & 1;
+    for (int k = 0; k < kSpecKernels; ++k) {
+        const bool jac = k >= 2, cv = k < 4 && (k & 1), conc = k == 4;
         const LaunchCfg &c = jac ? cj : cd;
         // launch bounds of the compiled shape: a CTA of fewer than 512 threads leaves each thread
         // more than 128 registers
@@ -113,7 +114,7 @@ std::string spec_source(const pj_mech &m, const LaunchCfg &cj, const LaunchCfg &
              "    q.groups = " + std::to_string(c.groups) + ";\n"
              "    q.shared_const = " + std::to_string(sconst) + ";\n"
              "    pj::eval_kernel_body<" + (jac ? "true" : "false") + ", " + std::to_string(c.wps) + ", " +
-             (cv ? "true" : "false") + ">(q);\n}\n";
+             (cv ? "true" : "false") + ", " + (conc ? "true" : "false") + ">(q);\n}\n";
     }
     return s;
 }
@@ -168,7 +169,8 @@ int specialize(pj_mech *m, std::string *err) {
 
     pj_spec *sp = new pj_spec();
     cudaError_t e = cudaLibraryLoadData(&sp->lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaLibraryGetKernel(&sp->kern[k], sp->lib, kSpecNames[k]);
+    for (int k = 0; k < kSpecKernels && e == cudaSuccess; ++k)
+        e = cudaLibraryGetKernel(&sp->kern[k], sp->lib, kSpecNames[k]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (sp->lib) cudaLibraryUnload(sp->lib);
@@ -198,6 +200,12 @@ const void *spec_kernel(const pj_mech *m, bool jac, bool cv, const LaunchCfg &c)
     const LaunchCfg &sc = jac ? sp->jac_cfg : sp->dydt_cfg;
     if (sc.wps != c.wps || sc.groups != c.groups) return nullptr;
     return reinterpret_cast<const void *>(sp->kern[(jac ? 2 : 0) + (cv ? 1 : 0)]);
+}
+
+const void *spec_conc_kernel(const pj_mech *m, const LaunchCfg &c) {
+    const pj_spec *sp = m->spec;
+    if (!sp || sp->jac_cfg.wps != c.wps || sp->jac_cfg.groups != c.groups) return nullptr;
+    return reinterpret_cast<const void *>(sp->kern[4]);
 }
 
 }  // namespace pj

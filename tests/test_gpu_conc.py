@@ -117,6 +117,21 @@ def test_full_size_batch_sampled():
     assert rep["n_nonfinite"] == 0 and rep["n_bad"] == 0, rep
 
 
+@pytest.mark.parametrize("cfg", [0, 2])
+def test_specialised_kernel_same_bits(cfg):
+    """The kernel compiled for the model (NVRTC) returns the data-driven kernel's bits."""
+    import paper_1605_03262_b300 as pj
+    model = synth.config_model(cfg)
+    blob = synth.to_bytes(model)
+    T, P, V, nmol = _dev(*synth.config_conc_states(cfg, 300))
+    base, fb = pj.Model(blob).eval_jacobian_conc(T, P, V, nmol, dydt=True)
+    g = pj.Model(blob)
+    assert g.specialize()["jacobian"]
+    vals, f = g.eval_jacobian_conc(T, P, V, nmol, dydt=True)
+    torch.cuda.synchronize()
+    assert torch.equal(vals, base) and torch.equal(f, fb)
+
+
 def test_argument_errors():
     import paper_1605_03262_b300 as pj
     model = synth.config_model(0)

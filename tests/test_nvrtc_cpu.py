@@ -59,6 +59,7 @@ def test_device_code_compiles_standalone_with_model_constants():
            '    q.m.N = 13; q.m.R = 27; q.m.rpc = 4; q.groups = 8;\n'
            '    pj::eval_kernel_body<true, 1, false>(q);\n'
            '    pj::eval_kernel_body<false, 2, true>(q);\n'
+           '    pj::eval_kernel_body<true, 2, false, true>(q);\n'
            '}\n')
     rc, log, size = _compile(src, _headers())
     assert rc == NVRTC_SUCCESS, log[:3000]
