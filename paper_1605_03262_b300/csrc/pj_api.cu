@@ -195,7 +195,7 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
            o_hc = push(blob, im.h_chunk), o_cc = push(blob, im.c_chunk), o_scc = push(blob, im.s_comb_chunk),
            o_scb = push(blob, im.s_comb), o_gpf = push(blob, im.g_pfirst), o_hpf = push(blob, im.h_pfirst),
            o_cpf = push(blob, im.c_pfirst);
-    size_t o_ccp = push(blob, im.cc_ptr), o_ccs = push(blob, im.cc_src), o_ccc = push(blob, im.cc_col),
+    size_t o_ccp = push(blob, im.cc_ptr), o_ccw = push(blob, im.cc_wr), o_ccc = push(blob, im.cc_col),
            o_dnu = push(blob, im.rx_dnu);
     pj::MathTables tables;
     pj::build_math_tables(tables);
@@ -279,9 +279,9 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.s_comb_chunk = reinterpret_cast<const int2 *>(b + o_scc);
     d.s_comb = reinterpret_cast<const int4 *>(b + o_scb);
     d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
-    d.cc_nnz = int(im.cc_src.size());
+    d.cc_nnz = int(im.cc_col.size());
     d.cc_ptr = reinterpret_cast<const int *>(b + o_ccp);
-    d.cc_src = reinterpret_cast<const int *>(b + o_ccs);
+    d.cc_wr = reinterpret_cast<const double *>(b + o_ccw);
     d.cc_col = reinterpret_cast<const int *>(b + o_ccc);
     d.rx_dnu = reinterpret_cast<const double *>(b + o_dnu);
     m->dev_model = reinterpret_cast<const pj::DevModel *>(b + o_dm);

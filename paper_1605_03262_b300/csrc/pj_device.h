@@ -98,11 +98,10 @@ struct DevModel {
     const int4 *s_comb;       // split row entry: staged position, first partial slot, partials, 0
     const MathTables *tables;  // exp/log tables (pj_fastmath.cuh)
     // molar-concentration basis: per species row k < N-1, its pattern entries cc_ptr[k]..cc_ptr[k+1]
-    // (columns n_j in ascending j); cc_src = the sparse-block entry of (k, j), or -1 where the row
-    // is dense only through species N. rx_dnu: sum_k nu_ki per reaction.
+    // (columns n_j, ascending j, in cc_col; cc_wr = W_j / W_k). rx_dnu: sum_k nu_ki per reaction.
     int cc_nnz;
-    const int *cc_ptr, *cc_src, *cc_col;
-    const double *rx_dnu;
+    const int *cc_ptr, *cc_col;
+    const double *cc_wr, *rx_dnu;
 };
 
 // Doubles of one warp's row stage: rpc staged rows and the partial slots of split entries.

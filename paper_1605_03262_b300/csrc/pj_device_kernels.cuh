@@ -753,26 +753,43 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
 //   d(dn_k/dt)/dn_j = D_kj - D_kN,
 //   d(dn_k/dt)/dV   = omega_k + G_k / W + [M] D_kN   (G_k = sum_i nu_ki a_i, a_i = -W (c sigma + psi R E)),
 //   d(dn_k/dt)/dT   = V (Theta_k - (d(dn_k/dt)/dV) / T)   (Theta_k = sum_i nu_ki theta_i),
-// and the T and V rows from the column sums sum_k H_k D_kj (HS_j) and sum_k D_kj (NS_j). Rows are
-// sparse: species k's row holds T, V and the columns n_j of its pattern (the species of k's
-// reactions, or all of them when species N takes part in one), in the static order of cc_ptr /
-// cc_src; the T and V rows are dense. Output per state: the CSR values, rows in state order.
+// and the T and V rows from the column sums sum_k H_k D_kj (HS_j) and sum_k D_kj (NS_j). The output
+// is CSR values per state, rows in state order: the dense T and V rows, then species row k with its
+// T and V entries and the columns n_j of its pattern (cc_ptr / cc_col). This function writes the T
+// and V rows and the source terms, and leaves each species row's constants for the row stage in the
+// gather arrays: J_k0 <- its T entry, A_k <- its V entry, C_k <- W_N C_k, so that the row stage's
+// fill C_k W_N / W_j plus the sparse schedule's (W_k / W_j) nu_ki b'_ij stage (W_k / W_j) (D_kj - D_kN).
 template <int WPS>
-__device__ __noinline__ void conc_finish(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
-                                         const StateIO &io, long long st, const Grp &g, const StateScalars &s,
-                                         double cp, double J00, double HA, double Hf) {
+__device__ __forceinline__ void conc_tv(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
+                                     const StateIO &io, long long st, const Grp &g, const StateScalars &s,
+                                     double cp, double J00, double HA, double Hf) {
     const int N = m.N;
     const int G = WPS ? WPS * 32 : g.G, NW = WPS ? WPS : g.wps;
     const int t = g.t, lane = g.lane, wg = g.wg;
     const double *sInvW = smem_const + 128 + N;
-    const double *scp = S + sc.cpk, *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sf = S + sc.f, *sHS = S + sc.HS;
-    const double *sb = S + sc.b;
-    double *sNS = S + sc.rows;                          // free once the gathers are combined
-    // NS_j = sum_k D_kj = sum_i dnu_i b'_ij over the column lists
+    const double *scp = S + sc.cpk, *sf = S + sc.f, *sHS = S + sc.HS, *sb = S + sc.b;
+    double *sJk0 = S + sc.Jk0, *sA = S + sc.A, *sCk = S + sc.Ck;
+    // NS_j = sum_k D_kj = sum_i dnu_i b'_ij: the column-sum schedule of HS_j with dnu_i in place of
+    // dH_i; pieces' partials where the gather partials were, then each column's pieces in order.
+    // The partial and NS arrays lie in the row-staging area, free until the row stage.
+    double *sNS = S + sc.part, *npart = S + sc.part + 3 * m.ngp;   // ngp >= N: no overlap
+    {
+        double acc = 0.0;
+        walk<HB, false, false>(m.h_chunk, m.nh, wg, NW, m.h_rec, lane, no_op,
+             [&](const uint4 &r) { return make_double2(__ldg(m.rx_dnu + r.z), sb[r.x & 0xffffff]); },
+             [&](const uint4 &r, const double2 &o) {
+                 acc = fma(o.x, o.y, acc);
+                 if (r.x >> 31) {
+                     npart[r.y] = acc;
+                     acc = 0.0;
+                 }
+             },
+             no_op);
+    }
+    group_sync<WPS>(g);
     for (int j = t; j < N; j += G) {
         double v = 0.0;
-        for (int e = __ldg(m.col_ptr + j); e < __ldg(m.col_ptr + j + 1); ++e)
-            v = fma(__ldg(m.rx_dnu + __ldg(m.col_rxn + e)), sb[__ldg(m.col_slot + e)], v);
+        for (int q = __ldg(m.h_pfirst + j); q < __ldg(m.h_pfirst + j + 1); ++q) v += npart[q];
         sNS[j] = v;
     }
     // SA = sum_k A_k / W_k, SF = sum_k f_k / W_k, SJ = sum_k J_k0 / W_k (every warp, same order)
@@ -797,8 +814,7 @@ __device__ __noinline__ void conc_finish(const DevModel &m, const Scratch &sc, d
     const double eT = -invcp / (V * rho);
     double *out = io.jac + st * io.ldj;
     const int ld = N + 1;
-    // T and V rows (dense, N + 1 columns each)
-    for (int x = t; x < 2 * ld; x += G) {
+    for (int x = t; x < 2 * ld; x += G) {               // T and V rows (dense)
         const int row = x >= ld, col = x - row * ld;
         double v;
         if (col < 2) {
@@ -811,29 +827,6 @@ __device__ __noinline__ void conc_finish(const DevModel &m, const Scratch &sc, d
         }
         __stcs(out + x, v);
     }
-    // species rows: warp wg takes rows wg, wg + NW, ...
-    for (int k = wg; k < N - 1; k += NW) {
-        const int e0 = __ldg(m.cc_ptr + k), len = __ldg(m.cc_ptr + k + 1) - e0;
-        double *o = out + 2 * ld + 2 * k + e0;
-        double DkN = 0.0;                               // d omega_k / d[X_N]
-        const int eN = __ldg(m.colN_nnz + k);
-        if (eN >= 0)
-            for (int c = __ldg(m.nnz_cptr + eN); c < __ldg(m.nnz_cptr + eN + 1); ++c)
-                DkN = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], DkN);
-        if (lane < 2) {
-            const double iWk = sInvW[k];
-            const double JV = M * fma(iWk, sA[k], DkN);
-            __stcs(o + lane, lane ? JV : V * fma(rho * iWk, sJk0[k], -JV * invT));
-        }
-        for (int e = lane; e < len; e += 32) {
-            const int src = __ldg(m.cc_src + e0 + e);
-            double v = 0.0;
-            if (src >= 0)
-                for (int c = __ldg(m.nnz_cptr + src); c < __ldg(m.nnz_cptr + src + 1); ++c)
-                    v = fma(__ldg(m.con_nu + c), sb[__ldg(m.con_slot + c)], v);
-            __stcs(o + 2 + e, v - DkN);
-        }
-    }
     if (io.dydt) {
         double *f = io.dydt + st * io.ldd;
         for (int k = t; k <= N; k += G) {
@@ -843,6 +836,15 @@ __device__ __noinline__ void conc_finish(const DevModel &m, const Scratch &sc, d
             else v = V * rho * sInvW[k - 2] * sf[k - 2];
             f[k] = v;
         }
+    }
+    group_sync<WPS>(g);                                 // the sums above have read A_k and J_k0
+    for (int k = t; k < N; k += G) {                    // species rows' constants for the row stage
+        const double iWk = sInvW[k], ck = sCk[k];
+        const double DkN = -WN * iWk * ck;              // d omega_k / d[X_N]
+        const double JV = M * fma(iWk, sA[k], DkN);
+        sJk0[k] = V * fma(rho * iWk, sJk0[k], -JV * invT);
+        sA[k] = JV;
+        sCk[k] = WN * ck;
     }
     group_sync<WPS>(g);
 }
@@ -1066,10 +1068,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         const double HSN = sHS[N - 1], cpN = scp[N - 1];
         const double e0 = Hf * invcp * invcp;
 
-        if constexpr (CONC) {
-            conc_finish<WPS>(m, sc, S, smem_const, io, st, g, s, cp, J00, HA, Hf);
-            return;
-        }
+        if constexpr (CONC) conc_tv<WPS>(m, sc, S, smem_const, io, st, g, s, cp, J00, HA, Hf);
         // ---- row stage: chunks of rpc rows staged per warp; dense FMA over the flattened
         //      chunk, then the chunk's lane-balanced sparse schedule, then 16-byte stores ----
         const int ld = N + 1, RPC = m.rpc;
@@ -1088,12 +1087,16 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
                  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                  __syncwarp();                          // the previous chunk's bulk copy has read the stage
-                 stage = stage0 + ((reinterpret_cast<uintptr_t>(Jout + (long long)r0 * ld) & 15) ? 1 : 0);
+                 stage = stage0 + ((!CONC && (reinterpret_cast<uintptr_t>(Jout + (long long)r0 * ld) & 15)) ? 1 : 0);
                  comb = __ldg(m.s_comb_chunk + c);     // split entries of this chunk
                  if (RPC == 1 && r0 > 0) {              // one species row: its constants once
                      const int k = r0 - 1;
                      const double a = sA[k], ck = sCk[k], jk0 = sJk0[k];
                      auto value1 = [&](int j) {
+                         if constexpr (CONC) {        // T and V entries; C_k W_N / W_j elsewhere
+                             const double w = (j == 0 || j == N) ? 0.0 : sInvW[j - 1];
+                             return (j == 0) ? jk0 : (j == N) ? a : ck * w;
+                         }
                          const double d = (j == 0 || j == N) ? 0.0 : sDelta[j - 1];
                          return (j == 0) ? jk0 : (j == N) ? 0.0 : fma(a, d, ck);
                      };
@@ -1114,8 +1117,8 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                  if (r0 == 0) {                         // energy row: its own loop, so that the
                      for (int j = lane; j < ld; j += 32) {   // species rows carry no FP64 work of it
                          double v;
-                         if (j == 0) v = J00;
-                         else if (j == N) v = 0.0;
+                         if (CONC || j == N) v = 0.0;  // (the concentration basis writes its T row itself)
+                         else if (j == 0) v = J00;
                          else v = fma(-invcp, fma(HA, sDelta[j - 1], sHS[j - 1] - HSN), (scp[j - 1] - cpN) * e0);
                          stage[j] = v;
                      }
@@ -1128,6 +1131,10 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                  }
                  auto value = [&](int rr_, int j_) {    // species row r0 + rr_ >= 1
                      const int k = r0 + rr_ - 1;
+                     if constexpr (CONC) {
+                         const double w = (j_ == 0 || j_ == N) ? 0.0 : sInvW[j_ - 1];
+                         return (j_ == 0) ? sJk0[k] : (j_ == N) ? sA[k] : sCk[k] * w;
+                     }
                      const double d = (j_ == 0 || j_ == N) ? 0.0 : sDelta[j_ - 1];
                      return (j_ == 0) ? sJk0[k] : (j_ == N) ? 0.0 : fma(sA[k], d, sCk[k]);
                  };
@@ -1184,6 +1191,34 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                  // async proxy; the odd first and last elements are plain stores
                  // (one-row chunks keep the warp's own 16-byte stores: their copy would have to be read
                  // before the next row's dense fill, measured slower)
+                 if constexpr (CONC) {                  // compact the staged rows into CSR rows
+                     __syncwarp();
+                     for (int rr = 0; rr < RPC && r0 + rr <= N; ++rr) {
+                         const int r = r0 + rr;
+                         if (r == 0 || r == N) continue;
+                         const int k = r - 1, e0 = __ldg(m.cc_ptr + k), len = __ldg(m.cc_ptr + k + 1) - e0;
+                         const double *srow = stage + rr * ld;
+                         double *o = Jout + 2 * ld + 2 * k + e0;
+                         if (lane < 2) __stcs(o + lane, srow[lane ? N : 0]);
+                         for (int e = lane; e < len; e += 32 * kDense) {   // loads first, then stores
+                             int col[kDense];
+                             double w[kDense], v[kDense];
+#pragma unroll
+                             for (int u = 0; u < kDense; ++u) {
+                                 const bool in = e + 32 * u < len;
+                                 col[u] = in ? __ldg(m.cc_col + e0 + e + 32 * u) : 0;
+                                 w[u] = in ? __ldg(m.cc_wr + e0 + e + 32 * u) : 0.0;
+                             }
+#pragma unroll
+                             for (int u = 0; u < kDense; ++u) v[u] = srow[1 + col[u]];
+#pragma unroll
+                             for (int u = 0; u < kDense; ++u)
+                                 if (e + 32 * u < len) __stcs(o + 2 + e + 32 * u, v[u] * w[u]);
+                         }
+                     }
+                     __syncwarp();
+                     return;
+                 }
                  if (RPC == 1) {
                      __syncwarp();
                      store_segment(Jout + (long long)r0 * ld, stage, nel, lane);
@@ -1207,7 +1242,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
              });
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         __syncwarp();                                   // the stage may be reused (gather partials)
-        if (io.dydt) {
+        if (!CONC && io.dydt) {
             double *out = io.dydt + st * io.ldd;
             for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -Hf * invcp : sf[k - 1];
         }

@@ -42,9 +42,9 @@ struct HostImage {
     std::vector<int> g_chunk, h_chunk, c_chunk, s_chunk;   // (record offset, rows) per chunk
     int s_npart = 0;
     std::vector<int> s_comb_chunk, s_comb;                 // (offset, count) per chunk; 4 ints per entry
-    // molar-concentration basis: species-row pattern (DevModel::cc_ptr / cc_src / cc_col), sum_k nu_ki
-    std::vector<int> cc_ptr, cc_src, cc_col;
-    std::vector<double> rx_dnu;
+    // molar-concentration basis: species-row pattern (DevModel::cc_ptr / cc_col / cc_wr), sum_k nu_ki
+    std::vector<int> cc_ptr, cc_col;
+    std::vector<double> cc_wr, rx_dnu;
 };
 
 

@@ -588,17 +588,17 @@ HostImage build_image(const void *buf, size_t len) {
         im.cc_ptr.assign(N, 0);
         for (int k = 0; k < N - 1; ++k) {
             const bool dense = im.colN_nnz[k] >= 0;
-            std::vector<int> at(N - 1, -1);
+            std::vector<char> at(N - 1, 0);
             for (int e = im.row_ptr[k]; e < im.row_ptr[k + 1]; ++e)
-                if (im.nnz_col[e] < N - 1) at[im.nnz_col[e]] = e;
+                if (im.nnz_col[e] < N - 1) at[im.nnz_col[e]] = 1;
             for (int j = 0; j < N - 1; ++j)
-                if (dense || at[j] >= 0) {
-                    im.cc_src.push_back(at[j]);
+                if (dense || at[j]) {
                     im.cc_col.push_back(j);
+                    im.cc_wr.push_back(m.W[j] / m.W[k]);
                 }
-            im.cc_ptr[k + 1] = int(im.cc_src.size());
+            im.cc_ptr[k + 1] = int(im.cc_col.size());
         }
-        im.rx_dnu.assign(R, 0.0);
+        im.rx_dnu.assign(R + 1, 0.0);                 // + the zero that padded schedule items read
         for (int i = 0; i < R; ++i)
             for (auto &e : net[i]) im.rx_dnu[i] += e.second;
     }
