@@ -375,7 +375,7 @@ def time_device(g, Td, Pd, Yd, J, steps, warmup, flush):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
-def run_config(cfg, steps, warmup, rank, cal, n_states=None):
+def run_config(cfg, steps, warmup, rank, cal, n_states=None, launch=None):
     import torch
     import paper_1605_03262_b300 as pj
     model = synth.config_model(cfg)
@@ -387,7 +387,11 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
     # tune on the workload itself when its output fits a 2 GB probe (a small batch wants another
     # shape than a large one), else on the tuner's synthetic batch
     own = n * (N + 1) ** 2 * 8 <= (2 << 30)
-    tune = autotune.autotune(g, blob, use_cache=False, probe=(Td, Pd, Yd) if own else None)
+    if launch:                                       # a fixed shape (--launch): no tuner launches
+        g.set_launch(*launch)
+        tune = {"n_probe": 0}
+    else:
+        tune = autotune.autotune(g, blob, use_cache=False, probe=(Td, Pd, Yd) if own else None)
     J = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
     # the data-driven kernel, then the kernel specialised for this model and shape (NVRTC), which
@@ -408,7 +412,8 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None):
                      "frac": achieved / cal["fp64_tflops"] if cal["fp64_tflops"] else None},
         "hbm_write_gbs": n * (N + 1) ** 2 * 8 / (ms_mean * 1e-3) / 1e9,
         "launch": {"warps_per_state": launch[0], "states_per_cta": launch[1], "ctas_per_sm": launch[2],
-                   "chosen_by": "autotuner (%d probe states)" % tune.get("n_probe", 0)},
+                   "chosen_by": ("fixed (--launch)" if launch else
+                                 "autotuner (%d probe states)" % tune.get("n_probe", 0))},
         "kernel": ("specialised for the model at run time (NVRTC, pj_mech_specialize)" if spec["ok"] else
                    "data-driven (specialisation failed: %s)" % spec["error"]),
         "specialisation": {"compile_s": spec["compile_seconds"], "cubin_bytes": spec["cubin_bytes"],
@@ -801,7 +806,8 @@ def run_ours(args):
     gpu_index = torch.cuda.current_device()
     _barrier(ws)
     with ClockSampler(gpu_index) as clk:
-        res, ctx = run_config(HEADLINE_CFG, args.steps, args.warmup, rank, cal)
+        res, ctx = run_config(HEADLINE_CFG, args.steps, args.warmup, rank, cal,
+                              launch=tuple(int(x) for x in args.launch.split(",")) if args.launch else None)
     clocks = clk.summary()
     g, model, T, P, Y = ctx[:5]
     torch.cuda.synchronize()
@@ -972,6 +978,8 @@ def main():
     ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS]", help="one small profiling case (for ncu)")
     ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
     ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
+    ap.add_argument("--launch", default=None, metavar="WPS,GROUPS,CTAS",
+                    help="fixed launch shape of the headline model (skips the autotuner, e.g. for ncu runs)")
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile, args.warmup, args.data_driven, args.conc)

@@ -808,10 +808,11 @@ __device__ __forceinline__ void conc_tv(const DevModel &m, const Scratch &sc, do
     const double Z = fma(fT * WN, cpN, fma(WN, HSN, HA));
     const double iWcp = invcp / W;
     const double JTT = fma(Z * invT, iWcp, J00);
-    const double JTV = -Z * iWcp / V;
+    const double invV = 1.0 / V, invM = 1.0 / M;
+    const double JTV = -Z * iWcp * invV;
     const double JVV = fT * invT + V * invT * JTV + (SA + NSN);
     const double JVT = V * (JTT * invT - fT * invT * invT + W * SF * invT + W * SJ - (SA + NSN) * invT);
-    const double eT = -invcp / (V * rho);
+    const double eT = -invcp * invV / rho;
     double *out = io.jac + st * io.ldj;
     const int ld = N + 1;
     for (int x = t; x < 2 * ld; x += G) {               // T and V rows (dense)
@@ -823,7 +824,7 @@ __device__ __forceinline__ void conc_tv(const DevModel &m, const Scratch &sc, do
             const int j = col - 2;
             const double Wj = __ldg(m.W + j);
             const double jt = eT * (fma(Wj, sHS[j], -WN * HSN) + fT * (Wj * scp[j] - WN * cpN));
-            v = row ? fma(V * invT, jt, (sNS[j] - NSN) / M) : jt;
+            v = row ? fma(V * invT, jt, (sNS[j] - NSN) * invM) : jt;
         }
         __stcs(out + x, v);
     }
@@ -1205,8 +1206,8 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                              double w[kDense], v[kDense];
 #pragma unroll
                              for (int u = 0; u < kDense; ++u) {
-                                 const bool in = e + 32 * u < len;
-                                 col[u] = in ? __ldg(m.cc_col + e0 + e + 32 * u) : 0;
+                                 const bool in = e + 32 * u < len;   // a full row: column = position
+                                 col[u] = !in ? 0 : len == N - 1 ? e + 32 * u : __ldg(m.cc_col + e0 + e + 32 * u);
                                  w[u] = in ? __ldg(m.cc_wr + e0 + e + 32 * u) : 0.0;
                              }
 #pragma unroll
