@@ -188,7 +188,8 @@ PJ_API int pj_eval_jacobian_fd(const pj_mech *m, int64_t n, const double *T, con
  * source generated for one mechanism and compiled for it), built at run time with NVRTC. enable != 0
  * compiles the library's evaluation kernels with every size and shared-memory offset of this model
  * and its current launch shapes (pj_set_launch) as compile-time constants, loads them on the current
- * device, and makes pj_eval_dydt / pj_eval_jacobian and the constant-volume calls use them while
+ * device, and makes pj_eval_dydt / pj_eval_jacobian, the constant-volume calls and
+ * pj_eval_jacobian_conc use them while
  * the launch shape stays the one they were compiled for (another shape uses the data-driven kernels;
  * call again to specialise for it). The results are bitwise those of the data-driven kernels.
  * enable == 0 releases them. Takes a few seconds. Errors: PJ_EINVAL, PJ_EUNSUPPORTED (NVRTC not
