@@ -515,6 +515,59 @@ def cv_form(per_config: dict, steps: int, warmup: int):
     return out
 
 
+def conc_e2e(g, model, cfg: int, nnz: int, steps: int):
+    """End to end through the Python API with host buffers, for the sparse concentration basis and
+    the dense constant-pressure Jacobian on the same number of states (as many as keep the dense
+    output within 2 GB): per step the pinned host inputs are copied to the device, the Jacobians
+    evaluated, and the outputs copied back to pinned host memory, all inside the CUDA-event
+    interval. The device-to-host copy (PCIe) bounds both, so the smaller sparse output shows here."""
+    import torch
+    N = model.n_species
+    n = int(min(synth.CONFIGS[cfg]["n_states"], (2 << 30) // (8 * (N + 1) ** 2)))
+    T, P, Y = synth.config_states(cfg, n)
+    Tc, Pc, Vc, nc = synth.config_conc_states(cfg, n)
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    hT, hP, hY, hTc, hPc, hVc, hnc = (pin(a) for a in (T, P, Y, Tc, Pc, Vc, nc))
+    dT, dP, dY, dTc, dPc, dVc, dnc = (torch.empty_like(h, device="cuda") for h in (hT, hP, hY, hTc, hPc, hVc, hnc))
+    dJ = torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")
+    hJ = torch.empty((n, N + 1, N + 1), dtype=torch.float64).pin_memory()
+    dv = torch.empty((n, nnz), dtype=torch.float64, device="cuda")
+    hv = torch.empty((n, nnz), dtype=torch.float64).pin_memory()
+
+    def dense():
+        for d, h in ((dT, hT), (dP, hP), (dY, hY)):
+            d.copy_(h, non_blocking=True)
+        g.eval_jacobian(dT, dP, dY, out=dJ)
+        hJ.copy_(dJ, non_blocking=True)
+
+    def sparse():
+        for d, h in ((dTc, hTc), (dPc, hPc), (dVc, hVc), (dnc, hnc)):
+            d.copy_(h, non_blocking=True)
+        g.eval_jacobian_conc(dTc, dPc, dVc, dnc, out=dv)
+        hv.copy_(dv, non_blocking=True)
+
+    res = {"n_states": n}
+    for key, fn, nbytes in (("dense_constant_pressure", dense, 8 * (N + 1) ** 2),
+                            ("concentration_basis", sparse, 8 * nnz)):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(3, steps)):
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            fn()
+            e_.record()
+            torch.cuda.synchronize()
+            ms.append(s_.elapsed_time(e_))
+        t = float(np.median(ms))
+        res[key] = {"ms": t, "jacobians_per_s": n / (t * 1e-3), "d2h_bytes_per_state": nbytes}
+    res["concentration_over_dense_throughput"] = (res["concentration_basis"]["jacobians_per_s"] /
+                                                  res["dense_constant_pressure"]["jacobians_per_s"])
+    del dJ, hJ, dv, hv
+    torch.cuda.empty_cache()
+    return res
+
+
 def conc_form(per_config: dict, steps: int, warmup: int):
     """The molar-concentration basis at constant pressure (state T, V, n_1..n_{N-1}), written as a
     sparse Jacobian: the same numbers of states as the constant-pressure Jacobian, at its launch
@@ -556,12 +609,13 @@ def conc_form(per_config: dict, steps: int, warmup: int):
             ms.append(s_.elapsed_time(e_))
         c_ms = float(np.median(ms))
         cp_ms = per_config[name]["ms_median"]
+        e2e = conc_e2e(g, model, cfg, nnz, steps)
         out[name] = {"n_states": n, "nnz_per_state": nnz, "density": nnz / (N + 1) ** 2,
                      "species_block_density": (nnz - 2 * (N + 1) - 2 * (N - 1)) / (N - 1) ** 2,
                      "bytes_written_per_state": 8 * nnz, "dense_bytes_per_state": 8 * (N + 1) ** 2,
                      "ms": c_ms, "jacobians_per_s": n / (c_ms * 1e-3),
                      "hbm_write_gbs": n * nnz * 8 / (c_ms * 1e-3) / 1e9,
-                     "constant_pressure_ms": cp_ms, "conc_over_constant_pressure": c_ms / cp_ms}
+                     "constant_pressure_ms": cp_ms, "conc_over_constant_pressure": c_ms / cp_ms, "e2e": e2e}
         del vals
         torch.cuda.empty_cache()
     del flush
