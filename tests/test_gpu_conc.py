@@ -132,6 +132,24 @@ def test_specialised_kernel_same_bits(cfg):
     assert torch.equal(vals, base) and torch.equal(f, fb)
 
 
+def test_values_do_not_depend_on_the_launch_shape():
+    """Every sum runs in a fixed lane order, so the bits are the same at every group width."""
+    import paper_1605_03262_b300 as pj
+    model = synth.config_model(1)
+    blob = synth.to_bytes(model)
+    T, P, V, nmol = _dev(*synth.config_conc_states(1, 200))
+    ref = None
+    for shape in ((1, 4, 1), (2, 7, 1), (4, 3, 1), (8, 1, 1)):
+        g = pj.Model(blob)
+        g.set_launch(*shape)
+        vals, f = g.eval_jacobian_conc(T, P, V, nmol, dydt=True)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = (vals, f)
+        else:
+            assert torch.equal(vals, ref[0]) and torch.equal(f, ref[1]), shape
+
+
 def test_argument_errors():
     import paper_1605_03262_b300 as pj
     model = synth.config_model(0)
