@@ -403,6 +403,7 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None, launch=None):
     dfe = dfma_equivalents(work, cal["ratios"])
     ms_mean = float(np.mean(ms))
     achieved = 2.0 * dfe * n / (ms_mean * 1e-3) / 1e12
+    fixed = bool(launch)
     launch = g.get_launch()
     res = {
         "n_states": n, "n_species": N, "n_reactions": model.n_reactions, "ms_per_step": ms_mean,
@@ -412,7 +413,7 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None, launch=None):
                      "frac": achieved / cal["fp64_tflops"] if cal["fp64_tflops"] else None},
         "hbm_write_gbs": n * (N + 1) ** 2 * 8 / (ms_mean * 1e-3) / 1e9,
         "launch": {"warps_per_state": launch[0], "states_per_cta": launch[1], "ctas_per_sm": launch[2],
-                   "chosen_by": ("fixed (--launch)" if launch else
+                   "chosen_by": ("fixed (--launch)" if fixed else
                                  "autotuner (%d probe states)" % tune.get("n_probe", 0))},
         "kernel": ("specialised for the model at run time (NVRTC, pj_mech_specialize)" if spec["ok"] else
                    "data-driven (specialisation failed: %s)" % spec["error"]),
