@@ -980,7 +980,7 @@ def run_reference(args):
 
 
 def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bool = False):
-    """--profile CFG:N[:WPS,GROUPS] -- a small case for ncu: warm-up launches, then one Jacobian
+    """--profile CFG:N[:WPS,GROUPS[,CTAS]] -- a small case for ncu: warm-up launches, then one Jacobian
     launch of the first N states of configuration CFG (inputs larger than L2 once N is a few
     thousand), at the given launch shape or else the autotuner's, with the kernel specialised for
     the model (the one the benchmark times; --data-driven for the other). The autotuner's own probe
@@ -997,7 +997,7 @@ def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bo
     blob = synth.to_bytes(model)
     g = pj.Model(blob)
     if shape:
-        g.set_launch(shape[0], shape[1], 1)
+        g.set_launch(shape[0], shape[1], shape[2] if len(shape) > 2 else 1)
     else:
         autotune.autotune(g, blob, use_cache=False)
     if not data_driven:
@@ -1030,7 +1030,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference comparison")
-    ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS]", help="one small profiling case (for ncu)")
+    ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS[,CTAS]]", help="one small profiling case (for ncu)")
     ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
     ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
     ap.add_argument("--launch", default=None, metavar="WPS,GROUPS,CTAS",
