@@ -469,6 +469,55 @@ def fd_form(per_config: dict, steps: int, warmup: int):
     return out
 
 
+def dydt_form(per_config: dict, steps: int, warmup: int):
+    """The source terms alone (Eqs. e:ode and e:dTdt, the call an ODE solver makes most often) on
+    the same states: launch shape tuned for this kernel, the kernel specialised for the model,
+    timed like the Jacobian (L2 flushed before each step). Per state it reads T, P and Y and
+    writes the N + 1 rates."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    out = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    for cfg in (0, 1, 2, 3):
+        name = synth.CONFIGS[cfg]["name"]
+        if name not in per_config:
+            continue
+        model = synth.config_model(cfg)
+        n = per_config[name]["n_states"]
+        T, P, Y = synth.config_states(cfg, n)
+        blob = synth.to_bytes(model)
+        g = pj.Model(blob)
+        Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+        N = model.n_species
+        autotune.autotune(g, blob, which="dydt", use_cache=False, probe=(Td, Pd, Yd))
+        spec = specialise(g)
+        F = torch.empty((n, N + 1), dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            flush.zero_()
+            g.eval_dydt(Td, Pd, Yd, out=F)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            g.eval_dydt(Td, Pd, Yd, out=F)
+            e.record()
+            torch.cuda.synchronize()
+            ms.append(s.elapsed_time(e))
+        d_ms = float(np.median(ms))
+        lc = g.get_launch("dydt")
+        out[name] = {"n_states": n, "ms": d_ms, "evaluations_per_s": n / (d_ms * 1e-3),
+                     "bytes_per_state": 8 * (N + 2) + 8 * (N + 1),
+                     "launch": {"warps_per_state": lc[0], "states_per_cta": lc[1], "ctas_per_sm": lc[2]},
+                     "kernel": "specialised (NVRTC)" if spec["ok"] else "data-driven",
+                     "jacobian_ms": per_config[name]["ms_median"],
+                     "dydt_over_jacobian": d_ms / per_config[name]["ms_median"]}
+        del F, g
+        torch.cuda.empty_cache()
+    return out
+
+
 def cv_form(per_config: dict, steps: int, warmup: int):
     """The constant-volume form (Section 3.3) on the same states at their densities, in the same
     launch shape and kernel kind (specialised) as the constant-pressure Jacobian, timed like it (L2
@@ -888,6 +937,8 @@ def run_ours(args):
         if not (args.headline_only or args.no_fd) else None
     cvf = cv_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
                   args.warmup) if not args.headline_only else None
+    dyf = dydt_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
+                    args.warmup) if not args.headline_only else None
     concf = conc_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
                       args.warmup) if not args.headline_only else None
     serving = serving_form() if not (args.headline_only or args.no_serving) else None
@@ -924,6 +975,7 @@ def run_ours(args):
         "batched_form": batched,
         "fd_form": fd,
         "cv_form": cvf,
+        "dydt_form": dyf,
         "conc_form": concf,
         "serving_form": serving,
     }
