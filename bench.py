@@ -1031,13 +1031,14 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bool = False):
+def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bool = False, dydt: bool = False):
     """--profile CFG:N[:WPS,GROUPS[,CTAS]] -- a small case for ncu: warm-up launches, then one Jacobian
     launch of the first N states of configuration CFG (inputs larger than L2 once N is a few
     thousand), at the given launch shape or else the autotuner's, with the kernel specialised for
     the model (the one the benchmark times; --data-driven for the other). The autotuner's own probe
     launches use a separate kernel instance count, so with an explicit shape the only launches
-    are the warm-ups and the profiled one. --conc: the molar-concentration basis kernel instead."""
+    are the warm-ups and the profiled one. --conc: the molar-concentration basis kernel instead;
+    --dydt: the source-term kernel, at its own shape (the given one, else its tuner's)."""
     import torch
     import paper_1605_03262_b300 as pj
     parts = spec.split(":")
@@ -1048,10 +1049,11 @@ def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bo
     T, P, Y = synth.config_states(cfg, n, seed_offset=1000)
     blob = synth.to_bytes(model)
     g = pj.Model(blob)
+    which = "dydt" if dydt else "jacobian"
     if shape:
-        g.set_launch(shape[0], shape[1], shape[2] if len(shape) > 2 else 1)
+        g.set_launch(shape[0], shape[1], shape[2] if len(shape) > 2 else 1, which=which)
     else:
-        autotune.autotune(g, blob, use_cache=False)
+        autotune.autotune(g, blob, which=which, use_cache=False)
     if not data_driven:
         specialise(g)
     if conc:
@@ -1064,6 +1066,13 @@ def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bo
         print("profile case done: concentration basis, cfg %d, %d states, launch %s" % (cfg, n, g.get_launch()))
         return
     Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+    if dydt:
+        F = torch.empty((n, model.n_species + 1), dtype=torch.float64, device="cuda")
+        for _ in range(warmup + 1):
+            g.eval_dydt(Td, Pd, Yd, out=F)
+        torch.cuda.synchronize()
+        print("profile case done: source terms, cfg %d, %d states, launch %s" % (cfg, n, g.get_launch("dydt")))
+        return
     J = torch.empty((n, model.n_species + 1, model.n_species + 1), dtype=torch.float64, device="cuda")
     for _ in range(warmup + 1):
         g.eval_jacobian(Td, Pd, Yd, out=J)
@@ -1085,11 +1094,12 @@ def main():
     ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS[,CTAS]]", help="one small profiling case (for ncu)")
     ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
     ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
+    ap.add_argument("--dydt", action="store_true", help="with --profile: the source-term kernel")
     ap.add_argument("--launch", default=None, metavar="WPS,GROUPS,CTAS",
                     help="fixed launch shape of the headline model (skips the autotuner, e.g. for ncu runs)")
     args = ap.parse_args()
     if args.profile:
-        return run_profile_case(args.profile, args.warmup, args.data_driven, args.conc)
+        return run_profile_case(args.profile, args.warmup, args.data_driven, args.conc, args.dydt)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
