@@ -60,6 +60,11 @@ MUTANTS = [
     ("source_terms.inc", "if (k < N - 1) f[2 + k] = V * wk_;", "if (k < N - 1) f[2 + k] = wk_;"),
     ("pyjac_oracle.c", "else { nz[col - 2] += I * h * Vs; dh = h * Vs; }", "else { nz[col - 2] += I * h * Vs; dh = h; }"),
     ("pyjac_oracle.c", "else if (col == 1) { Vz += I * h * Vs; dh = h * Vs; }", "else if (col == 1) { Vz += I * h; dh = h * Vs; }"),
+    # the Troe and SRI blending values (pinned in the mid-range of log10 P_r)
+    ("source_terms.inc", "SCALAR Bt = 0.806 - 1.1762 * lFc - 0.14 * lPr;", "SCALAR Bt = 0.8 - 1.1762 * lFc - 0.14 * lPr;"),
+    ("source_terms.inc", "SCALAR Bt = 0.806 - 1.1762 * lFc - 0.14 * lPr;", "SCALAR Bt = 0.806 - 1.176 * lFc - 0.14 * lPr;"),
+    ("source_terms.inc", "return pow(Fc, 1.0 / (1.0 + (At / Bt) * (At / Bt)));", "return pow(Fc, 1.0 / (1.0 + (At / Bt)));"),
+    ("source_terms.inc", "SCALAR X = 1.0 / (1.0 + lPr * lPr);", "SCALAR X = 1.0 / (1.0 + lPr);"),
 ]
 
 EPS = 2.0 ** -52
@@ -222,6 +227,28 @@ def _pins(lib) -> list:
         big = np.abs(Jn[0, :, col]) > 1e-3 * np.abs(Jn[0, :, col]).max()
         if not np.all(np.abs(fd - Jn[0, :, col])[big] <= 1e-6 * np.abs(Jn[0, big, col])):
             failed.append("conc jacobian")
+            break
+    # 7. Troe (with and without T**) and SRI blending values at mid-range log10 P_r, by hand
+    from tests.test_oracle_pins import _pressure_for_Pr, _sri_F_by_hand, _troe_F_by_hand
+    Tf, Yf = 1400.0, np.array([0.2, 0.2, 0.2, 0.2, 0.2])
+    k0, kinf = (1.0e3, 0.0, 0.0), (1.0e4, 0.5, 100.0)
+    FIVE = [(1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1)]
+    cases = [(synth.F_TROE, (0.35, 180.0, 2500.0, 0.0, 0.0), 0, lambda Pr: _troe_F_by_hand(Tf, Pr, 0.35, 180.0, 2500.0)),
+             (synth.F_TROE, (0.35, 180.0, 2500.0, 4200.0, 0.0), 1,
+              lambda Pr: _troe_F_by_hand(Tf, Pr, 0.35, 180.0, 2500.0, 4200.0)),
+             (synth.F_SRI, (0.7, 450.0, 1300.0, 1.2, 0.15), 0, lambda Pr: _sri_F_by_hand(Tf, Pr, 0.7, 450.0, 1300.0, 1.2, 0.15))]
+    for ftype, fp, has, Fh in cases:
+        r = synth.Reaction(kind=synth.KIND_FALLOFF, rev_mode=synth.REV_IRREVERSIBLE, reac=[(2, 1)],
+                           prod=[(0, 1), (1, 1)], tb_mode=synth.TB_MIXTURE, k0=k0, kinf=kinf, ftype=ftype,
+                           fparams=fp, troe_has_T2=has)
+        omf = oracle.load_model(synth.to_bytes(mechs.one_reaction_model(r, FIVE)), lib=lib)
+        bad = False
+        for lpr in (-2.0, 0.5, 3.0):
+            Pr = 10.0 ** lpr
+            c = omf.reaction_rates(Tf, _pressure_for_Pr(Tf, Pr, k0, kinf), Yf)["c"][0]
+            bad |= not abs(c - Pr / (1 + Pr) * Fh(Pr)) <= 1e-12 * abs(c)
+        if bad:
+            failed.append("falloff blending")
             break
     return failed
 

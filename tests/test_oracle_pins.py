@@ -172,6 +172,55 @@ def test_troe_blending_equals_fcent_where_A_vanishes():
     assert c == pytest.approx(target_Pr / (1 + target_Pr) * Fc, rel=1e-10)
 
 
+def _troe_F_by_hand(T, Pr, a, T3, T1, T2=None):
+    """Troe blending factor of Section 2.3.3 written out: F_cent from its three (or two) terms,
+    A_Troe and B_Troe from log10 P_r and log10 F_cent, and log10 F = log10 F_cent / (1 + (A/B)^2)."""
+    Fc = (1.0 - a) * math.exp(-T / T3) + a * math.exp(-T / T1)
+    if T2 is not None:
+        Fc += math.exp(-T2 / T)
+    lpr, lfc = math.log10(Pr), math.log10(Fc)
+    A = lpr - 0.67 * lfc - 0.4
+    B = 0.806 - 1.1762 * lfc - 0.14 * lpr
+    return 10.0 ** (lfc / (1.0 + (A / B) ** 2))
+
+
+def _sri_F_by_hand(T, Pr, a, b, c, d, e):
+    """SRI blending factor of Section 2.3.3 written out: X = 1 / (1 + (log10 P_r)^2) and
+    F = d T^e (a exp(-b/T) + exp(-T/c))^X."""
+    X = 1.0 / (1.0 + math.log10(Pr) ** 2)
+    return d * T ** e * (a * math.exp(-b / T) + math.exp(-T / c)) ** X
+
+
+def _pressure_for_Pr(T, Pr, k0, kinf):
+    """Pressure at which P_r = (k_0 / k_inf) [M] takes the value Pr, [M] = P / (R T) (unit efficiencies)."""
+    k0v = k0[0] * T ** k0[1] * math.exp(-k0[2] / T)
+    kiv = kinf[0] * T ** kinf[1] * math.exp(-kinf[2] / T)
+    return Pr * kiv / k0v * R_GAS * T
+
+
+@pytest.mark.parametrize("lpr", [-2.0, 0.5, 3.0])
+@pytest.mark.parametrize("form", ["troe", "troe_T2", "sri"])
+def test_troe_and_sri_blending_values_in_mid_range(form, lpr):
+    """The pressure modifier c = P_r / (1 + P_r) F of a falloff reaction at log10 P_r of -2, 0.5 and 3,
+    against F computed by hand from Section 2.3.3 (the exponent (A/B)^2 and the constants 0.67, 0.4,
+    0.806, 1.1762, 0.14 of Troe; the squared log10 P_r in the SRI exponent X)."""
+    T, _, Y = _state(5)
+    k0, kinf = (1.0e3, 0.0, 0.0), (1.0e4, 0.5, 100.0)
+    Pr = 10.0 ** lpr
+    if form == "sri":
+        fp = (0.7, 450.0, 1300.0, 1.2, 0.15)
+        F = _sri_F_by_hand(T, Pr, *fp)
+        r = _falloff(KIND_FALLOFF, F_SRI, fp, k0=k0, kinf=kinf)
+    else:
+        a, T3, T1, T2 = 0.35, 180.0, 2500.0, 4200.0
+        has = form == "troe_T2"
+        F = _troe_F_by_hand(T, Pr, a, T3, T1, T2 if has else None)
+        r = _falloff(KIND_FALLOFF, F_TROE, (a, T3, T1, T2 if has else 0.0, 0.0), has_T2=int(has), k0=k0, kinf=kinf)
+    c = _om(mechs.one_reaction_model(r, TWO)).reaction_rates(T, _pressure_for_Pr(T, Pr, k0, kinf), Y)["c"][0]
+    assert c == pytest.approx(Pr / (1.0 + Pr) * F, rel=1e-12)
+    assert abs(F - 1.0) > 1e-3                       # a point where the blending matters
+
+
 def test_falloff_pressure_limits():
     T, _, Y = _state(5)
     k0, kinf = (1.0e3, 0.2, 500.0), (1.0e4, 0.5, 100.0)
