@@ -268,31 +268,35 @@ PJ_API void pj_batch_free(pj_batch *b);
  * that owns a fixed device memory pool and forbids cudaMalloc/cudaFree inside its time step
  * (those calls can synchronise the device and fragment the pool), or code that must not meet an
  * allocation failure in the middle of a run. pj_batch_run_noalloc evaluates the same items as
- * pj_batch_create + pj_batch_run would (same arithmetic, same results), but keeps the launch's
- * working data -- the item table, the tile bounds and the tile counter -- in one fixed static
- * device array of the library (about 16 KB, held by every GPU that loads the library until the
- * process exits) instead of device memory it would allocate. It calls no cudaMalloc, cudaFree or
- * other allocating routine; the caller still provides every input and output buffer.
+ * pj_batch_create + pj_batch_run would (same arithmetic, bitwise the same results), without
+ * device memory of its own: the item table and the tile bounds travel to the kernel by value, in
+ * its parameter block, and the one piece of device scratch -- the tile counter from which the
+ * CTAs take tiles -- lies in a fixed static device array of the library (256 bytes, held by every
+ * GPU that loads the library until the process exits). It calls no cudaMalloc, cudaFree or other
+ * allocating routine; the caller still provides every input and output buffer.
  *
  * Limits and rules:
- *   - at most 64 items per call; more are rejected with PJ_EINVAL and a message naming the limit;
+ *   - at most 64 items per call (the size of the parameter block); more are rejected with
+ *     PJ_EINVAL and a message naming the limit; items with n = 0 are allowed anywhere in the list;
  *   - which: 0 = Jacobian (jac required, dydt optional), 1 = source terms (dydt required);
  *     tile_states: states per tile, 0 = four times the states a CTA evaluates concurrently;
- *   - every call uses the same array, which keeps the last call's contents; each call re-writes
- *     the table and zeroes the tile counter (copied from the host on the given stream) before its
- *     kernel starts. Calls that overlap on the GPU race on the array: order them on one stream, or
- *     wait for one to finish before issuing the next;
+ *   - every call uses the same counter, which keeps the last call's value; each call zeroes it
+ *     with an asynchronous memset on the given stream before its kernel starts. Calls that
+ *     overlap on the GPU race on it: order them on one stream, or wait for one to finish before
+ *     issuing the next;
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress); make
  *     that first call before any stream capture;
- *   - asynchronous on the stream; argument errors as pj_batch_create.
+ *   - asynchronous on the stream: the call does not wait for earlier work on the stream, and
+ *     reads nothing of the host's item array after it returns; argument errors as
+ *     pj_batch_create.
  */
 PJ_API int pj_batch_run_noalloc(const pj_batch_item *items, int n_items, int which, int tile_states, void *stream);
 
 /*
- * The same launch with the item table, tile bounds and counter in a device workspace of the
- * caller (at least pj_batch_workspace_bytes() bytes, 16-byte aligned, on the current device)
- * instead of the library's static array: calls on different workspaces may overlap on the GPU (one
- * workspace per stream, e.g. a server's pool). At most 64 items; same argument rules and errors as
+ * The same launch with the tile counter in a device workspace of the caller (at least
+ * pj_batch_workspace_bytes() bytes, 16-byte aligned, on the current device) instead of the
+ * library's static array: calls on different workspaces may overlap on the GPU (one workspace per
+ * stream, e.g. a server's pool). At most 64 items; same argument rules and errors as
  * pj_batch_run_noalloc, plus PJ_EINVAL for a missing, small, misaligned or non-device workspace.
  * Calls that share a workspace must be ordered on one stream.
  */

@@ -377,9 +377,10 @@ def batch_workspace_bytes() -> int:
 
 def run_batch(items, which: str = "jacobian", workspace=None, tile_states: int = 0, stream=None) -> None:
     """One persistent launch over up to 64 (Model, T, P, Y, out[, dydt_out]) items without a plan:
-    the item table goes to ``workspace`` (a CUDA uint8 tensor of at least batch_workspace_bytes();
-    calls sharing one must be ordered on a stream) or, without one, to the library's static array
-    (pj_batch_run_noalloc; calls must not overlap on the GPU)."""
+    the item table travels in the kernel's parameter block; the tile counter goes to ``workspace``
+    (a CUDA uint8 tensor of at least batch_workspace_bytes(); calls sharing one must be ordered on a
+    stream) or, without one, to the library's static array (pj_batch_run_noalloc; calls must not
+    overlap on the GPU)."""
     w = 0 if which == "jacobian" else 1
     arr, keep = _batch_items(items, w)
     if workspace is None:

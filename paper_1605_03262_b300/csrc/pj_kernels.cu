@@ -150,49 +150,54 @@ cudaError_t launch_batch(const BatchParams &p, bool jac, int blocks, int threads
 // Some callers cannot allocate device memory in their call path: a solver or CFD code that owns a
 // fixed memory pool and forbids cudaMalloc/cudaFree inside its time step (both can synchronise the
 // device and fragment the pool), or code that must not meet an allocation failure mid-run. For
-// them the batched launch keeps its working data -- the item table, the tile bounds of every item
-// and the tile counter -- in the fixed static device array below instead of a cudaMalloc'd plan.
-// The caller still passes the state inputs and the outputs.
+// them the batched launch passes its item table and tile bounds to the kernel by value (a kernel
+// parameter block, at most 64 items) and keeps its one piece of device scratch, the tile counter
+// that the CTAs draw tiles from, in the fixed static device array below instead of a cudaMalloc'd
+// plan. The caller still passes the state inputs and the outputs.
 
 namespace pj {
 
-constexpr int kNoAllocMaxItems = 64;   // largest number of items one call accepts
+constexpr int kNoAllocMaxItems = 64;   // largest number of items one call accepts (parameter space)
 
-struct NoAllocScratch {
-    int counter;                       // tile counter, zeroed at the start of every call
-    int n_items;
-    int pad[62];
-    int tile_first[kNoAllocMaxItems + 1];   // first tile of each item; tile_first[n_items] = tiles
+// The launch's table, copied into the kernel's parameter space at launch (about 13 KB of the 32 KB
+// that a kernel's parameters may take): nothing of it lives in device memory.
+struct NoAllocTable {
+    int ntiles, n_items;
+    int *counter;                      // tile counter in device memory, zeroed before every launch
+    int tile_first[kNoAllocMaxItems + 1];   // first tile of each item; tile_first[n_items] = ntiles
     long long tile_states[kNoAllocMaxItems];
     long long n_states[kNoAllocMaxItems];
     BatchItem items[kNoAllocMaxItems];
 };
+static_assert(sizeof(NoAllocTable) < 32000, "kernel parameter block");
 
-// The array (about 16 KB): held by every device that loads the library, until the process exits.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+// Device scratch of one launch: the tile counter, padded to one 256-byte line.
+constexpr int kNoAllocScratchInts = 64;
+// The array (256 bytes): held by every device that loads the library, until the process exits.
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocScratchInts];
 
 template <bool JAC>
-__global__ void __launch_bounds__(512, 1) pj_batch_noalloc_kernel(NoAllocScratch *scr, int ntiles) {
+__global__ void __launch_bounds__(512, 1) pj_batch_noalloc_kernel(const __grid_constant__ NoAllocTable p) {
     extern __shared__ __align__(16) double smem[];
     __shared__ DevModel s_m;
     __shared__ int s_tile, s_item;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
-            const int tile = atomicAdd(&scr->counter, 1);
+            const int tile = atomicAdd(p.counter, 1);
             int it = 0;
-            if (tile < ntiles)
-                while (it + 1 < scr->n_items && tile >= scr->tile_first[it + 1]) ++it;
+            if (tile < p.ntiles)
+                while (it + 1 < p.n_items && tile >= p.tile_first[it + 1]) ++it;   // skips items without tiles
             s_tile = tile;
             s_item = it;
         }
         __syncthreads();
         const int tile = s_tile, item = s_item;
-        if (tile >= ntiles) break;
-        const BatchItem &it = scr->items[item];
-        const long long ts = scr->tile_states[item];
-        const long long begin = (long long)(tile - scr->tile_first[item]) * ts;
-        const long long end = min(begin + ts, scr->n_states[item]);
+        if (tile >= p.ntiles) break;
+        const BatchItem &it = p.items[item];
+        const long long ts = p.tile_states[item];
+        const long long begin = (long long)(tile - p.tile_first[item]) * ts;
+        const long long end = min(begin + ts, p.n_states[item]);
         Grp g;
         g.wps = it.wps;
         g.G = it.wps * 32;
@@ -231,11 +236,12 @@ int noalloc_fail(int code, const std::string &msg) { return pj::set_error(code, 
 
 namespace {
 
-// Builds the item table of a batched launch on the host, copies it with the zeroed tile counter
-// into the device scratch `scratch` (the static array or a caller's workspace) on the stream, and
-// launches the persistent batched kernel over it.
+// Builds the item table of a batched launch on the host, zeroes the tile counter at `counter` (in
+// the static array or a caller's workspace) with an asynchronous memset on the stream, and
+// launches the persistent batched kernel with the table as its parameter block. Nothing waits on
+// the host for earlier work on the stream, and no host memory is read after the call returns.
 int batch_run_table(const char *fn, const pj_batch_item *items, int n_items, int which, int tile_states, int dev,
-                    void *scratch, cudaStream_t st) {
+                    int *counter, cudaStream_t st) {
     using namespace pj;
     const std::string f(fn);
     cudaError_t e;
@@ -250,10 +256,10 @@ int batch_run_table(const char *fn, const pj_batch_item *items, int n_items, int
     const size_t budget = size_t(optin) > fa.sharedSizeBytes ? size_t(optin) - fa.sharedSizeBytes : 0;
     const int threads = 512;
 
-    // the item table, built on the host stack and copied into the scratch
-    NoAllocScratch h;
+    NoAllocTable h;
     std::memset(&h, 0, sizeof(h));
     h.n_items = n_items;
+    h.counter = counter;
     size_t smem = 0;
     int ntiles = 0;
     for (int i = 0; i < n_items; ++i) {
@@ -288,19 +294,18 @@ int batch_run_table(const char *fn, const pj_batch_item *items, int n_items, int
         ntiles += int(nt);
     }
     h.tile_first[n_items] = ntiles;
-    h.counter = 0;                     // what must start at zero: the tile counter
-    // the copy brings the zeroed counter and this call's table; a call still running on the GPU
-    // with the same array would race with it
-    e = cudaMemcpyAsync(scratch, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
+    h.ntiles = ntiles;
     if (ntiles == 0) return PJ_OK;
+    // what must start at zero: the tile counter. A call still running on the GPU with the same
+    // counter would race with this one.
+    e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("counter reset: ") + cudaGetErrorString(e));
     e = jac ? cudaFuncSetAttribute(pj_batch_noalloc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))
             : cudaFuncSetAttribute(pj_batch_noalloc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel attribute: ") + cudaGetErrorString(e));
     const int blocks = std::max(1, std::min(sms, ntiles));
-    NoAllocScratch *scr = static_cast<NoAllocScratch *>(scratch);
-    if (jac) pj_batch_noalloc_kernel<true><<<blocks, threads, smem, st>>>(scr, ntiles);
-    else pj_batch_noalloc_kernel<false><<<blocks, threads, smem, st>>>(scr, ntiles);
+    if (jac) pj_batch_noalloc_kernel<true><<<blocks, threads, smem, st>>>(h);
+    else pj_batch_noalloc_kernel<false><<<blocks, threads, smem, st>>>(h);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(PJ_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return PJ_OK;
@@ -315,7 +320,7 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const
         return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: bad argument");
     if (n_items > kNoAllocMaxItems)
         return noalloc_fail(PJ_EINVAL, "pj_batch_run_noalloc: " + std::to_string(n_items) +
-                                           " items, more than the static scratch holds (" +
+                                           " items, more than one call's parameter table holds (" +
                                            std::to_string(kNoAllocMaxItems) + ")");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -335,12 +340,12 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_noalloc(const
         }
         scratch = g_noalloc_ptr[dev];
     }
-    return batch_run_table("pj_batch_run_noalloc", items, n_items, which, tile_states, dev, scratch,
+    return batch_run_table("pj_batch_run_noalloc", items, n_items, which, tile_states, dev, static_cast<int *>(scratch),
                            static_cast<cudaStream_t>(stream));
 }
 
 extern "C" __attribute__((visibility("default"))) size_t pj_batch_workspace_bytes(void) {
-    return sizeof(pj::NoAllocScratch);
+    return sizeof(int) * pj::kNoAllocScratchInts;
 }
 
 extern "C" __attribute__((visibility("default"))) int pj_batch_run_ws(const pj_batch_item *items, int n_items,
@@ -352,7 +357,7 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_ws(const pj_b
     if (n_items > kNoAllocMaxItems)
         return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: " + std::to_string(n_items) + " items, more than a workspace holds (" +
                                            std::to_string(kNoAllocMaxItems) + ")");
-    if (!workspace || workspace_bytes < sizeof(NoAllocScratch) || (reinterpret_cast<uintptr_t>(workspace) & 15))
+    if (!workspace || workspace_bytes < sizeof(int) * kNoAllocScratchInts || (reinterpret_cast<uintptr_t>(workspace) & 15))
         return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: workspace null, smaller than pj_batch_workspace_bytes() or "
                                        "not 16-byte aligned");
     int dev = 0;
@@ -364,6 +369,6 @@ extern "C" __attribute__((visibility("default"))) int pj_batch_run_ws(const pj_b
         cudaGetLastError();
         return noalloc_fail(PJ_EINVAL, "pj_batch_run_ws: workspace is not device memory of the current device");
     }
-    return batch_run_table("pj_batch_run_ws", items, n_items, which, tile_states, dev, workspace,
+    return batch_run_table("pj_batch_run_ws", items, n_items, which, tile_states, dev, static_cast<int *>(workspace),
                            static_cast<cudaStream_t>(stream));
 }
