@@ -421,9 +421,16 @@ def run_config(cfg, steps, warmup, rank, cal, n_states=None, launch=None):
                            "data_driven_ms_median": float(np.median(ms_dd)),
                            "specialised_over_data_driven": float(np.median(ms)) / float(np.median(ms_dd))},
     }
+    # sampled rows of the last timed launch's output, for the parity report of the CPU-baseline leg
+    idx = np.unique(np.linspace(0, n - 1, min(n, PARITY_SAMPLE[cfg])).astype(np.int64))
+    res["_parity_sample"] = (idx, J[torch.as_tensor(idx, device="cuda")].cpu().numpy())
     del J, flush
     return res, (g, model, T, P, Y, Td, Pd, Yd)
 
+
+# states per model whose Jacobians from the timed launch are compared with the oracle (evenly
+# spaced over the batch): about a second of oracle time each on 16 host cores
+PARITY_SAMPLE = {0: 1024, 1: 1024, 2: 512, 3: 256}
 
 FD_WORKSPACE_BYTES = 4 << 30
 
@@ -863,20 +870,64 @@ def e2e_host(g, T, P, Y, steps):
             "d2h_bytes_per_step": int(n * (N + 1) ** 2 * 8), "s_per_step": t}
 
 
-def cpu_baseline(cfg, budget_s=12.0):
-    """The oracle as it stands, on the host cores, on a bounded sample of the same workload."""
+EPS = 2.0 ** -52
+
+
+def parity_report(gpu, ora, scale):
+    """Tolerance report of the GPU Jacobians against the oracle's on the same states.
+
+    Bar per entry: |x_gpu - x_oracle| <= 1e-10 max(|x_oracle|, 1e-20) + 64 eps S, S the oracle's sum
+    of the absolute values of the terms of that entry. strict_fail counts entries that miss the
+    plain 1e-10 relative bar (they pass only through the 64 eps S term, which covers the rounding
+    of a cancelled sum), with the largest condition number kappa = S / |x| among them; well_cond
+    are the entries with kappa <= 4500, where the bar is the plain relative one; bad = entries
+    outside the bar (0 for parity). E_rel is the paper's per-state error norm (Section 5.1, Eq.
+    e:error_norm): the Frobenius norm of elementwise relative errors over entries with
+    |J| >= ||J||_F / 1e20; E_rel_well_cond_max is the largest E_rel over the well-conditioned
+    entries alone (in an entry with kappa near 1/eps both sides hold rounding noise, which E_rel
+    counts at full weight)."""
+    gpu, ora, scale = (np.asarray(x, dtype=np.float64) for x in (gpu, ora, scale))
+    finite = np.isfinite(gpu) & np.isfinite(ora)
+    err = np.abs(gpu - ora)
+    rel_bar = 1e-10 * np.maximum(np.abs(ora), 1e-20)
+    ok = finite & (err <= rel_bar + 64.0 * EPS * scale)
+    strict = finite & (err <= rel_bar)
+    with np.errstate(over="ignore", divide="ignore", invalid="ignore"):
+        kappa = np.where(np.abs(ora) > 0, scale / np.maximum(np.abs(ora), 1e-300), 0.0)
+        rel = np.where(np.abs(ora) > 1e-20, err / np.maximum(np.abs(ora), 1e-20), 0.0)
+    well = (kappa <= 4500.0) & (np.abs(ora) >= 1e-20)
+    sf = ~strict & finite
+    erel, erel_w = [], []
+    for g_, o_, w_ in zip(gpu, ora, well):
+        m = (np.abs(o_) >= np.linalg.norm(o_) / 1e20) & (o_ != 0)
+        erel.append(float(np.linalg.norm((g_[m] - o_[m]) / o_[m])))
+        m &= w_
+        erel_w.append(float(np.linalg.norm((g_[m] - o_[m]) / o_[m])))
+    erel, erel_w = np.array(erel), np.array(erel_w)
+    return {"states": int(gpu.shape[0]), "entries": int(ora.size), "bad": int((~ok).sum()),
+            "nonfinite": int((~finite).sum()), "strict_fail": int(sf.sum()),
+            "strict_fail_max_kappa": float(kappa[sf].max()) if sf.any() else 0.0,
+            "well_cond": int(well.sum()), "well_cond_max_rel": float(rel[well].max()) if well.any() else 0.0,
+            "E_rel_median": float(np.median(erel)), "E_rel_max": float(erel.max()),
+            "E_rel_well_cond_max": float(erel_w.max())}
+
+
+def cpu_baseline(cfg, T, P, Y, sample=None, budget_s=12.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the same workload (the
+    first states of the batch the GPU evaluated), then on one core. With sample = (indices, GPU
+    Jacobians of those states from the timed launch), the oracle's Jacobians of those states (with
+    their rounding scales) give the parity report of that launch."""
     import oracle
     model = synth.config_model(cfg)
     om = oracle.load_model(synth.to_bytes(model))
     cores = oracle.max_threads()
-    T, P, Y = synth.config_states(cfg, 4 * cores)
+    n0 = min(len(T), 4 * cores)
     t0 = time.perf_counter()
-    om.jacobian(T, P, Y)
-    per = (time.perf_counter() - t0) / len(T)
-    ns = int(max(cores, min(synth.CONFIGS[cfg]["n_states"], budget_s / max(per, 1e-9))))
-    T, P, Y = synth.config_states(cfg, ns)
+    om.jacobian(T[:n0], P[:n0], Y[:n0])
+    per = (time.perf_counter() - t0) / n0
+    ns = int(max(min(cores, len(T)), min(len(T), budget_s / max(per, 1e-9))))
     t0 = time.perf_counter()
-    om.jacobian(T, P, Y)
+    om.jacobian(T[:ns], P[:ns], Y[:ns])
     dt = time.perf_counter() - t0
     # the same oracle on one core, on a shorter sample
     oracle.set_threads(1)
@@ -887,12 +938,87 @@ def cpu_baseline(cfg, budget_s=12.0):
         dt1 = time.perf_counter() - t1
     finally:
         oracle.set_threads(cores)
-    return {"value": ns / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d of the %d states of %s, oracle FP64 C with OpenMP over states"
-                      % (ns, synth.CONFIGS[cfg]["n_states"], synth.CONFIGS[cfg]["name"]),
-            "seconds": dt,
-            "one_core": {"value": n1 / dt1, "unit": UNIT, "cores": 1, "sample": "first %d states" % n1,
-                         "seconds": dt1}}
+    out = {"value": ns / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "first %d of the %d states of %s, oracle FP64 C with OpenMP over states"
+                     % (ns, len(T), synth.CONFIGS[cfg]["name"]),
+           "seconds": dt,
+           "one_core": {"value": n1 / dt1, "unit": UNIT, "cores": 1, "sample": "first %d states" % n1,
+                        "seconds": dt1}}
+    if sample is not None:
+        idx, Jg = sample
+        Jo, _, Js, _ = om.jacobian(T[idx], P[idx], Y[idx], with_scale=True)
+        out["parity"] = parity_report(Jg, Jo, Js)
+    return out
+
+
+def _sig(x, d=4):
+    """x rounded to d significant digits (compact JSON)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not math.isfinite(x):
+        return x
+    return float("%.*g" % (d, x))
+
+
+def compact_config(res: dict, cpu: dict) -> dict:
+    """One model's numbers for the JSON line: throughput, roofline fraction, step times, launch shape,
+    the oracle on the host cores and the parity report of the timed launch."""
+    lc = res["launch"]
+    out = {"states": res["n_states"], "jacobians_per_s": _sig(res["jacobians_per_s"]),
+           "frac": _sig(res["roofline"]["frac"], 3), "ms_median": _sig(res["ms_median"]),
+           "ms_min": _sig(res["ms_min"]),
+           "launch": "%dx%dx%d" % (lc["warps_per_state"], lc["states_per_cta"], lc["ctas_per_sm"]),
+           "kernel": "specialised" if res["kernel"].startswith("specialised") else "data-driven"}
+    if cpu:
+        out["oracle_jacobians_per_s"] = _sig(cpu["value"])
+        out["oracle_cores"] = cpu["cores"]
+        if "parity" in cpu:
+            p = cpu["parity"]
+            out["parity"] = {k: (_sig(v, 3) if isinstance(v, float) else v) for k, v in p.items()}
+    return out
+
+
+def compact_forms(batched, serving, dyf, cvf, fd, concf) -> dict:
+    """Headline numbers of the batched, serving, source-term, constant-volume, finite-difference and
+    concentration-basis measurements (the full records go to the detail file)."""
+    out = {}
+    if batched:
+        ms = batched["many_small"]
+        out["batched"] = {
+            "mix_ms": {"plain": _sig(batched["plain_sequential"]["ms"]),
+                       "persistent": _sig(batched["batched_persistent"]["ms"]),
+                       "graph": _sig(batched["batched_graph"]["ms"])},
+            "small64_ms": {"plain": _sig(ms["plain_sequential"]["ms"]), "plain_graph": _sig(ms["plain_graph"]["ms"]),
+                           "persistent": _sig(ms["batched_persistent"]["ms"]),
+                           "graph": _sig(ms["batched_graph"]["ms"])}}
+        for key in ("shape", "small64_shape"):
+            if key in batched:
+                out["batched"][key] = batched[key]
+    if serving:
+        sv = {"capacity_jacobians_per_s": _sig(serving["capacity_closed_loop"]["jacobians_per_s"]),
+              "plain_jacobians_per_s": _sig(serving["plain_per_request_closed_loop"]["jacobians_per_s"])}
+        for k, v in serving["offered"].items():
+            cb, pl = v["continuous_batching"], v["plain_per_request"]
+            sv[k] = {"p50_ms": _sig(cb["p50_ms"], 3), "p99_ms": _sig(cb["p99_ms"], 3),
+                     "plain_p50_ms": _sig(pl["p50_ms"], 3), "plain_p99_ms": _sig(pl["p99_ms"], 3)}
+            if "host_p99_ms" in cb:
+                sv[k]["host_p50_ms"] = _sig(cb["host_p50_ms"], 3)
+                sv[k]["host_p99_ms"] = _sig(cb["host_p99_ms"], 3)
+        out["serving"] = sv
+    if dyf:
+        out["dydt_evals_per_s"] = {k: _sig(v["evaluations_per_s"], 3) for k, v in dyf.items()}
+    if cvf:
+        out["cv_over_cp_time"] = {k: _sig(v["cv_over_constant_pressure"], 3) for k, v in cvf.items()}
+    if fd:
+        out["fd_over_analytic_time"] = {k: _sig(v["fd_over_analytic"], 3) for k, v in fd.items()}
+    if concf:
+        out["conc_over_cp_time"] = {k: _sig(v["conc_over_constant_pressure"], 3) for k, v in concf.items()}
+    return out
+
+
+def detail_path(args):
+    if args.detail:
+        return args.detail
+    d = os.path.join(os.getcwd(), "gpurun_out")
+    return os.path.join(d, "bench_detail.json") if os.path.isdir(d) else None
 
 
 def run_ours(args):
@@ -922,47 +1048,47 @@ def run_ours(args):
     e2e = e2e_host(g, T, P, Y, max(1, min(args.steps, 3))) if not args.no_e2e else None
     if e2e is not None and ws > 1:
         e2e["value"] = _sum_over_ranks(ws, e2e["value"])
-    per_config = {}
+    headline = synth.CONFIGS[HEADLINE_CFG]["name"]
+    per_config, states = {headline: res}, {headline: (T, P, Y)}
+    del ctx, g
     if not args.headline_only:
         for cfg in (0, 2, 3):
-            r, _ = run_config(cfg, max(3, args.steps // 2), args.warmup, rank, cal)
-            per_config[synth.CONFIGS[cfg]["name"]] = {k: r[k] for k in ("n_states", "ms_per_step", "ms_median",
-                                                                        "ms_min", "jacobians_per_s",
-                                                                        "roofline", "hbm_write_gbs", "launch",
-                                                                        "fp64_dfma_equiv_per_jacobian",
-                                                                        "kernel", "specialisation")}
+            r, c = run_config(cfg, max(3, args.steps // 2), args.warmup, rank, cal)
+            per_config[synth.CONFIGS[cfg]["name"]] = r
+            states[synth.CONFIGS[cfg]["name"]] = c[2:5]
+            del c
             torch.cuda.empty_cache()
     batched = batched_form(max(3, args.steps // 2), args.warmup) if not args.headline_only else None
-    fd = fd_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), 3, 1) \
-        if not (args.headline_only or args.no_fd) else None
-    cvf = cv_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
-                  args.warmup) if not args.headline_only else None
-    dyf = dydt_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
-                    args.warmup) if not args.headline_only else None
-    concf = conc_form(dict(per_config, **{synth.CONFIGS[HEADLINE_CFG]["name"]: res}), max(3, args.steps // 2),
-                      args.warmup) if not args.headline_only else None
+    fd = fd_form(per_config, 3, 1) if not (args.headline_only or args.no_fd) else None
+    cvf = cv_form(per_config, max(3, args.steps // 2), args.warmup) if not args.headline_only else None
+    dyf = dydt_form(per_config, max(3, args.steps // 2), args.warmup) if not args.headline_only else None
+    concf = conc_form(per_config, max(3, args.steps // 2), args.warmup) if not args.headline_only else None
     serving = serving_form() if not (args.headline_only or args.no_serving) else None
-    per_config[synth.CONFIGS[HEADLINE_CFG]["name"]] = {k: res[k] for k in ("n_states", "ms_per_step",
-                                                                            "ms_median", "ms_min",
-                                                                            "jacobians_per_s", "roofline",
-                                                                            "hbm_write_gbs", "launch",
-                                                                            "fp64_dfma_equiv_per_jacobian",
-                                                                            "kernel", "specialisation")}
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
+    # the oracle on the host cores, per model, with the parity report of each timed launch
+    cpu = {}
+    if not args.no_cpu_baseline:
+        for cfg in (0, 1, 2, 3):
+            name = synth.CONFIGS[cfg]["name"]
+            if name in per_config:
+                cpu[name] = cpu_baseline(cfg, *states[name], sample=per_config[name]["_parity_sample"],
+                                         budget_s=12.0 if cfg == HEADLINE_CFG else 4.0)
     roof = dict(res["roofline"])
     roof["traffic"] = stored_traffic(HEADLINE_CFG, res["n_states"])
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof["algorithmic_bytes"] = res["n_states"] * (8 * (res["n_species"] + 1) ** 2 + 8 * (res["n_species"] + 2))
     roof["peak_source"] = "measured FP64 FMA throughput on this GPU in this run (libpjcalib)"
+    # the line: the standard keys first, then the per-model numbers and the forms' headline numbers
+    # (the end of the line is what a tail of the output keeps); full records in the detail file
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(HEADLINE_CFG), "model": synth.CONFIGS[HEADLINE_CFG]["name"],
+        "config": {"workload": workload_name(HEADLINE_CFG), "model": headline,
                    "n_states_per_gpu": res["n_states"], "n_species": res["n_species"],
                    "n_reactions": res["n_reactions"], "parallelism": "states sharded over %d GPU(s)" % ws,
                    "l2": "flushed before every timed step (256 MB write)", "launch": res["launch"]},
@@ -970,17 +1096,22 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
         "e2e": e2e,
-        "calibration": cal,
-        "per_config": per_config,
-        "batched_form": batched,
-        "fd_form": fd,
-        "cv_form": cvf,
-        "dydt_form": dyf,
-        "conc_form": concf,
-        "serving_form": serving,
+        "calibration": {"fp64_tflops": _sig(cal["fp64_tflops"]), "store_gbs": _sig(cal["store_gbs"]),
+                        "fma_per": {k: _sig(v, 3) for k, v in cal["ratios"].items()}},
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(HEADLINE_CFG)
+    if headline in cpu:
+        line["cpu_baseline"] = {k: v for k, v in cpu[headline].items() if k != "parity"}
+    line["forms"] = compact_forms(batched, serving, dyf, cvf, fd, concf)
+    line["per_config"] = {name: compact_config(r, cpu.get(name)) for name, r in per_config.items()}
+    dp = detail_path(args)
+    if dp:
+        detail = {"per_config": {k: {kk: vv for kk, vv in r.items() if kk != "_parity_sample"}
+                                 for k, r in per_config.items()},
+                  "cpu_baseline": cpu, "calibration": cal, "batched_form": batched, "fd_form": fd, "cv_form": cvf,
+                  "dydt_form": dyf, "conc_form": concf, "serving_form": serving}
+        with open(dp, "w") as f:
+            json.dump(detail, f, indent=1)
+        line["detail_file"] = os.path.relpath(dp, os.getcwd())
     print(json.dumps(line))
     sys.stdout.flush()
     if ws > 1:
@@ -1095,6 +1226,9 @@ def main():
     ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
     ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
     ap.add_argument("--dydt", action="store_true", help="with --profile: the source-term kernel")
+    ap.add_argument("--detail", default=None, metavar="PATH",
+                    help="file for the full measurement records (default gpurun_out/bench_detail.json if that "
+                         "directory exists)")
     ap.add_argument("--launch", default=None, metavar="WPS,GROUPS,CTAS",
                     help="fixed launch shape of the headline model (skips the autotuner, e.g. for ncu runs)")
     args = ap.parse_args()
