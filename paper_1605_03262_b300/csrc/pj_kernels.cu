@@ -51,6 +51,10 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
         sc.rows_per_chunk = 0;
         sc.part = take(m.ngp);
     }
+    // The reaction stage reads the same species of several states at once (group g at g * total):
+    // a total of 2 mod 16 doubles puts up to eight groups in eight different pairs of shared-memory
+    // banks (a total of 0 or 8 mod 16 would put several in one pair and serialise their loads).
+    o += (2 - o % 16 + 16) % 16;
     sc.total = o;
     return sc;
 }

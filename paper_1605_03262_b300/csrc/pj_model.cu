@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <numeric>
 #include <stdexcept>
@@ -227,7 +228,18 @@ enum RecMode {
 // Lays out one chunk of tasks over the 32 lanes of a warp. Tasks are packed largest first onto
 // the least-loaded lane (longest-processing-time rule); each lane's items run back to back with an
 // end flag on the last item of every task; shorter lanes are padded with neutral items. Which lane
-// evaluates a task does not change its value: a task is always summed by one lane, in item order.
+// evaluates a task does not change its value: a task is always summed by one lane, in the order
+// its items are laid out here.
+//
+// Item order (shared-memory banks): the items of one record row are read by one load instruction
+// per operand array, 32 lanes at once. A 64-bit load is served in half-warps; two lanes of a
+// half-warp whose different indices agree mod 16 fall in the same pair of 4-byte banks and
+// serialise. So the rows are filled one at a time, and each lane takes, of the items it may take
+// next (the rest of its current task, or any item of a task it has not started), the first whose
+// indices (the operand index, and for column sums also the reaction index) are free mod 16 in its
+// half-warp so far; failing that, the one with the fewest clashes. The order depends on the model
+// only, so every launch shape sums each task in the same order (bitwise the same results).
+//
 // Records are lane-interleaved (record ioff + 32 t + lane is the lane's t-th item). The chunk table
 // gets (ioff, rows).
 void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code, int pad_aux, RecMode mode,
@@ -246,6 +258,124 @@ void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code,
     }
     size_t len = 0;
     for (int l = 0; l < 32; ++l) len = std::max(len, load[l]);
+
+    // bank-aware item order: seq[l][pos] = (task, item) or (null, 0) for a neutral item
+    struct Slot {
+        const Task *t = nullptr;
+        int q = 0;
+    };
+    std::vector<std::vector<Slot>> seq(32, std::vector<Slot>(len));
+    {
+        struct LaneState {
+            std::vector<const Task *> pending;   // tasks not started, in packing order
+            const Task *cur = nullptr;
+            std::vector<int> rest;               // items of cur not yet placed, in task order
+        };
+        std::vector<LaneState> ls(32);
+        for (int l = 0; l < 32; ++l) ls[l].pending = lane[l];
+        const bool two = mode == kRecAux;
+        auto key0 = [&](const Slot &x) -> long long { return x.t ? (long long)x.t->idx[x.q] : (long long)pad_idx; };
+        auto key1 = [&](const Slot &x) -> long long { return x.t ? (long long)x.t->aux[x.q] : (long long)pad_aux; };
+        for (size_t row = 0; row < len; ++row) {
+            for (int h = 0; h < 2; ++h) {
+                // candidates of each lane of the half-warp (its next items), then a matching of lanes
+                // to distinct banks (augmenting paths, lanes with the fewest choices first); a lane
+                // left unmatched takes its candidate with the fewest clashes
+                std::vector<std::vector<Slot>> cand(16);
+                std::vector<int> start_task(16, -1);   // a lane starting a task: candidates from pending
+                for (int i = 0; i < 16; ++i) {
+                    LaneState &st = ls[16 * h + i];
+                    if (st.cur && !st.rest.empty()) {
+                        for (int u : st.rest) cand[i].push_back(Slot{st.cur, u});
+                    } else if (!st.pending.empty()) {
+                        start_task[i] = 1;
+                        for (const Task *t : st.pending)
+                            for (int u = 0; u < int(t->idx.size()); ++u) cand[i].push_back(Slot{t, u});
+                    }
+                }
+                long long owner_addr[16];
+                int owner[16];
+                for (int b2 = 0; b2 < 16; ++b2) owner[b2] = -1, owner_addr[b2] = -1;
+                bool pads = false;
+                for (int i = 0; i < 16; ++i)
+                    if (cand[i].empty()) pads = true;
+                if (pads) {
+                    owner[pad_idx & 15] = 16;              // the neutral items' shared address
+                    owner_addr[pad_idx & 15] = pad_idx;
+                }
+                std::vector<int> choice(16, -1);
+                std::vector<int> order;
+                for (int i = 0; i < 16; ++i)
+                    if (!cand[i].empty()) order.push_back(i);
+                std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cand[x].size() < cand[y].size(); });
+                std::function<bool(int, std::vector<char> &)> augment = [&](int i, std::vector<char> &seen) {
+                    for (int c = 0; c < int(cand[i].size()); ++c) {
+                        const long long a = key0(cand[i][c]);
+                        const int bk = int(a & 15);
+                        if (seen[bk] || owner[bk] == 16) continue;
+                        seen[bk] = 1;
+                        if (owner[bk] == -1 || augment(owner[bk], seen)) {
+                            owner[bk] = i, owner_addr[bk] = a, choice[i] = c;
+                            return true;
+                        }
+                    }
+                    return false;
+                };
+                for (int i : order) {
+                    std::vector<char> seen(16, 0);
+                    augment(i, seen);
+                }
+                // unmatched lanes: the candidate with the fewest clashes against what the row holds so
+                // far (an address already in the row costs nothing: the lanes share it); the column
+                // sums' reaction index counts as a second operand
+                std::vector<std::vector<long long>> in0(16), in1(16);
+                auto add = [](std::vector<long long> &v, long long x) {
+                    if (std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+                };
+                auto clash = [](const std::vector<long long> &v, long long x) {
+                    return std::find(v.begin(), v.end(), x) != v.end() ? 0 : int(v.size());
+                };
+                if (pads) add(in1[pad_aux & 15], pad_aux);
+                for (int b2 = 0; b2 < 16; ++b2)
+                    if (owner[b2] != -1) add(in0[b2], owner_addr[b2]);
+                if (two)
+                    for (int i = 0; i < 16; ++i)
+                        if (choice[i] >= 0) add(in1[key1(cand[i][choice[i]]) & 15], key1(cand[i][choice[i]]));
+                for (int i : order) {
+                    if (choice[i] >= 0) continue;
+                    int bc = 1 << 30, bi = 0;
+                    for (int c = 0; c < int(cand[i].size()) && bc > 0; ++c) {
+                        int v = clash(in0[key0(cand[i][c]) & 15], key0(cand[i][c]));
+                        if (two) v += clash(in1[key1(cand[i][c]) & 15], key1(cand[i][c]));
+                        if (v < bc) bc = v, bi = c;
+                    }
+                    choice[i] = bi;
+                    add(in0[key0(cand[i][bi]) & 15], key0(cand[i][bi]));
+                    if (two) add(in1[key1(cand[i][bi]) & 15], key1(cand[i][bi]));
+                }
+                for (int i = 0; i < 16; ++i) {
+                    const int l = 16 * h + i;
+                    LaneState &st = ls[l];
+                    if (choice[i] < 0) {
+                        seq[l][row] = Slot{};
+                        continue;
+                    }
+                    const Slot pick = cand[i][choice[i]];
+                    if (start_task[i] >= 0) {
+                        st.cur = pick.t;
+                        st.pending.erase(std::find(st.pending.begin(), st.pending.end(), pick.t));
+                        st.rest.clear();
+                        for (int u = 0; u < int(pick.t->idx.size()); ++u)
+                            if (u != pick.q) st.rest.push_back(u);
+                    } else {
+                        st.rest.erase(std::find(st.rest.begin(), st.rest.end(), pick.q));
+                    }
+                    seq[l][row] = pick;
+                }
+            }
+        }
+    }
+
     const size_t ioff = recs.size() / words;
     recs.resize((ioff + len * 32) * words, 0u);
     for (size_t x = ioff; x < ioff + len * 32; ++x) {           // neutral items (coefficient 0)
@@ -253,25 +383,27 @@ void emit_chunk(std::vector<const Task *> tasks, unsigned pad_idx, int pad_code,
         if (mode == kRecAux) recs[x * words + 2] = uint32_t(pad_aux);
     }
     for (int l = 0; l < 32; ++l) {
-        size_t pos = 0;
-        for (const Task *t : lane[l]) {
-            for (size_t q = 0; q < t->idx.size(); ++q, ++pos) {
-                uint32_t *r = &recs[(ioff + pos * 32 + l) * words];
-                const bool last = q + 1 == t->idx.size();
-                const unsigned end = last ? 0x80000000u : 0u;
-                if (mode == kRecCoef) {
-                    r[0] = t->idx[q] | (q == 0 ? 0x40000000u : 0u) | (t->partial ? 0x20000000u : 0u) | end;
-                    r[1] = uint32_t(t->dst);
-                    const double coef = t->scale * double(t->code[q] - kNuBias);
-                    uint64_t bits;
-                    std::memcpy(&bits, &coef, 8);
-                    r[2] = uint32_t(bits);
-                    r[3] = uint32_t(bits >> 32);
-                } else {
-                    r[0] = t->idx[q] | (unsigned(t->code[q]) << 24) | end;
-                    r[1] = last ? uint32_t(t->dst) : 0u;
-                    if (mode == kRecAux) r[2] = uint32_t(t->aux[q]);
-                }
+        for (size_t pos = 0; pos < len; ++pos) {
+            const Slot &x = seq[l][pos];
+            if (!x.t) continue;
+            const Task *t = x.t;
+            const bool first = pos == 0 || seq[l][pos - 1].t != t;
+            const bool last = pos + 1 == len || seq[l][pos + 1].t != t;
+            uint32_t *r = &recs[(ioff + pos * 32 + l) * words];
+            const unsigned end = last ? 0x80000000u : 0u;
+            const int q = x.q;
+            if (mode == kRecCoef) {
+                r[0] = t->idx[q] | (first ? 0x40000000u : 0u) | (t->partial ? 0x20000000u : 0u) | end;
+                r[1] = uint32_t(t->dst);
+                const double coef = t->scale * double(t->code[q] - kNuBias);
+                uint64_t bits;
+                std::memcpy(&bits, &coef, 8);
+                r[2] = uint32_t(bits);
+                r[3] = uint32_t(bits >> 32);
+            } else {
+                r[0] = t->idx[q] | (unsigned(t->code[q]) << 24) | end;
+                r[1] = last ? uint32_t(t->dst) : 0u;
+                if (mode == kRecAux) r[2] = uint32_t(t->aux[q]);
             }
         }
     }
