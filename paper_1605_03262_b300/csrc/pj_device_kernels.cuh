@@ -625,85 +625,147 @@ __device__ __forceinline__ void init_neutral(const DevModel &m, const Scratch &s
     }
 }
 
-// One state, evaluated by one group: state prep, thermodynamics, reaction stage, gathers and rows.
-// State scalars that the stages after the state prep use.
-struct Prep {
-    StateScalars s;
-    double cp, dcpdT;
+// Per-state scalars of a round: each is computed once per state, by thread x of the CTA for the
+// round's state x, and read by the state's group from its scalar block (sc.scal). Computed in the
+// group instead, every warp of the group would issue the same FP64 operations (divisions, logs)
+// again: on a GPU whose FP64 pipe binds, that repetition cost about 8 % of the Jacobian's issue
+// slots with two-warp groups and more with wider ones.
+enum ScalarSlot : int {
+    kST = 0, kSinvT, kSlnT, kSP, kSlnP, kSW, kSrho, kSCtot,   // read by the reaction stage as a block
+    kSinvrho, kScp, kSdcpdT, kSinvcp, kSJ00, kSe0, kSHf, kSNumScalars
 };
+// Group sums the CTA-wide scalar steps read (sc.red): sum Y/W, c_p, dc_p/dT, rho (concentration
+// basis), then the energy sums HA, Hf, HJ0, CF.
+enum RedSlot : int { kRsYW = 0, kRcp, kRdcp, kRrho, kRHA, kRHf, kRHJ0, kRCF };
 
-// State prep and thermodynamics (Sections 2.1-2.2): Y, c_p,k, H_k, B_k (and derivatives) of every
-// species, the mixture sums, and the concentrations. Ends with the group synchronised. CV: the
-// input is rho instead of p, and the energy arrays hold c_v,k = c_p,k - R/W_k and the molar
-// internal energy U_k = H_k - R T (Section 3.3), so that the energy row below is the constant-volume one.
+// Step 1 of a round (all threads of the CTA): T, 1/T, ln T and p (rho at constant volume) of every
+// state of the round. base: the round's first state; gact: its states.
+template <bool CV>
+__device__ __forceinline__ void round_scalars_in(const DevModel &m, const Scratch &sc, const StateIO &io,
+                                                 long long base, int gact, double *S0, int stride) {
+    const int x = threadIdx.x;
+    if (x < gact) {
+        double *o = S0 + size_t(x) * stride + sc.scal;
+        const long long st = base + x;
+        const double T = __ldg(io.T + st);
+        o[kST] = T;
+        o[kSinvT] = 1.0 / T;
+        o[kSlnT] = fast_log(T, m.tables);
+        o[CV ? kSrho : kSP] = __ldg(io.P + st);
+    }
+    __syncthreads();
+}
+
+// Step 2 (all threads): the mixture scalars from the group sums (Section 2.1): W = 1/sum(Y/W), [M]
+// (Ctot) = p/(RT) or, at constant volume, rho sum(Y/W) with p = Ctot R T, rho, ln p and 1/rho.
+template <bool CV, bool CONC>
+__device__ __forceinline__ void round_scalars_mix(const DevModel &m, const Scratch &sc, int gact, double *S0,
+                                                  int stride) {
+    __syncthreads();                                    // the groups' sums are in place
+    const int x = threadIdx.x;
+    if (x < gact) {
+        double *o = S0 + size_t(x) * stride + sc.scal;
+        const double *r = S0 + size_t(x) * stride + sc.red;
+        const double sYW = r[kRsYW], T = o[kST];
+        o[kSW] = 1.0 / sYW;
+        o[kScp] = r[kRcp];
+        o[kSdcpdT] = r[kRdcp];
+        if constexpr (CV) {                                 // p = rho R T / W (Eq. e:state)
+            o[kSCtot] = o[kSrho] * sYW;
+            o[kSP] = o[kSCtot] * kR * T;
+        } else if constexpr (CONC) {
+            o[kSCtot] = o[kSP] / (kR * T);
+            o[kSrho] = r[kRrho];
+        } else {
+            o[kSCtot] = o[kSP] / (kR * T);
+            o[kSrho] = o[kSCtot] * o[kSW];
+        }
+        o[kSlnP] = fast_log(o[kSP], m.tables);
+        o[kSinvrho] = 1.0 / o[kSrho];
+        o[kSinvcp] = 1.0 / o[kScp];
+    }
+    __syncthreads();
+}
+
+// The scalars of one state (after step 2), as the reaction stage and the gathers use them.
+__device__ __forceinline__ StateScalars load_scalars(const double *o) {
+    StateScalars s;
+    s.T = o[kST], s.invT = o[kSinvT], s.lnT = o[kSlnT], s.P = o[kSP], s.lnP = o[kSlnP], s.W = o[kSW];
+    s.rho = o[kSrho], s.Ctot = o[kSCtot];
+    return s;
+}
+
+// State prep and thermodynamics (Sections 2.1-2.2), called by every thread of the CTA (active:
+// the thread's group has a state this round): Y, c_p,k, H_k, B_k (and derivatives) of every
+// species, the mixture sums, the round's scalars and the concentrations. CV: the input is rho
+// instead of p, and the energy arrays hold c_v,k = c_p,k - R/W_k and the molar internal energy
+// U_k = H_k - R T (Section 3.3), so that the energy row below is the constant-volume one.
 // CONC: the molar-concentration basis at constant pressure; the input is (T, P, V, n_1..n_{N-1}),
 // [X_k] = n_k / V and [X_N] = P / (R T) - sum_{k<N} [X_k] by the ideal-gas law.
 template <bool JAC, int WPS, bool CV = false, bool CONC = false>
-__device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
-                                           const StateIO &io, long long st, const Grp &g) {
+__device__ __forceinline__ void state_prep(const DevModel &m, const Scratch &sc, double *S, const double *smem_const,
+                                           const StateIO &io, long long st, const Grp &g, bool active, int gact,
+                                           double *S0, int stride) {
     const int N = m.N;
     const int G = WPS ? WPS * 32 : g.G, NW = WPS ? WPS : g.wps;
     const int t = g.t, lane = g.lane, wg = g.wg;
     const double *sInvW = smem_const + 128 + N;
     double *sC = S + sc.C, *sB = S + sc.B, *sdB = S + sc.dB, *sH = S + sc.H, *scp = S + sc.cpk;
     double *sJk0 = S + sc.Jk0, *sf = S + sc.f, *sred = S + sc.red;
-    // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
-    StateScalars s;
-    s.T = __ldg(io.T + st);
-    if constexpr (CV) s.rho = __ldg(io.P + st);
-    else if constexpr (!CONC) s.P = __ldg(io.P + st);
-    s.invT = 1.0 / s.T;
-    s.lnT = fast_log(s.T, m.tables);
-    const double *Ys = io.Y + st * io.ldy;
+    const double *o = S + sc.scal;
+    round_scalars_in<CV>(m, sc, io, st - g.grp, gact, S0, stride);
     double *sY = sf;   // Y parks in the f array until the concentrations exist
-    double rho_c = 0.0;
-    if constexpr (CONC) {
-        // every warp forms the sums in the same lane order, so all hold the same bits
-        s.P = __ldg(io.P + st);
-        s.Ctot = s.P / (kR * s.T);
-        const double invV = 1.0 / __ldg(io.V + st);
-        double sx = 0.0;
-        for (int k = lane; k < N - 1; k += 32) sx += __ldg(Ys + k) * invV;
-        sx = warp_sum(sx);
-        for (int k = t; k < N; k += G) sC[k] = k < N - 1 ? __ldg(Ys + k) * invV : s.Ctot - sx;
+    if (active) {
+        // ---- state prep and thermodynamics (Sections 2.1-2.2) ----
+        const double T = o[kST], invT = o[kSinvT], lnT = o[kSlnT];
+        const double *Ys = io.Y + st * io.ldy;
+        if constexpr (CONC) {
+            // every warp forms the sums in the same lane order, so all hold the same bits
+            const double Ctot = o[kSP] / (kR * T);
+            const double invV = 1.0 / __ldg(io.V + st);
+            double sx = 0.0;
+            for (int k = lane; k < N - 1; k += 32) sx += __ldg(Ys + k) * invV;
+            sx = warp_sum(sx);
+            for (int k = t; k < N; k += G) sC[k] = k < N - 1 ? __ldg(Ys + k) * invV : Ctot - sx;
+            group_sync<WPS>(g);
+            double rho_c = 0.0;
+            for (int k = lane; k < N; k += 32) rho_c = fma(sC[k], __ldg(m.W + k), rho_c);
+            rho_c = warp_sum(rho_c);
+            if (t == 0) sred[kRrho] = rho_c;
+            const double irho = 1.0 / rho_c;
+            for (int k = t; k < N; k += G) sY[k] = sC[k] * __ldg(m.W + k) * irho;
+        } else {
+            for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
+        }
+        for (int k = t; k < N; k += G) {
+            const Thermo th = species_thermo<JAC>(m, k, T, invT, lnT);
+            scp[k] = kR * sInvW[k] * (CV ? th.cpR - 1.0 : th.cpR);
+            sH[k] = kR * (CV ? th.HR - T : th.HR);
+            sB[k] = th.B;
+            if constexpr (JAC) {
+                sdB[k] = th.dB;
+                sJk0[k] = kR * sInvW[k] * th.dcpR;   // dcp_k/dT parks in the J_k0 array
+            }
+        }
         group_sync<WPS>(g);
-        for (int k = lane; k < N; k += 32) rho_c = fma(sC[k], __ldg(m.W + k), rho_c);
-        rho_c = warp_sum(rho_c);
-        const double irho = 1.0 / rho_c;
-        for (int k = t; k < N; k += G) sY[k] = sC[k] * __ldg(m.W + k) * irho;
-    } else {
-        for (int k = t; k < N; k += G) sY[k] = __ldg(Ys + k);
-    }
-    for (int k = t; k < N; k += G) {
-        const Thermo th = species_thermo<JAC>(m, k, s.T, s.invT, s.lnT);
-        scp[k] = kR * sInvW[k] * (CV ? th.cpR - 1.0 : th.cpR);
-        sH[k] = kR * (CV ? th.HR - s.T : th.HR);
-        sB[k] = th.B;
-        if constexpr (JAC) {
-            sdB[k] = th.dB;
-            sJk0[k] = kR * sInvW[k] * th.dcpR;   // dcp_k/dT parks in the J_k0 array
-        }
-    }
-    group_sync<WPS>(g);
-    // species sums sum Y/W, sum Y cp_k, sum Y dcp_k/dT in a fixed 32-lane order: a one-warp group
-    // computes all three; in wider groups warp w computes every NW-th sum and shares it (same order,
-    // same bits)
-    double sYW, cp, dcpdT;
-    if (NW == 1) {
-        double r1 = 0.0, r2 = 0.0, r3 = 0.0;
-        for (int k = lane; k < N; k += 32) {
-            const double y = sY[k];
-            r1 = fma(y, sInvW[k], r1);
-            r2 = fma(y, scp[k], r2);
-            if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
-        }
-        double r4 = 0.0;
-        warp_sum4(r1, r2, r3, r4);
-        sYW = r1;
-        cp = r2;
-        dcpdT = JAC ? r3 : 0.0;
-    } else {
-        if (JAC && NW == 2 && wg == 0) {                // warp 0: sums 0 and 2, reduced together
+        // species sums sum Y/W, sum Y cp_k, sum Y dcp_k/dT in a fixed 32-lane order: a one-warp group
+        // computes all three; in wider groups warp w computes every NW-th sum (same order, same bits)
+        if (NW == 1) {
+            double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+            for (int k = lane; k < N; k += 32) {
+                const double y = sY[k];
+                r1 = fma(y, sInvW[k], r1);
+                r2 = fma(y, scp[k], r2);
+                if constexpr (JAC) r3 = fma(y, sJk0[k], r3);
+            }
+            double r4 = 0.0;
+            warp_sum4(r1, r2, r3, r4);
+            if (lane == 0) {
+                sred[kRsYW] = r1;
+                sred[kRcp] = r2;
+                sred[kRdcp] = JAC ? r3 : 0.0;
+            }
+        } else if (JAC && NW == 2 && wg == 0) {             // warp 0: sums 0 and 2, reduced together
             double r = 0.0, u = 0.0;
             for (int k = lane; k < N; k += 32) {
                 const double y = sY[k];
@@ -712,8 +774,8 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
             }
             warp_sum2(r, u);
             if (lane == 0) {
-                sred[0] = r;
-                sred[2] = u;
+                sred[kRsYW] = r;
+                sred[kRdcp] = u;
             }
         } else {
             for (int q = wg; q < (JAC ? 3 : 2); q += NW) {
@@ -723,27 +785,15 @@ __device__ __forceinline__ Prep state_prep(const DevModel &m, const Scratch &sc,
                 r = warp_sum(r);
                 if (lane == 0) sred[q] = r;
             }
+            if (!JAC && wg == 0 && lane == 0) sred[kRdcp] = 0.0;
         }
-        group_sync<WPS>(g);
-        sYW = sred[0];
-        cp = sred[1];
-        dcpdT = JAC ? sred[2] : 0.0;
     }
-    s.W = 1.0 / sYW;
-    if constexpr (CV) {                                 // p = rho R T / W (Eq. e:state)
-        s.Ctot = s.rho * sYW;
-        s.P = s.Ctot * kR * s.T;
-    } else if constexpr (CONC) {
-        s.rho = rho_c;
-    } else {
-        s.Ctot = s.P / (kR * s.T);
-        s.rho = s.Ctot * s.W;
+    round_scalars_mix<CV, CONC>(m, sc, gact, S0, stride);
+    if (active && !CONC) {
+        const double rho = o[kSrho];
+        for (int k = t; k < N; k += G) sC[k] = rho * sY[k] * sInvW[k];
     }
-    s.lnP = fast_log(s.P, m.tables);
-    if constexpr (!CONC)
-        for (int k = t; k < N; k += G) sC[k] = s.rho * sY[k] * sInvW[k];
-    group_sync<WPS>(g);
-    return Prep{s, cp, dcpdT};
+    // the reaction stage that follows starts with a CTA barrier
 }
 
 // Molar-concentration basis at constant pressure: state (T, V, n_1..n_{N-1}) at fixed P, with
@@ -869,10 +919,14 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     double *sq = S + sc.q, *sth = S + sc.th, *sa = S + sc.a, *sdH = S + sc.dH, *sb = S + sc.b;
     double *spart = S + sc.part;
     (void)sHS;
-    Prep pp{};
-    if (active) pp = state_prep<JAC, WPS, CV, CONC>(m, sc, S, smem_const, io, st, g);
-    const StateScalars s = pp.s;
-    const double cp = pp.cp, dcpdT = pp.dcpdT;
+    state_prep<JAC, WPS, CV, CONC>(m, sc, S, smem_const, io, st, g, active, gact, S0, stride);
+    StateScalars s{};
+    double cp = 0.0, dcpdT = 0.0, invrho = 0.0, invcp = 0.0;
+    if (active) {                                       // (an inactive group's scratch may not exist)
+        const double *o = S + sc.scal;
+        s = load_scalars(o);
+        cp = o[kScp], dcpdT = o[kSdcpdT], invrho = o[kSinvrho], invcp = o[kSinvcp];
+    }
     double *sred = S + sc.red;
     // ---- reaction stage, all of the round's states together ----
     // Item k = (reaction i, group gg), reactions in code-path order and groups fastest: a warp's
@@ -881,10 +935,6 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     // families first, so warps that drew falloff items take fewer of the rest and the stage ends
     // balanced. The arithmetic of a reaction does not depend on who evaluates it.
     __shared__ int s_next_item;
-    if (active && t == 0) {
-        double *o = S + sc.scal;
-        o[0] = s.T, o[1] = s.invT, o[2] = s.lnT, o[3] = s.P, o[4] = s.lnP, o[5] = s.W, o[6] = s.rho, o[7] = s.Ctot;
-    }
     if (threadIdx.x == 0) s_next_item = blockDim.x;     // every warp's first run is its own
     __syncthreads();
     const int nitems = R * gact;
@@ -896,10 +946,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         if (k < nitems) {
             const int i = k / gact, gg = k - i * gact;
             double *Sg = S0 + size_t(gg) * stride;
-            const double *v = Sg + sc.scal;
-            StateScalars sg;
-            sg.T = v[0], sg.invT = v[1], sg.lnT = v[2], sg.P = v[3], sg.lnP = v[4], sg.W = v[5], sg.rho = v[6];
-            sg.Ctot = v[7];
+            const StateScalars sg = load_scalars(Sg + sc.scal);
             reaction<JAC, CV>(m, i, sg, Sg + sc.C, Sg + sc.B, Sg + sc.dB, Sg + sc.H, sNu, Sg + sc.q, Sg + sc.th,
                               Sg + sc.a, Sg + sc.dH, Sg + sc.b);
         }
@@ -907,7 +954,6 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     __syncthreads();
     if (!active) return;
 
-    const double invrho = 1.0 / s.rho;
     if constexpr (!JAC) {
         double w = 0.0;                                 // omega_k through the species-gather schedule
         walk<GB, false, false>(m.g_chunk, m.ng, wg, NW, m.g_rec, lane, no_op,
@@ -931,7 +977,6 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         for (int k = lane; k < N; k += 32) hf = fma(sH[k] * sInvW[k], sf[k], hf);
         hf = warp_sum(hf);
         double *out = io.dydt + st * io.ldd;
-        const double invcp = 1.0 / cp;
         for (int k = t; k <= N; k += G) out[k] = (k == 0) ? -hf * invcp : sf[k - 1];
         group_sync<WPS>(g);
         return;
@@ -1064,7 +1109,6 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
             HJ0 = sred[6];
             CF = sred[7];
         }
-        const double invcp = 1.0 / cp;
         const double J00 = -invcp * (fma(-dcpdT * invcp, Hf, CF) + HJ0);
         const double HSN = sHS[N - 1], cpN = scp[N - 1];
         const double e0 = Hf * invcp * invcp;
@@ -1330,6 +1374,69 @@ __global__ void __launch_bounds__(512, 1) pj_batch_kernel(const __grid_constant_
             __syncthreads();
         }
         run_tile<JAC>(s_m, it, smem, tl.begin, tl.begin + tl.count, g);
+        __syncthreads();
+    }
+}
+
+// Batched form, specialised for a plan's models (kernels generated by pj_nvrtc.cu). The model of
+// the CTA's current tile sits in s_batch_model (shared memory, visible to every function of the
+// kernel); each (model, group width) pair of the plan is a slot whose sizes, offsets and width
+// Spec supplies as compile-time constants.
+__shared__ DevModel s_batch_model;
+
+template <bool JAC, int WPS, class Spec>
+__device__ __forceinline__ void run_tile_spec(const BatchItem *itp, long long begin, long long end, bool fresh) {
+    extern __shared__ __align__(16) double smem[];
+    const BatchItem &it = *itp;
+    DevModel m = s_batch_model;
+    Spec::spec_model(m);
+    Scratch sc;
+    Spec::spec_scratch(sc);
+    Grp g;
+    g.wps = WPS;
+    g.G = WPS * 32;
+    g.grp = threadIdx.x / g.G;
+    g.t = threadIdx.x - g.grp * g.G;
+    g.lane = threadIdx.x & 31;
+    g.wg = g.t >> 5;
+    const int groups = it.groups;
+    double *S0 = smem + it.shared_const;
+    double *S = S0 + size_t(g.grp) * sc.total;
+    const bool member = g.grp < groups;
+    if (fresh) {
+        load_model_consts(m, smem);
+        if (member) init_neutral<JAC>(m, sc, S, g.t);
+        __syncthreads();
+    }
+    const StateIO io = it.io;
+    for (long long base = begin; base < end; base += groups) {
+        const int gact = int(min((long long)groups, end - base));
+        eval_state<JAC, WPS>(m, sc, S, smem, io, base + g.grp, g, member && g.grp < gact, gact, S0, sc.total);
+    }
+}
+
+// Persistent loop of the specialised batched kernel: CTAs take tiles from the plan's counter and
+// run(slot, item, begin, end, fresh) evaluates one (fresh: the item differs from the CTA's last).
+template <class Run>
+__device__ __forceinline__ void batch_spec_body(const BatchParams &p, Run &&run) {
+    __shared__ int s_tile;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= p.ntiles) break;
+        const BatchTile tl = p.tiles[tile];
+        const BatchItem *it = p.items + tl.item;
+        const bool fresh = tl.item != cur;
+        if (fresh) {
+            const int *src = reinterpret_cast<const int *>(it->m);
+            int *dst = reinterpret_cast<int *>(&s_batch_model);
+            for (int w = threadIdx.x; w < int(sizeof(DevModel) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+        }
+        run(it->pad, it, tl.begin, tl.begin + tl.count, fresh);
+        cur = tl.item;
         __syncthreads();
     }
 }

@@ -30,7 +30,7 @@ Scratch make_scratch(const DevModel &m, bool jac, int wps) {
     sc.cpk = take(N);
     sc.f = take(N);
     sc.red = take(8);
-    sc.scal = take(8);
+    sc.scal = take(kSNumScalars);
     sc.q = take(R + 1);
     if (jac) {
         sc.dB = take(N);
