@@ -684,8 +684,10 @@ BATCH_MIX = ((0, 16384), (1, 65536), (2, 32768), (3, 2048))
 
 def batched_form(steps: int, warmup: int):
     """The batched form against plain per-model launches on one mixed batch of the four model
-    sizes: sequential plain launches (each model at its autotuned shape), one persistent batched
-    launch, and the batched launch replayed from a CUDA graph. Same states and outputs in all three."""
+    sizes: sequential plain launches (each model at its autotuned shape, its kernels specialised),
+    one persistent batched launch with the default plan on the data-driven kernel, and the plan the
+    batch autotuner picks with its kernel specialised for the four models; each plain and replayed
+    from a CUDA graph. Same states and outputs in all of them. Then the same on 64 small requests."""
     import torch
     import paper_1605_03262_b300 as pj
     items, total = [], 0
@@ -694,6 +696,7 @@ def batched_form(steps: int, warmup: int):
         blob = synth.to_bytes(model)
         g = pj.Model(blob)
         autotune.autotune(g, blob, use_cache=False)
+        specialise(g)
         T, P, Y = synth.config_states(cfg, n, seed_offset=2000)
         Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
         N = model.n_species
@@ -701,13 +704,6 @@ def batched_form(steps: int, warmup: int):
         items.append((g, Td, Pd, Yd, J))
         total += n
     flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
-
-    def plain():
-        for g, Td, Pd, Yd, J in items:
-            g.eval_jacobian(Td, Pd, Yd, out=J)
-
-    plan = pj.BatchPlan(items)
-    graph = plan.capture()
 
     def timed(fn):
         for _ in range(warmup):
@@ -723,17 +719,42 @@ def batched_form(steps: int, warmup: int):
             e.record()
             torch.cuda.synchronize()
             ms.append(s.elapsed_time(e))
-        return float(np.mean(ms))
+        return float(np.median(ms))
 
-    t_plain = timed(plain)
-    t_batch = timed(plan.run)
-    t_graph = timed(graph.replay)
-    out = {"mix": {synth.CONFIGS[c]["name"]: n for c, n in BATCH_MIX}, "total_states": total,
-           "plain_sequential": {"ms": t_plain, "jacobians_per_s": total / (t_plain * 1e-3), "launches": len(items)},
-           "batched_persistent": {"ms": t_batch, "jacobians_per_s": total / (t_batch * 1e-3), "launches": 1,
-                                  "tiles": plan.n_tiles, "threads_per_cta": plan.threads_per_cta},
-           "batched_graph": {"ms": t_graph, "jacobians_per_s": total / (t_graph * 1e-3), "launches": 1}}
-    del plan, graph
+    def forms(its, n_states):
+        def plain():
+            for g, Td, Pd, Yd, J in its:
+                g.eval_jacobian(Td, Pd, Yd, out=J)
+
+        plain_graph = torch.cuda.CUDAGraph()
+        s_cap = torch.cuda.Stream()
+        s_cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_cap):
+            plain()                        # warm-up outside the capture
+            torch.cuda.synchronize()
+            with torch.cuda.graph(plain_graph, stream=s_cap):
+                for g, Td, Pd, Yd, J in its:
+                    g.eval_jacobian(Td, Pd, Yd, out=J, stream=s_cap)
+        torch.cuda.current_stream().wait_stream(s_cap)
+        dflt = pj.BatchPlan(its)
+        dflt_graph = dflt.capture()
+        tuned, rep = autotune.autotune_batch(its, use_cache=False)
+        tuned_graph = tuned.capture()
+        out = {"requests": len(its), "total_states": n_states,
+               "plain_sequential": {"ms": timed(plain), "launches": len(its), "kernels": "specialised per model"},
+               "plain_graph": {"ms": timed(plain_graph.replay), "launches": len(its)},
+               "batched_default": {"ms": timed(dflt.run), "graph_ms": timed(dflt_graph.replay), "launches": 1,
+                                   "tiles": dflt.n_tiles, "kernel": "data-driven"},
+               "batched_tuned": {"ms": timed(tuned.run), "graph_ms": timed(tuned_graph.replay), "launches": 1,
+                                 "tiles": tuned.n_tiles, "choice": rep["choice"], "item_shapes": rep["item_shapes"],
+                                 "tuning_ms": rep["timings"], "specialised": rep["specialised"]}}
+        for k in ("plain_sequential", "batched_default", "batched_tuned"):
+            out[k]["jacobians_per_s"] = n_states / (out[k]["ms"] * 1e-3)
+        del dflt, dflt_graph, tuned, tuned_graph, plain_graph
+        return out
+
+    out = {"mix": {synth.CONFIGS[c]["name"]: n for c, n in BATCH_MIX}}
+    out.update(forms(items, total))
 
     # many small batches (the form's use: 64 requests of 16-1,024 states over the four models), one
     # persistent launch against 64 launches, plain or replayed from a graph
@@ -747,32 +768,8 @@ def batched_form(steps: int, warmup: int):
         Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
         small.append((g, Td, Pd, Yd, torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")))
         stotal += n
-
-    def plain_small():
-        for g, Td, Pd, Yd, J in small:
-            g.eval_jacobian(Td, Pd, Yd, out=J)
-
-    plain_graph = torch.cuda.CUDAGraph()
-    s_cap = torch.cuda.Stream()
-    s_cap.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s_cap):
-        plain_small()                      # warm-up outside the capture
-        torch.cuda.synchronize()
-        with torch.cuda.graph(plain_graph, stream=s_cap):
-            for g, Td, Pd, Yd, J in small:
-                g.eval_jacobian(Td, Pd, Yd, out=J, stream=s_cap)
-    torch.cuda.current_stream().wait_stream(s_cap)
-    splan = pj.BatchPlan(small)
-    sgraph = splan.capture()
-    ts_plain, ts_pgraph = timed(plain_small), timed(plain_graph.replay)
-    ts_batch, ts_graph = timed(splan.run), timed(sgraph.replay)
-    out["many_small"] = {
-        "requests": len(small), "total_states": stotal,
-        "plain_sequential": {"ms": ts_plain, "launches": len(small)},
-        "plain_graph": {"ms": ts_pgraph, "launches": len(small)},
-        "batched_persistent": {"ms": ts_batch, "launches": 1, "tiles": splan.n_tiles},
-        "batched_graph": {"ms": ts_graph, "launches": 1}}
-    del items, small, flush, splan, sgraph, plain_graph
+    out["many_small"] = forms(small, stotal)
+    del items, small, flush
     torch.cuda.empty_cache()
     return out
 
@@ -981,17 +978,12 @@ def compact_forms(batched, serving, dyf, cvf, fd, concf) -> dict:
     concentration-basis measurements (the full records go to the detail file)."""
     out = {}
     if batched:
-        ms = batched["many_small"]
-        out["batched"] = {
-            "mix_ms": {"plain": _sig(batched["plain_sequential"]["ms"]),
-                       "persistent": _sig(batched["batched_persistent"]["ms"]),
-                       "graph": _sig(batched["batched_graph"]["ms"])},
-            "small64_ms": {"plain": _sig(ms["plain_sequential"]["ms"]), "plain_graph": _sig(ms["plain_graph"]["ms"]),
-                           "persistent": _sig(ms["batched_persistent"]["ms"]),
-                           "graph": _sig(ms["batched_graph"]["ms"])}}
-        for key in ("shape", "small64_shape"):
-            if key in batched:
-                out["batched"][key] = batched[key]
+        def one(b):
+            return {"plain": _sig(b["plain_sequential"]["ms"]), "plain_graph": _sig(b["plain_graph"]["ms"]),
+                    "default": _sig(b["batched_default"]["ms"]), "default_graph": _sig(b["batched_default"]["graph_ms"]),
+                    "tuned": _sig(b["batched_tuned"]["ms"]), "tuned_graph": _sig(b["batched_tuned"]["graph_ms"]),
+                    "tuned_choice": b["batched_tuned"]["choice"]}
+        out["batched"] = {"mix_ms": one(batched), "small64_ms": one(batched["many_small"])}
     if serving:
         sv = {"capacity_jacobians_per_s": _sig(serving["capacity_closed_loop"]["jacobians_per_s"]),
               "plain_jacobians_per_s": _sig(serving["plain_per_request_closed_loop"]["jacobians_per_s"])}

@@ -258,9 +258,40 @@ typedef struct {
 
 PJ_API int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj_batch_shape *shape,
                            pj_batch **out);
+
+/*
+ * The same plan with a shape per item (item_shapes[i] for items[i]; item_shapes may be NULL, and a
+ * 0 entry takes the default): warps_per_state in {1, 2, 4, 8, 16} (default: the model's
+ * pj_set_launch setting, halved while a state does not fit), states_per_cta (default and upper
+ * bound: as many as the CTA's threads and shared memory allow) and tile_states (default: the
+ * plan's). The autotuner of the batched form chooses these; results do not depend on them.
+ * Errors as pj_batch_create, plus PJ_EINVAL for a width outside the set or wider than the CTA.
+ */
+typedef struct {
+    int warps_per_state;
+    int states_per_cta;
+    int tile_states;
+} pj_batch_item_shape;
+
+PJ_API int pj_batch_create_ex(const pj_batch_item *items, int n_items, int which, const pj_batch_shape *shape,
+                              const pj_batch_item_shape *item_shapes, pj_batch **out);
 PJ_API int pj_batch_run(pj_batch *b, void *stream);
 PJ_API int pj_batch_info(const pj_batch *b, int *n_tiles, size_t *smem_bytes, int *threads_per_cta);
 PJ_API void pj_batch_free(pj_batch *b);
+
+/*
+ * The plan's kernel specialised for its models (the per-mechanism code generation of Sections 4
+ * and 6, as pj_mech_specialize, for a mixed batch): enable != 0 compiles with NVRTC one persistent
+ * kernel in which every distinct (model, warps per state) pair of the plan is a branch with that
+ * model's sizes, shared-memory offsets and group width as compile-time constants, and makes
+ * pj_batch_run launch it; enable == 0 returns to the data-driven kernel. Same results, bit for bit.
+ * Takes seconds (one compile per plan); call it before capturing pj_batch_run into a graph.
+ * pj_batch_spec_info reports whether the plan runs it, its number of branches, the compile time
+ * and code size (any output may be NULL). Errors as pj_mech_specialize.
+ */
+PJ_API int pj_batch_specialize(pj_batch *b, int enable);
+PJ_API int pj_batch_spec_info(const pj_batch *b, int *active, int *slots, double *compile_seconds,
+                              size_t *cubin_bytes);
 
 /*
  * Batched launch that allocates nothing (the paper has no counterpart; it serves callers, not the

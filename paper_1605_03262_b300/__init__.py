@@ -49,6 +49,10 @@ class pj_batch_shape(ctypes.Structure):
     _fields_ = [("threads_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("tile_states", ctypes.c_int)]
 
 
+class pj_batch_item_shape(ctypes.Structure):
+    _fields_ = [("warps_per_state", ctypes.c_int), ("states_per_cta", ctypes.c_int), ("tile_states", ctypes.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -88,6 +92,11 @@ def load_library(path: str = LIB_PATH):
             "pj_launch_smem_bytes": ([vp, i32, ctypes.POINTER(pj_launch), ctypes.POINTER(sz)], i32),
             "pj_batch_create": ([ctypes.POINTER(pj_batch_item), i32, i32, ctypes.POINTER(pj_batch_shape),
                                  ctypes.POINTER(vp)], i32),
+            "pj_batch_create_ex": ([ctypes.POINTER(pj_batch_item), i32, i32, ctypes.POINTER(pj_batch_shape),
+                                    ctypes.POINTER(pj_batch_item_shape), ctypes.POINTER(vp)], i32),
+            "pj_batch_specialize": ([vp, i32], i32),
+            "pj_batch_spec_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(sz)], i32),
             "pj_batch_run": ([vp, vp], i32),
             "pj_batch_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(sz), ctypes.POINTER(i32)], i32),
             "pj_batch_free": ([vp], None),
@@ -400,12 +409,20 @@ class BatchPlan:
     capture run() into a CUDA graph with capture() and replay it."""
 
     def __init__(self, items, which: str = "jacobian", threads_per_cta: int = 0, ctas_per_sm: int = 0,
-                 tile_states: int = 0):
+                 tile_states: int = 0, item_shapes=None):
+        """item_shapes: optional per-item (warps_per_state, states_per_cta, tile_states), 0 = default."""
         self.which = 0 if which == "jacobian" else 1
         arr, self._keep = _batch_items(items, self.which)
         shape = pj_batch_shape(threads_per_cta, ctas_per_sm, tile_states)
         h = ctypes.c_void_p()
-        _check(library().pj_batch_create(arr, len(items), self.which, ctypes.byref(shape), ctypes.byref(h)))
+        if item_shapes is None:
+            _check(library().pj_batch_create(arr, len(items), self.which, ctypes.byref(shape), ctypes.byref(h)))
+        else:
+            if len(item_shapes) != len(items):
+                raise ValueError("one item shape per item")
+            ish = (pj_batch_item_shape * len(items))(*[pj_batch_item_shape(*map(int, x)) for x in item_shapes])
+            _check(library().pj_batch_create_ex(arr, len(items), self.which, ctypes.byref(shape), ish,
+                                                ctypes.byref(h)))
         self._h = h
         nt, sm, th = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int()
         _check(library().pj_batch_info(h, ctypes.byref(nt), ctypes.byref(sm), ctypes.byref(th)))
@@ -413,6 +430,17 @@ class BatchPlan:
 
     def run(self, stream=None) -> None:
         _check(library().pj_batch_run(self._h, _stream_handle(stream)))
+
+    def specialize(self, enable: bool = True) -> dict:
+        """Compile (NVRTC) and use the plan's kernel specialised for its models (pj_batch_specialize);
+        returns spec_info()."""
+        _check(library().pj_batch_specialize(self._h, 1 if enable else 0))
+        return self.spec_info()
+
+    def spec_info(self) -> dict:
+        a, n, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_size_t()
+        _check(library().pj_batch_spec_info(self._h, ctypes.byref(a), ctypes.byref(n), ctypes.byref(t), ctypes.byref(b)))
+        return {"active": bool(a.value), "slots": n.value, "compile_seconds": t.value, "cubin_bytes": b.value}
 
     def capture(self):
         """CUDA graph of one run (counter reset + persistent launch); replay() re-evaluates."""

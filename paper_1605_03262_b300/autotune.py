@@ -9,6 +9,7 @@ evaluates a probe batch with each feasible shape and keeps the fastest. Choices 
 from __future__ import annotations
 
 import hashlib
+import math
 import json
 import os
 import threading
@@ -16,7 +17,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-__all__ = ["candidate_shapes", "autotune", "cache_path"]
+__all__ = ["candidate_shapes", "autotune", "cache_path", "batch_candidates", "autotune_batch"]
 
 _lock = threading.Lock()
 
@@ -152,3 +153,102 @@ def autotune(model, blob: bytes, which: str = "jacobian", probe: Optional[Sequen
     return {"shape": best, "cached": False, "ms": refined.get(best, timings[best]), "n_probe": n,
             "timings": {"%d,%d,%d" % k: v for k, v in sorted(timings.items(), key=lambda kv: kv[1])[:8]},
             "refined": {"%d,%d,%d" % k: v for k, v in sorted(refined.items(), key=lambda kv: kv[1])}}
+
+
+# ---------------------------------------------------------------------------------------------
+# the batched form: one persistent launch over items of several models
+
+def batch_candidates(items, which: str = "jacobian") -> List[dict]:
+    """Candidate plans for a batched launch: CTA sizes (512, 448 or 384 threads) and tiles of 2, 4, 8
+    or 16 rounds of each item's states per CTA (states per CTA from the model's tuned launch shape;
+    the group width is the model's, halved by the library where a state does not fit the CTA, so
+    that the candidates of one CTA size share one specialised kernel)."""
+    out = []
+    for threads in (512, 448, 384):
+        base = []
+        for it in items:
+            wps, groups, _ = it[0].get_launch(which)
+            base.append(max(1, min(groups, threads // (32 * wps))))
+        for rounds in (2, 4, 8, 16):
+            # width 0: the model's own, halved by the library while a state does not fit the CTA
+            out.append({"threads_per_cta": threads, "rounds": rounds,
+                        "item_shapes": [(0, g, rounds * g) for g in base]})
+    return out
+
+
+def _mix_key(items, which: str) -> str:
+    import torch
+    parts = []
+    for it in items:
+        m = it[0]
+        n = int(it[3].shape[0])
+        parts.append("%d:%d:%s:%d" % (m.n_species, m.n_reactions, ",".join(map(str, m.get_launch(which))),
+                                      int(math.log2(max(n, 1)))))
+    return "batch|%s|%s|%s" % (torch.cuda.get_device_name(items[0][0].device), which, ";".join(parts))
+
+
+def autotune_batch(items, which: str = "jacobian", specialise: bool = True, reps: int = 3,
+                   use_cache: bool = True, candidates: Optional[List[dict]] = None):
+    """Choose the batched launch's CTA size and per-item tile sizes for this item mix by timing
+    candidate plans on the data-driven batched kernel (each run after a write larger than L2;
+    median of ``reps``), then, with ``specialise``, the fastest candidate again with its kernel
+    specialised for the mix's models (NVRTC), keeping whichever is faster. Returns (plan, report).
+    The choice is cached by the mix's shape (models' sizes and launch shapes, log2 of each item's
+    state count)."""
+    import torch
+    from . import BatchPlan
+    key = _mix_key(items, which)
+    cands = candidates if candidates is not None else batch_candidates(items, which)
+    hit = None
+    if use_cache and candidates is None:
+        with _lock:
+            hit = _load_cache().get(key)
+        if hit:
+            cands = [c for c in cands if c["threads_per_cta"] == hit[0] and c["rounds"] == hit[1]] or cands
+    if not cands:
+        raise RuntimeError("no feasible batched launch for these items")
+    l2 = torch.cuda.get_device_properties(items[0][0].device).L2_cache_size
+    flush = torch.empty(max(2 * l2, 1 << 20) // 8, dtype=torch.float64, device=items[0][0].device)
+
+    def time_plan(plan):
+        plan.run()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for s, e in ev:
+            flush.zero_()
+            s.record()
+            plan.run()
+            e.record()
+        torch.cuda.synchronize()
+        return float(np.median([s.elapsed_time(e) for s, e in ev]))
+
+    timings, best, best_plan = {}, None, None
+    for c in cands:
+        plan = BatchPlan(items, which=which, threads_per_cta=c["threads_per_cta"], item_shapes=c["item_shapes"])
+        name = "%d threads, %d rounds per tile" % (c["threads_per_cta"], c["rounds"])
+        timings[name] = time_plan(plan)
+        if best is None or timings[name] < timings[best]:
+            if best_plan is not None:
+                best_plan.close()
+            best, best_plan = name, plan
+        else:
+            plan.close()
+    choice = next(c for c in cands if "%d threads, %d rounds per tile" % (c["threads_per_cta"], c["rounds"]) == best)
+    spec_ms = None
+    use_spec = bool(hit[2]) if hit and len(hit) > 2 else None
+    if specialise and use_spec is not False:
+        best_plan.specialize()
+        spec_ms = time_plan(best_plan)
+        if use_spec is None:
+            use_spec = spec_ms < timings[best]
+        if not use_spec:
+            best_plan.specialize(False)
+    del flush
+    if use_cache:
+        with _lock:
+            cache = _load_cache()
+            cache[key] = [choice["threads_per_cta"], choice["rounds"], bool(use_spec)]
+            _store_cache(cache)
+    return best_plan, {"choice": best, "ms": spec_ms if use_spec else timings[best], "timings": timings,
+                       "specialised_ms": spec_ms, "item_shapes": choice["item_shapes"],
+                       "specialised": best_plan.spec_info()}

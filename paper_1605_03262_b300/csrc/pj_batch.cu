@@ -16,16 +16,6 @@
 #include "../../include/pyjac_b300.h"
 #include "pj_internal.h"
 
-struct pj_batch {
-    int which = 0;                 // 0 Jacobian, 1 source terms
-    int device = 0;
-    int threads = 0, ctas_per_sm = 1, sms = 0;
-    size_t smem = 0;
-    int ntiles = 0;
-    void *dev = nullptr;           // items | tiles | counter
-    pj::BatchParams params{};
-};
-
 namespace {
 
 int bfail(int code, const std::string &msg) { return pj::set_error(code, msg); }
@@ -54,6 +44,11 @@ int check_dev(const void *p, int dev, const char *name) {
 extern "C" {
 
 int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj_batch_shape *shape, pj_batch **out) {
+    return pj_batch_create_ex(items, n_items, which, shape, nullptr, out);
+}
+
+int pj_batch_create_ex(const pj_batch_item *items, int n_items, int which, const pj_batch_shape *shape,
+                       const pj_batch_item_shape *item_shapes, pj_batch **out) {
     if (!items || n_items < 1 || !out || (which != 0 && which != 1))
         return bfail(PJ_EINVAL, "pj_batch_create: bad argument");
     *out = nullptr;
@@ -94,9 +89,29 @@ int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj
         }
         int wps = 0, groups = 0;
         pj::Scratch sc{};
-        if (!pj::batch_group_shape(*m, jac, threads, budget, &wps, &groups, &sc))
+        const pj_batch_item_shape *is = item_shapes ? &item_shapes[i] : nullptr;
+        if (is && (is->warps_per_state < 0 || is->states_per_cta < 0 || is->tile_states < 0))
+            return bfail(PJ_EINVAL, "pj_batch_create: item " + std::to_string(i) + ": negative shape entry");
+        if (is && is->warps_per_state > 0) {
+            // the caller's group width and (optionally) states per CTA, checked against the CTA
+            wps = is->warps_per_state;
+            if (!(wps == 1 || wps == 2 || wps == 4 || wps == 8 || wps == 16) || wps * 32 > threads)
+                return bfail(PJ_EINVAL, "pj_batch_create: item " + std::to_string(i) + ": warps per state");
+            sc = pj::make_scratch(m->dev, jac, wps);
+            const int sconst = pj::shared_const_doubles(m->N);
+            int gmax = threads / (32 * wps);
+            if (wps > 1) gmax = std::min(gmax, 15);
+            while (gmax > 0 && (size_t(sconst) + size_t(sc.total) * gmax) * 8 > budget) --gmax;
+            groups = is->states_per_cta > 0 ? std::min(is->states_per_cta, gmax) : gmax;
+            if (groups < 1)
+                return bfail(PJ_EUNSUPPORTED, "pj_batch_create: item " + std::to_string(i) +
+                                                  ": one state's working set does not fit in shared memory");
+        } else if (!pj::batch_group_shape(*m, jac, threads, budget, &wps, &groups, &sc)) {
             return bfail(PJ_EUNSUPPORTED, "pj_batch_create: item " + std::to_string(i) +
                                               ": one state's working set does not fit in shared memory");
+        } else if (is && is->states_per_cta > 0) {
+            groups = std::min(groups, is->states_per_cta);
+        }
         const int sconst = pj::shared_const_doubles(m->N);
         smem = std::max(smem, (size_t(sconst) + size_t(sc.total) * groups) * 8);
         pj::BatchItem &b = bi[i];
@@ -111,7 +126,8 @@ int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj
     // tiles: consecutive states of one item, costliest first
     std::vector<pj::BatchTile> tiles;
     for (int i = 0; i < n_items; ++i) {
-        const long long ts = tile_req > 0 ? tile_req : 4LL * bi[i].groups;
+        const long long ts = (item_shapes && item_shapes[i].tile_states > 0) ? item_shapes[i].tile_states
+                             : tile_req > 0 ? tile_req : 4LL * bi[i].groups;
         for (long long b = 0; b < items[i].n; b += ts) {
             pj::BatchTile t{};
             t.item = i;
@@ -125,6 +141,18 @@ int pj_batch_create(const pj_batch_item *items, int n_items, int which, const pj
     });
     pj_batch *bt = new (std::nothrow) pj_batch();
     if (!bt) return bfail(PJ_ENOMEM, "host allocation failed");
+    for (int i = 0; i < n_items; ++i) {               // slot of each item: its (model, group width)
+        int slot = -1;
+        for (size_t k = 0; k < bt->slot_mech.size(); ++k)
+            if (bt->slot_mech[k] == items[i].mech && bt->slot_wps[k] == bi[i].wps) slot = int(k);
+        if (slot < 0) {
+            slot = int(bt->slot_mech.size());
+            bt->slot_mech.push_back(items[i].mech);
+            bt->slot_wps.push_back(bi[i].wps);
+        }
+        bi[i].pad = slot;
+    }
+    bt->items = bi;
     bt->which = which;
     bt->device = dev;
     bt->threads = threads;
@@ -168,8 +196,14 @@ int pj_batch_run(pj_batch *b, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((e = cudaMemsetAsync(b->params.counter, 0, sizeof(int), st)) != cudaSuccess) return bcuda(e, "counter reset");
     const int blocks = std::max(1, std::min(b->sms * b->ctas_per_sm, b->ntiles));
-    if ((e = pj::launch_batch(b->params, b->which == 0, blocks, b->threads, b->smem, st)) != cudaSuccess)
-        return bcuda(e, "batch kernel launch");
+    if (b->spec) {                                    // the kernel specialised for this plan
+        const void *k = reinterpret_cast<const void *>(b->spec->kern);
+        void *args[] = {&b->params};
+        e = cudaLaunchKernel(k, dim3(blocks), dim3(b->threads), args, b->smem, st);
+    } else {
+        e = pj::launch_batch(b->params, b->which == 0, blocks, b->threads, b->smem, st);
+    }
+    if (e != cudaSuccess) return bcuda(e, "batch kernel launch");
     return PJ_OK;
 }
 
@@ -181,8 +215,39 @@ int pj_batch_info(const pj_batch *b, int *n_tiles, size_t *smem_bytes, int *thre
     return PJ_OK;
 }
 
+int pj_batch_specialize(pj_batch *b, int enable) {
+    if (!b) return bfail(PJ_EINVAL, "pj_batch_specialize: null plan");
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
+    if (cur != b->device) return bfail(PJ_EINVAL, "pj_batch_specialize: the current device is not the plan's device");
+    if (!enable) {
+        pj::batch_spec_release(b);
+        return PJ_OK;
+    }
+    std::string err;
+    const int rc = pj::specialize_batch(b, &err);
+    if (rc != PJ_OK) return bfail(rc, "pj_batch_specialize: " + err);
+    if (b->spec && (e = cudaFuncSetAttribute(reinterpret_cast<const void *>(b->spec->kern),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem))) != cudaSuccess) {
+        pj::batch_spec_release(b);
+        return bcuda(e, "specialised batch kernel attribute");
+    }
+    return PJ_OK;
+}
+
+int pj_batch_spec_info(const pj_batch *b, int *active, int *slots, double *compile_seconds, size_t *cubin_bytes) {
+    if (!b) return bfail(PJ_EINVAL, "pj_batch_spec_info: null plan");
+    if (active) *active = b->spec != nullptr;
+    if (slots) *slots = int(b->slot_mech.size());
+    if (compile_seconds) *compile_seconds = b->spec ? b->spec->compile_seconds : 0.0;
+    if (cubin_bytes) *cubin_bytes = b->spec ? b->spec->cubin_bytes : 0;
+    return PJ_OK;
+}
+
 void pj_batch_free(pj_batch *b) {
     if (!b) return;
+    pj::batch_spec_release(b);
     if (b->dev) cudaFree(b->dev);
     delete b;
 }

@@ -97,6 +97,33 @@ struct pj_mech {
     std::vector<int> cc_ptr, cc_col;   // molar-concentration basis: species-row pattern (host copy)
 };
 
+// Kernel of a batched plan specialised for its models (pj_nvrtc.cu): each distinct (model, warps
+// per state) pair of the plan is a slot whose sizes, offsets and group width are compile-time
+// constants; the kernel dispatches on the slot of a tile's item (BatchItem::pad).
+struct pj_batch_spec {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    double compile_seconds = 0.0;
+    size_t cubin_bytes = 0;
+    int slots = 0;
+};
+
+// A batched plan (pj_batch.cu): launch shape, device copies of the item table and tiles, and the
+// host copies the specialisation needs.
+struct pj_batch {
+    int which = 0;                 // 0 Jacobian, 1 source terms
+    int device = 0;
+    int threads = 0, ctas_per_sm = 1, sms = 0;
+    size_t smem = 0;
+    int ntiles = 0;
+    void *dev = nullptr;           // items | tiles | counter
+    pj::BatchParams params{};
+    std::vector<pj::BatchItem> items;        // host copy; pad = the item's slot
+    std::vector<const pj_mech *> slot_mech;  // per slot: its model
+    std::vector<int> slot_wps;               // per slot: warps per state
+    pj_batch_spec *spec = nullptr;
+};
+
 namespace pj {
 // Group width, states per CTA and scratch of one model in a batched launch of `threads` threads
 // and `budget` bytes of dynamic shared memory per CTA: the model's configured width, halved while
@@ -111,6 +138,8 @@ namespace pj {
 // release them; the kernel for (jac, cv) if one was compiled for launch shape c, else null.
 int specialize(pj_mech *m, std::string *err);
 void spec_release(pj_mech *m);
+int specialize_batch(pj_batch *b, std::string *err);
+void batch_spec_release(pj_batch *b);
 const void *spec_kernel(const pj_mech *m, bool jac, bool cv, const LaunchCfg &c);
 const void *spec_conc_kernel(const pj_mech *m, const LaunchCfg &c);
 constexpr int kSpecKernels = 5;

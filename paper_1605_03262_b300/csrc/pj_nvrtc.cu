@@ -11,6 +11,7 @@
 #include <dlfcn.h>
 
 #include <chrono>
+#include <map>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -119,10 +120,14 @@ std::string spec_source(const pj_mech &m, const LaunchCfg &cj, const LaunchCfg &
     return s;
 }
 
-}  // namespace
 
-// Compiles and loads the specialised kernels of a model for its current launch shapes.
-int specialize(pj_mech *m, std::string *err) {
+int nvrtc_compile(const NvrtcApi &api, const std::string &src, const char *name, const std::string &arch,
+                  std::vector<char> *out, std::string *err);
+
+// Compiles source (with the embedded device headers) for the current device's sm_XXa with NVRTC and
+// loads it as a library. PJ_OK, or a status with the reason (the compiler log) in *err.
+int compile_and_load(const std::string &src, const char *name, cudaLibrary_t *lib, size_t *cubin_bytes,
+                     double *seconds, std::string *err) {
     const NvrtcApi &api = nvrtc_api();
     if (!api.ok) {
         *err = api.why;
@@ -135,20 +140,48 @@ int specialize(pj_mech *m, std::string *err) {
         *err = "no CUDA device";
         return PJ_ECUDA;
     }
-    if (m->jac_cfg.groups < 1 || m->dydt_cfg.groups < 1) {
-        *err = "the model's working set does not fit in shared memory";
-        return PJ_EUNSUPPORTED;
-    }
+    const std::string arch = "-arch=sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a";
     const auto t0 = std::chrono::steady_clock::now();
-    const std::string src = spec_source(*m, m->jac_cfg, m->dydt_cfg);
+    // compiled code of this process, by target and source: a plan or model specialised again for
+    // the same source (another plan over the same models and widths) loads it without compiling
+    static std::mutex cache_mu;
+    static std::map<std::string, std::vector<char>> cache;
+    const std::string key = arch + '\n' + src;
+    std::vector<char> bin;
+    {
+        std::lock_guard<std::mutex> lk(cache_mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) bin = it->second;
+    }
+    if (bin.empty()) {
+        const int rc = nvrtc_compile(api, src, name, arch, &bin, err);
+        if (rc != PJ_OK) return rc;
+        std::lock_guard<std::mutex> lk(cache_mu);
+        if (cache.size() >= 64) cache.clear();    // bounded: a long-running process keeps at most 64
+        cache[key] = bin;
+    }
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *cubin_bytes = bin.size();
+    cudaError_t e = cudaLibraryLoadData(lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *lib = nullptr;
+        *err = std::string("loading the specialised kernels failed: ") + cudaGetErrorString(e);
+        return PJ_ECUDA;
+    }
+    return PJ_OK;
+}
+
+// One NVRTC compilation of src for arch into a cubin.
+int nvrtc_compile(const NvrtcApi &api, const std::string &src, const char *name, const std::string &arch,
+                  std::vector<char> *out, std::string *err) {
     const char *hdr_src[3] = {kSrcFastmath, kSrcDevice, kSrcDeviceKernels};
     const char *hdr_name[3] = {"pj_fastmath.cuh", "pj_device.h", "pj_device_kernels.cuh"};
     nvrtcProgram prog = nullptr;
-    if (api.create(&prog, src.c_str(), "pj_spec.cu", 3, hdr_src, hdr_name) != NVRTC_SUCCESS) {
+    if (api.create(&prog, src.c_str(), name, 3, hdr_src, hdr_name) != NVRTC_SUCCESS) {
         *err = "nvrtcCreateProgram failed";
         return PJ_ECUDA;
     }
-    const std::string arch = "-arch=sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a";
     const char *opts[] = {arch.c_str(), "-std=c++17", "-default-device"};
     const nvrtcResult rc = api.compile(prog, 3, opts);
     if (rc != NVRTC_SUCCESS) {
@@ -162,29 +195,118 @@ int specialize(pj_mech *m, std::string *err) {
     }
     size_t nbin = 0;
     api.cubin_size(prog, &nbin);
-    std::vector<char> bin(nbin);
-    api.cubin(prog, bin.data());
+    out->assign(nbin, 0);
+    api.cubin(prog, out->data());
     api.destroy(&prog);
-    const double seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return PJ_OK;
+}
 
+// Source of a batched plan's specialised kernel: per slot a Spec type with the model's sizes and
+// scratch layout, a function that evaluates a tile of that slot with the slot's group width, and
+// a switch over the slots in the persistent loop. With several slots each slot's function is a
+// separate (non-inlined) function, so that the register allocation of one branch does not weigh
+// on the others.
+std::string batch_spec_source(const pj_batch &b) {
+    const bool jac = b.which == 0;
+    const char *J = jac ? "true" : "false";
+    const int ns = int(b.slot_mech.size());
+    std::string s = "#include \"pj_device_kernels.cuh\"\nnamespace {\n";
+    for (int k = 0; k < ns; ++k) {
+        const pj_mech &m = *b.slot_mech[k];
+        const std::string sk = std::to_string(k);
+        std::string body;
+        emit_model(body, m.dev);
+        emit_scratch(body, "spec_scratch", make_scratch(m.dev, jac, b.slot_wps[k]));
+        // emit_model / emit_scratch write free functions; wrap them as static members of Slot<k>
+        std::string wrapped;
+        size_t pos = 0;
+        while (pos < body.size()) {
+            size_t e = body.find('\n', pos);
+            std::string line = body.substr(pos, e - pos);
+            const std::string pre = "__device__ __forceinline__ void ";
+            if (line.compare(0, pre.size(), pre) == 0) line = "    static " + line;
+            wrapped += line + "\n";
+            pos = e + 1;
+        }
+        s += "struct Slot" + sk + " {\n" + wrapped + "};\n";
+        s += std::string("__device__ ") + (ns > 1 ? "__noinline__" : "__forceinline__") + " void run_slot" + sk +
+             "(const pj::BatchItem *it, long long b, long long e, bool f) {\n"
+             "    pj::run_tile_spec<" + J + ", " + std::to_string(b.slot_wps[k]) + ", Slot" + sk + ">(it, b, e, f);\n}\n";
+    }
+    s += "}  // namespace\n";
+    s += "extern \"C\" __global__ void __launch_bounds__(512, 1) pj_spec_batch(const __grid_constant__ pj::BatchParams p) {\n"
+         "    pj::batch_spec_body(p, [](int slot, const pj::BatchItem *it, long long b, long long e, bool f) {\n"
+         "        switch (slot) {\n";
+    for (int k = 0; k < ns; ++k)
+        s += "        case " + std::to_string(k) + ": run_slot" + std::to_string(k) + "(it, b, e, f); break;\n";
+    s += "        default: break;\n        }\n    });\n}\n";
+    return s;
+}
+
+}  // namespace
+
+// Compiles and loads the specialised kernels of a model for its current launch shapes.
+int specialize(pj_mech *m, std::string *err) {
+    if (m->jac_cfg.groups < 1 || m->dydt_cfg.groups < 1) {
+        *err = "the model's working set does not fit in shared memory";
+        return PJ_EUNSUPPORTED;
+    }
+    const std::string src = spec_source(*m, m->jac_cfg, m->dydt_cfg);
     pj_spec *sp = new pj_spec();
-    cudaError_t e = cudaLibraryLoadData(&sp->lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-    for (int k = 0; k < kSpecKernels && e == cudaSuccess; ++k)
+    int rc = compile_and_load(src, "pj_spec.cu", &sp->lib, &sp->cubin_bytes, &sp->compile_seconds, err);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kSpecKernels && rc == PJ_OK && e == cudaSuccess; ++k)
         e = cudaLibraryGetKernel(&sp->kern[k], sp->lib, kSpecNames[k]);
-    if (e != cudaSuccess) {
+    if (rc == PJ_OK && e != cudaSuccess) {
         cudaGetLastError();
+        *err = std::string("loading the specialised kernels failed: ") + cudaGetErrorString(e);
+        rc = PJ_ECUDA;
+    }
+    if (rc != PJ_OK) {
         if (sp->lib) cudaLibraryUnload(sp->lib);
         delete sp;
-        *err = std::string("loading the specialised kernels failed: ") + cudaGetErrorString(e);
-        return PJ_ECUDA;
+        return rc;
     }
     sp->jac_cfg = m->jac_cfg;
     sp->dydt_cfg = m->dydt_cfg;
-    sp->compile_seconds = seconds;
-    sp->cubin_bytes = nbin;
     spec_release(m);
     m->spec = sp;
     return PJ_OK;
+}
+
+// Compiles and loads the kernel of a batched plan specialised for its slots.
+int specialize_batch(pj_batch *b, std::string *err) {
+    if (b->slot_mech.empty()) {
+        *err = "the plan has no items";
+        return PJ_EINVAL;
+    }
+    const std::string src = batch_spec_source(*b);
+    pj_batch_spec *sp = new pj_batch_spec();
+    int rc = compile_and_load(src, "pj_spec_batch.cu", &sp->lib, &sp->cubin_bytes, &sp->compile_seconds, err);
+    if (rc == PJ_OK) {
+        const cudaError_t e = cudaLibraryGetKernel(&sp->kern, sp->lib, "pj_spec_batch");
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *err = std::string("loading the specialised batch kernel failed: ") + cudaGetErrorString(e);
+            rc = PJ_ECUDA;
+        }
+    }
+    if (rc != PJ_OK) {
+        if (sp->lib) cudaLibraryUnload(sp->lib);
+        delete sp;
+        return rc;
+    }
+    sp->slots = int(b->slot_mech.size());
+    batch_spec_release(b);
+    b->spec = sp;
+    return PJ_OK;
+}
+
+void batch_spec_release(pj_batch *b) {
+    if (!b->spec) return;
+    if (b->spec->lib) cudaLibraryUnload(b->spec->lib);
+    delete b->spec;
+    b->spec = nullptr;
 }
 
 void spec_release(pj_mech *m) {

@@ -86,3 +86,61 @@ def test_batch_argument_errors():
     with pytest.raises(pj.LibraryError):
         pj.BatchPlan([(g, T, P, Y, torch.empty((T.shape[0], g.n_species + 1, g.n_species + 1),
                                                 dtype=torch.float64, device="cuda"))], threads_per_cta=100)
+
+
+def _jac_items(items):
+    outs = []
+    for g, T, P, Y in items:
+        N = g.n_species
+        outs.append((torch.full((T.shape[0], N + 1, N + 1), float("nan"), dtype=torch.float64, device="cuda"),
+                     torch.full((T.shape[0], N + 1), float("nan"), dtype=torch.float64, device="cuda")))
+    return outs
+
+
+@pytest.mark.parametrize("which", ["jacobian", "dydt"])
+def test_specialised_batch_kernel_equals_plain_launches(which):
+    """The plan's kernel compiled for its models (NVRTC; one branch per (model, group width)) gives
+    the plain per-model results bit for bit, with per-item shapes, also from a graph."""
+    import paper_1605_03262_b300 as pj
+    items = _items(seed=11)
+    g0 = items[0][0]                                    # the first model again, at another width
+    items.append((g0, *_dev(*synth.generate_states(g0.n_species, 200, seed=99))))
+    outs = _jac_items(items)
+    if which == "jacobian":
+        plan_items = [(g, T, P, Y, J, f) for (g, T, P, Y), (J, f) in zip(items, outs)]
+    else:
+        plan_items = [(g, T, P, Y, f) for (g, T, P, Y), (J, f) in zip(items, outs)]
+    # the first and last items share a model at different widths: two branches for it
+    shapes = [(1, 8, 24), (2, 0, 0), (0, 3, 0), (0, 0, 5), (4, 2, 7), (2, 0, 9)]
+    plan = pj.BatchPlan(plan_items, which=which, item_shapes=shapes)
+    info = plan.specialize()
+    assert info["active"] and info["slots"] == len(items) and info["cubin_bytes"] > 0
+    graph = plan.capture()
+    graph.replay()
+    torch.cuda.synchronize()
+    for (g, T, P, Y), (J, f) in zip(items, outs):
+        if which == "jacobian":
+            ref, fref = g.eval_jacobian(T, P, Y, dydt=True)
+            assert torch.equal(J, ref)
+            assert torch.equal(f, fref)
+        else:
+            assert torch.equal(f, g.eval_dydt(T, P, Y))
+    assert not plan.specialize(False)["active"]
+
+
+def test_batch_autotuner_picks_a_timed_candidate_and_keeps_results():
+    import paper_1605_03262_b300 as pj
+    from paper_1605_03262_b300 import autotune
+    items = _items(seed=13)[:3]
+    outs = _jac_items(items)
+    plan_items = [(g, T, P, Y, J) for (g, T, P, Y), (J, f) in zip(items, outs)]
+    plan, rep = autotune.autotune_batch(plan_items, use_cache=False)
+    assert rep["choice"] in rep["timings"] and rep["specialised_ms"] is not None
+    assert rep["specialised"]["active"] == (rep["specialised_ms"] < rep["timings"][rep["choice"]])
+    assert len(rep["timings"]) == len(autotune.batch_candidates(plan_items))
+    for J, _ in outs:
+        J.fill_(float("nan"))
+    plan.run()
+    torch.cuda.synchronize()
+    for (g, T, P, Y), (J, f) in zip(items, outs):
+        assert torch.equal(J, g.eval_jacobian(T, P, Y))
