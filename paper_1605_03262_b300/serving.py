@@ -17,6 +17,14 @@ future. A scheduler thread runs iterations continuously:
   otherwise it waits in the queue (no out-of-memory, no rejection). Iterations run on a pool of
   streams, so requests admitted while others are on the GPU overlap with them.
 
+A request whose estimated GPU time exceeds ``chunk_ms`` is cut into chunks of about that time
+(consecutive states; the per-state time of each model is measured when the server starts). The
+server admits one chunk of such a request at a time, each launch writing its slice of the
+request's output, and sends the request to the back of the queue after each chunk, so a small
+request that arrives behind a large one waits for at most one chunk instead of the whole request.
+The request completes when its last chunk has. States are evaluated independently, so a chunked
+result is bitwise the unchunked one.
+
 Model images stay resident for the server's lifetime. Each request's latency is measured from
 :meth:`submit` to the completion event of its iteration (results in device memory), and, with
 ``host_results=True``, to the end of the copy to host memory. The evaluation itself is the
@@ -36,7 +44,8 @@ __all__ = ["Server", "Request"]
 
 
 class Request:
-    __slots__ = ("rid", "name", "T", "P", "Y", "n", "t_submit", "t_done", "future", "dydt")
+    __slots__ = ("rid", "name", "T", "P", "Y", "n", "t_submit", "t_done", "future", "dydt", "chunks", "next",
+                 "left", "dev", "out", "host", "bytes", "ready")
 
     def __init__(self, rid, name, T, P, Y, dydt):
         self.rid, self.name, self.T, self.P, self.Y = rid, name, T, P, Y
@@ -45,13 +54,19 @@ class Request:
         self.t_done = None
         self.future: concurrent.futures.Future = concurrent.futures.Future()
         self.dydt = dydt
+        self.chunks = None        # state ranges of a chunked request, else None
+        self.next = 0             # next chunk to admit
+        self.left = 0             # chunks not yet completed
+        self.dev = self.out = self.host = None   # device inputs, device outputs, host outputs
+        self.bytes = 0
+        self.ready = None         # event: the request's inputs are on the device (chunked requests)
 
 
 class _Iteration:
-    __slots__ = ("reqs", "model", "stream", "event", "bytes", "J", "F", "offsets", "host", "results")
+    __slots__ = ("reqs", "model", "stream", "event", "bytes", "J", "F", "offsets", "host", "results", "chunk")
 
     def __init__(self):
-        self.reqs, self.offsets, self.host, self.results = [], [], None, None
+        self.reqs, self.offsets, self.host, self.results, self.chunk = [], [], None, None, False
 
 
 class Server:
@@ -67,7 +82,7 @@ class Server:
 
     def __init__(self, models: Dict[str, object], hbm_budget: Optional[int] = None, max_inflight: int = 6,
                  max_batch_states: int = 65536, host_results: bool = False, discard_results: bool = False,
-                 mixed: bool = False):
+                 mixed: bool = False, chunk_ms: Optional[float] = 1.0):
         import torch
         self.torch = torch
         self.models = dict(models)
@@ -95,8 +110,11 @@ class Server:
         self.error: Optional[BaseException] = None
         self._thread: Optional[threading.Thread] = None
         self._next_id = 0
+        self.chunk_ms = chunk_ms if (chunk_ms and not self.mixed) else None
+        self.state_ms: Dict[str, float] = {}      # measured GPU time per state, per model
+        self._stage = {}                          # per stream: pinned host staging (discarded host results)
         self.stats = {"iterations": 0, "requests": 0, "states": 0, "max_inflight_seen": 0, "waits_for_memory": 0,
-                      "merged_requests": 0}
+                      "merged_requests": 0, "chunked_requests": 0, "chunks": 0}
 
     # -- client side ---------------------------------------------------------------------------
     def submit(self, name: str, T, P, Y, dydt: bool = False) -> concurrent.futures.Future:
@@ -113,12 +131,46 @@ class Server:
         with self._cv:
             req = Request(self._next_id, name, T, P, Y, dydt)
             req.future.request = req          # lets clients read the request's timings
+            cs = self._chunk_states(name)
+            if cs and req.n > cs:
+                k = -(-req.n // cs)
+                edges = [req.n * x // k for x in range(k + 1)]
+                req.chunks = list(zip(edges[:-1], edges[1:]))
+                req.left = k
             self._next_id += 1
             self._queue.append(req)
             self._cv.notify()
         return req.future
 
+    def _chunk_states(self, name: str) -> int:
+        """States per chunk of a request to this model (0: requests are not cut)."""
+        if not self.chunk_ms or name not in self.state_ms:
+            return 0
+        return max(1, int(self.chunk_ms / self.state_ms[name]))
+
+    def calibrate(self, n_states: int = 2048) -> Dict[str, float]:
+        """Measure each model's GPU time per state (a warm launch of a synthetic batch that fills
+        the GPU), which sets the chunk sizes."""
+        torch = self.torch
+        from . import synth
+        for name, m in self.models.items():
+            N = m.n_species
+            T, P, Y = (torch.as_tensor(a, dtype=torch.float64, device=self.device)
+                       for a in synth.generate_states(N, n_states, seed=4242))
+            J = torch.empty((n_states, N + 1, N + 1), dtype=torch.float64, device=self.device)
+            m.eval_jacobian(T, P, Y, out=J)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            m.eval_jacobian(T, P, Y, out=J)
+            e1.record()
+            torch.cuda.synchronize()
+            self.state_ms[name] = e0.elapsed_time(e1) / n_states
+            del J, T, P, Y
+        return dict(self.state_ms)
+
     def start(self) -> "Server":
+        if self.chunk_ms and not self.state_ms:
+            self.calibrate()
         if self._thread is None:
             self._stop = False
             self._thread = threading.Thread(target=self._loop, name="pyjac-b300-server", daemon=True)
@@ -183,6 +235,22 @@ class Server:
         for it in done:
             self._inflight.remove(it)
             t = time.perf_counter()
+            if it.chunk:                          # one chunk of a request: complete it after its last
+                r = it.reqs[0]
+                r.left -= 1
+                if r.left == 0:
+                    r.t_done = t
+                    if self.discard_results:
+                        r.future.set_result(None)
+                    else:
+                        J, F = r.host if self.host_results else r.out
+                        if self.host_results:
+                            J, F = J.numpy(), F.numpy() if F is not None else None
+                        r.future.set_result((J, F) if r.dydt else J)
+                    r.dev = r.out = r.host = r.ready = None
+                    self._held -= r.bytes
+                self._free_streams.append(it.stream)
+                continue
             for x, r in enumerate(it.reqs):
                 r.t_done = t
                 if self.discard_results:
@@ -269,6 +337,67 @@ class Server:
             self.stats["max_inflight_seen"] = max(self.stats["max_inflight_seen"], len(self._inflight))
             admitted = True
 
+    def _host_buffer(self, stream, shape):
+        """Pinned host memory for a copy of the given shape: a fresh buffer handed to the client, or,
+        when results are discarded, the stream's reused staging buffer."""
+        torch = self.torch
+        count = int(np.prod(shape))
+        if not self.discard_results:
+            return torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        buf = self._stage.get(id(stream))
+        if buf is None or buf.numel() < count:
+            buf = torch.empty(max(count, 1), dtype=torch.float64, pin_memory=True)
+            self._stage[id(stream)] = buf
+        return buf[:count].view(shape)
+
+    def _admit_chunk(self, r: Request, model) -> None:
+        """One chunk of a chunked request on a free stream, into its slice of the request's output
+        (inputs and outputs of the whole request are allocated at its first chunk)."""
+        torch = self.torch
+        a, b = r.chunks[r.next]
+        it = _Iteration()
+        it.reqs, it.model, it.bytes, it.chunk = [r], model, 0, True
+        it.stream = self._free_streams.pop()
+        N = model.n_species
+        with torch.cuda.stream(it.stream):
+            if r.next == 0:
+                r.bytes = self._bytes(model, r.n)
+                self._held += r.bytes
+                r.dev = tuple(torch.as_tensor(x, dtype=torch.float64).to(self.device, non_blocking=True)
+                              for x in (r.T, r.P, r.Y))
+                J = torch.empty((r.n, N + 1, N + 1), dtype=torch.float64, device=self.device)
+                F = torch.empty((r.n, N + 1), dtype=torch.float64, device=self.device) if r.dydt else None
+                r.out = (J, F)
+                if self.host_results and not self.discard_results:
+                    r.host = (torch.empty((r.n, N + 1, N + 1), dtype=torch.float64, pin_memory=True),
+                              torch.empty((r.n, N + 1), dtype=torch.float64, pin_memory=True) if r.dydt else None)
+                r.ready = torch.cuda.Event()
+                r.ready.record(it.stream)                  # the inputs are on the device
+                self.stats["chunked_requests"] += 1
+            else:
+                it.stream.wait_event(r.ready)             # later chunks run on other streams
+            T, P, Y = r.dev
+            J, F = r.out
+            model.eval_jacobian(T[a:b], P[a:b], Y[a:b], out=J[a:b], dydt_out=F[a:b] if F is not None else None,
+                                stream=it.stream)
+            if self.host_results:
+                if self.discard_results:                  # the copy counts, its result is dropped
+                    self._host_buffer(it.stream, (b - a, N + 1, N + 1)).copy_(J[a:b], non_blocking=True)
+                else:
+                    r.host[0][a:b].copy_(J[a:b], non_blocking=True)
+                    if F is not None:
+                        r.host[1][a:b].copy_(F[a:b], non_blocking=True)
+            it.event = torch.cuda.Event()
+            it.event.record(it.stream)
+        r.next += 1
+        self._inflight.append(it)
+        self.stats["iterations"] += 1
+        self.stats["chunks"] += 1
+        if r.next == 1:
+            self.stats["requests"] += 1
+            self.stats["states"] += r.n
+        self.stats["max_inflight_seen"] = max(self.stats["max_inflight_seen"], len(self._inflight))
+
     def _admit_merged(self) -> bool:
         torch = self.torch
         admitted = False
@@ -278,10 +407,22 @@ class Server:
                     return admitted
                 head = self._queue[0]
                 model = self.models[head.name]
+                if head.chunks is not None:
+                    if head.next == 0 and self._held + self._bytes(model, head.n) > self.hbm_budget:
+                        self.stats["waits_for_memory"] += 1
+                        return admitted
+                    self._queue.popleft()
+                    if head.next + 1 < len(head.chunks):
+                        self._queue.append(head)          # its next chunk after the others queued now
+            if head.chunks is not None:
+                self._admit_chunk(head, model)
+                admitted = True
+                continue
+            with self._cv:
                 # merge queued requests of the head's model, in arrival order, up to the state cap
                 take, n = [], 0
                 for r in self._queue:
-                    if r.name != head.name:
+                    if r.name != head.name or r.chunks is not None:
                         continue
                     if take and n + r.n > self.max_batch_states:
                         break
@@ -319,10 +460,10 @@ class Server:
                 it.F = torch.empty((n, N + 1), dtype=torch.float64, device=self.device) if want_f else None
                 model.eval_jacobian(T, P, Y, out=it.J, dydt_out=it.F, stream=it.stream)
                 if self.host_results:
-                    Jh = torch.empty(it.J.shape, dtype=torch.float64, pin_memory=True)
+                    Jh = self._host_buffer(it.stream, tuple(it.J.shape))
                     Jh.copy_(it.J, non_blocking=True)
                     Fh = None
-                    if it.F is not None:
+                    if it.F is not None and not self.discard_results:
                         Fh = torch.empty(it.F.shape, dtype=torch.float64, pin_memory=True)
                         Fh.copy_(it.F, non_blocking=True)
                     it.host = (Jh.numpy(), Fh.numpy() if Fh is not None else None)

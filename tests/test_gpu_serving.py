@@ -35,12 +35,14 @@ def test_results_alone_equal_results_in_the_mix():
     probe = trace[17]
     with Server(models, max_inflight=1) as srv:
         alone = srv.submit(*probe).result(timeout=60).cpu()
-    with Server(models, max_inflight=4) as srv:
+    # the mix with request chunking on (chunks of about 20 us of GPU time: every request of more
+    # than a few states of the larger models is cut)
+    with Server(models, max_inflight=4, chunk_ms=0.02) as srv:
         futs = [srv.submit(*r) for r in trace]
         results = [f.result(timeout=120) for f in futs]
         stats = dict(srv.stats)
     assert torch.equal(results[17].cpu(), alone)
-    assert stats["requests"] == len(trace)
+    assert stats["requests"] == len(trace) and stats["chunked_requests"] > 0
     # plain per-request evaluation agrees too
     for (name, T, P, Y), res in zip(trace[:6], results[:6]):
         ref = models[name].eval_jacobian(T, P, Y)
@@ -134,3 +136,31 @@ def test_run_batch_with_workspaces_equals_plain_launches():
         assert torch.equal(it[4], ref)
     with pytest.raises(pj.LibraryError):
         pj.run_batch(items, workspace=ws[0][:16])      # too small
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_chunked_request_equals_unchunked_result(host):
+    """A large request cut into chunks (each launch writing its slice of the output, chunks on
+    several streams, small requests admitted between them) returns the plain launch's bits, with
+    the source terms beside the Jacobian, on the device or copied to host memory."""
+    from paper_1605_03262_b300.serving import Server
+    models = _models()
+    big = synth.CONFIGS[1]["name"]
+    N = models[big].n_species
+    T, P, Y = synth.generate_states(N, 3000, seed=61)
+    small = _trace(models, 8, seed=62)
+    with Server(models, max_inflight=4, chunk_ms=0.05, host_results=host) as srv:
+        f_big = srv.submit(big, T, P, Y, dydt=True)
+        f_small = [srv.submit(*r) for r in small]
+        J, F = f_big.result(timeout=120)
+        rest = [f.result(timeout=120) for f in f_small]
+        stats = dict(srv.stats)
+    assert stats["chunked_requests"] >= 1 and stats["chunks"] > 2
+    Jr, Fr = models[big].eval_jacobian(*(torch.as_tensor(a, device="cuda") for a in (T, P, Y)), dydt=True)
+    J, F = torch.as_tensor(J).cuda(), torch.as_tensor(F).cuda()
+    assert torch.equal(J, Jr) and torch.equal(F, Fr)
+    for (name, Ts, Ps, Ys), res in zip(small, rest):
+        ref = models[name].eval_jacobian(*(torch.as_tensor(a, device="cuda") for a in (Ts, Ps, Ys)))
+        assert torch.equal(torch.as_tensor(res).cuda(), ref)
+    # the big request did not hold the small ones back until its end: some finished before it
+    assert min(f.request.t_done for f in f_small) <= f_big.request.t_done
