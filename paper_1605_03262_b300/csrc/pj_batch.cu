@@ -201,6 +201,10 @@ int pj_batch_run(pj_batch *b, void *stream) {
         void *args[] = {&b->params};
         e = cudaLaunchKernel(k, dim3(blocks), dim3(b->threads), args, b->smem, st);
     } else {
+        // the kernel's dynamic shared memory limit is one per process: another plan may have set
+        // a smaller one since this plan was built
+        if ((e = pj::prepare_batch_kernel(b->which == 0, b->smem, nullptr)) != cudaSuccess)
+            return bcuda(e, "batch kernel attribute");
         e = pj::launch_batch(b->params, b->which == 0, blocks, b->threads, b->smem, st);
     }
     if (e != cudaSuccess) return bcuda(e, "batch kernel launch");
