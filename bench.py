@@ -791,8 +791,11 @@ def serving_form(seed: int = 7, open_loop_s: float = 2.0):
     """The serving form: continuous batching over the four resident models, against the plain
     per-mechanism launch (one request at a time, no merging, no overlap) on the same requests.
     Capacity = closed-loop throughput of a fixed trace; then Poisson arrivals at 0.5x and 0.8x that
-    capacity (requests/s), with p50/p99 latency (submit -> result in device memory). Every server
-    first serves 40 untimed warm-up requests (a long-running server is warm)."""
+    capacity (requests/s), with p50/p99 latency (submit -> result in device memory); then the same
+    with every result copied to host memory (submit -> result in host memory) at half of the
+    capacity measured with the copies. Requests above about 1 ms of GPU time are cut into chunks
+    (the server's default); the plain per-request baseline cuts nothing. Every server first serves
+    40 untimed warm-up requests (a long-running server is warm)."""
     import torch
     import paper_1605_03262_b300 as pj
     from paper_1605_03262_b300.serving import Server, latency_summary
@@ -831,7 +834,7 @@ def serving_form(seed: int = 7, open_loop_s: float = 2.0):
     cap_trace = _request_trace(models, 160, seed)
     warm = _request_trace(models, 40, seed + 999)            # each server sees these first, untimed
     cap = run(cap_trace, [0.0] * len(cap_trace), warm)
-    cap_plain = run(cap_trace, [0.0] * len(cap_trace), warm, max_inflight=1, max_batch_states=1)
+    cap_plain = run(cap_trace, [0.0] * len(cap_trace), warm, max_inflight=1, max_batch_states=1, chunk_ms=None)
     req_rate = cap["requests"] / cap["wall_s"]
     res = {"capacity_closed_loop": cap, "plain_per_request_closed_loop": cap_plain, "offered": {}}
     rng = np.random.default_rng(seed + 1)
@@ -843,8 +846,18 @@ def serving_form(seed: int = 7, open_loop_s: float = 2.0):
         res["offered"]["%.1fx" % frac] = {
             "request_rate_per_s": lam,
             "continuous_batching": run(trace, arrivals, warm),
-            "plain_per_request": run(trace, arrivals, warm, max_inflight=1, max_batch_states=1),
+            "plain_per_request": run(trace, arrivals, warm, max_inflight=1, max_batch_states=1, chunk_ms=None),
         }
+    # latency to results in host memory: the device-to-host copy (PCIe, ~56 GB/s) bounds that
+    # capacity, so the open-loop run offers half of the capacity measured with the copies
+    cap_host = run(cap_trace, [0.0] * len(cap_trace), warm, host_results=True)
+    res["capacity_closed_loop_host"] = cap_host
+    lam = 0.5 * cap_host["requests"] / cap_host["wall_s"]
+    n_req = max(20, int(lam * open_loop_s))
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+    trace = _request_trace(models, n_req, seed + 70)
+    res["offered_host"] = {"0.5x": {"request_rate_per_s": lam, "continuous_batching": run(trace, arrivals, warm,
+                                                                                          host_results=True)}}
     torch.cuda.empty_cache()
     return res
 
@@ -991,9 +1004,10 @@ def compact_forms(batched, serving, dyf, cvf, fd, concf) -> dict:
             cb, pl = v["continuous_batching"], v["plain_per_request"]
             sv[k] = {"p50_ms": _sig(cb["p50_ms"], 3), "p99_ms": _sig(cb["p99_ms"], 3),
                      "plain_p50_ms": _sig(pl["p50_ms"], 3), "plain_p99_ms": _sig(pl["p99_ms"], 3)}
-            if "host_p99_ms" in cb:
-                sv[k]["host_p50_ms"] = _sig(cb["host_p50_ms"], 3)
-                sv[k]["host_p99_ms"] = _sig(cb["host_p99_ms"], 3)
+        if "capacity_closed_loop_host" in serving:
+            h = serving["offered_host"]["0.5x"]["continuous_batching"]
+            sv["host"] = {"capacity_jacobians_per_s": _sig(serving["capacity_closed_loop_host"]["jacobians_per_s"]),
+                          "0.5x_p50_ms": _sig(h["p50_ms"], 3), "0.5x_p99_ms": _sig(h["p99_ms"], 3)}
         out["serving"] = sv
     if dyf:
         out["dydt_evals_per_s"] = {k: _sig(v["evaluations_per_s"], 3) for k, v in dyf.items()}

@@ -318,13 +318,9 @@ class Server:
                 if self.host_results:
                     hres = []
                     for J, F in results:
-                        Jh = torch.empty(J.shape, dtype=torch.float64, pin_memory=True)
-                        Jh.copy_(J, non_blocking=True)
-                        Fh = None
-                        if F is not None:
-                            Fh = torch.empty(F.shape, dtype=torch.float64, pin_memory=True)
-                            Fh.copy_(F, non_blocking=True)
-                        hres.append((Jh.numpy(), Fh.numpy() if Fh is not None else None))
+                        Jh = self._copy_to_host(it.stream, J)
+                        Fh = self._copy_to_host(it.stream, F) if F is not None else None
+                        hres.append((Jh.numpy() if Jh is not None else None, Fh.numpy() if Fh is not None else None))
                     results = hres
                 it.results = results
                 it.event = torch.cuda.Event()
@@ -337,18 +333,27 @@ class Server:
             self.stats["max_inflight_seen"] = max(self.stats["max_inflight_seen"], len(self._inflight))
             admitted = True
 
-    def _host_buffer(self, stream, shape):
-        """Pinned host memory for a copy of the given shape: a fresh buffer handed to the client, or,
-        when results are discarded, the stream's reused staging buffer."""
+    STAGE_DOUBLES = 1 << 24             # 128 MB of pinned staging per stream (discarded host results)
+
+    def _copy_to_host(self, stream, src):
+        """Copy a device result to host memory on the stream: into a fresh pinned buffer that is
+        returned (results handed to the client), or, when results are discarded, piece by piece
+        through the stream's fixed pinned staging buffer (the copy takes its PCIe time, the host
+        memory stays bounded); returns None then."""
         torch = self.torch
-        count = int(np.prod(shape))
         if not self.discard_results:
-            return torch.empty(shape, dtype=torch.float64, pin_memory=True)
+            h = torch.empty(src.shape, dtype=torch.float64, pin_memory=True)
+            h.copy_(src, non_blocking=True)
+            return h
         buf = self._stage.get(id(stream))
-        if buf is None or buf.numel() < count:
-            buf = torch.empty(max(count, 1), dtype=torch.float64, pin_memory=True)
+        if buf is None:
+            buf = torch.empty(self.STAGE_DOUBLES, dtype=torch.float64, pin_memory=True)
             self._stage[id(stream)] = buf
-        return buf[:count].view(shape)
+        flat = src.reshape(-1)
+        for a in range(0, flat.numel(), buf.numel()):
+            b = min(flat.numel(), a + buf.numel())
+            buf[: b - a].copy_(flat[a:b], non_blocking=True)
+        return None
 
     def _admit_chunk(self, r: Request, model) -> None:
         """One chunk of a chunked request on a free stream, into its slice of the request's output
@@ -382,7 +387,7 @@ class Server:
                                 stream=it.stream)
             if self.host_results:
                 if self.discard_results:                  # the copy counts, its result is dropped
-                    self._host_buffer(it.stream, (b - a, N + 1, N + 1)).copy_(J[a:b], non_blocking=True)
+                    self._copy_to_host(it.stream, J[a:b])
                 else:
                     r.host[0][a:b].copy_(J[a:b], non_blocking=True)
                     if F is not None:
@@ -460,13 +465,9 @@ class Server:
                 it.F = torch.empty((n, N + 1), dtype=torch.float64, device=self.device) if want_f else None
                 model.eval_jacobian(T, P, Y, out=it.J, dydt_out=it.F, stream=it.stream)
                 if self.host_results:
-                    Jh = self._host_buffer(it.stream, tuple(it.J.shape))
-                    Jh.copy_(it.J, non_blocking=True)
-                    Fh = None
-                    if it.F is not None and not self.discard_results:
-                        Fh = torch.empty(it.F.shape, dtype=torch.float64, pin_memory=True)
-                        Fh.copy_(it.F, non_blocking=True)
-                    it.host = (Jh.numpy(), Fh.numpy() if Fh is not None else None)
+                    Jh = self._copy_to_host(it.stream, it.J)
+                    Fh = self._copy_to_host(it.stream, it.F) if it.F is not None else None
+                    it.host = (Jh.numpy() if Jh is not None else None, Fh.numpy() if Fh is not None else None)
                     it.J = it.F = None
                 it.event = torch.cuda.Event()
                 it.event.record(it.stream)
