@@ -277,7 +277,7 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.c_chunk = reinterpret_cast<const int2 *>(b + o_cc);
     d.s_npart = im.s_npart;
     d.s_comb_chunk = reinterpret_cast<const int2 *>(b + o_scc);
-    d.s_comb = reinterpret_cast<const int4 *>(b + o_scb);
+    d.s_comb = reinterpret_cast<const int2 *>(b + o_scb);
     d.tables = reinterpret_cast<const pj::MathTables *>(b + o_mt);
     d.cc_nnz = int(im.cc_col.size());
     d.cc_ptr = reinterpret_cast<const int *>(b + o_ccp);

@@ -94,8 +94,11 @@ struct DevModel {
     const uint4 *h_rec, *c_rec, *s_rec;   // column sums, C_k, sparse rows
     const int2 *g_chunk, *h_chunk, *c_chunk, *s_chunk;   // per chunk: record offset, rows
     int s_npart;              // partial slots a warp needs for the split row entries of one chunk
-    const int2 *s_comb_chunk; // per row chunk: offset into s_comb, number of split entries
-    const int4 *s_comb;       // split row entry: staged position, first partial slot, partials, 0
+    const int2 *s_comb_chunk; // per row chunk: its first combine pass, number of passes
+    // combine passes of the split row entries, one record per lane: x = the element the lane
+    // loads (>= 0: staged position of the entry's value; < 0: -1 - partial slot), y = position
+    // in the entry's segment | segment length << 8 | tree levels of the pass << 16
+    const int2 *s_comb;
     const MathTables *tables;  // exp/log tables (pj_fastmath.cuh)
     // molar-concentration basis: per species row k < N-1, its pattern entries cc_ptr[k]..cc_ptr[k+1]
     // (columns n_j, ascending j, in cc_col; cc_wr = W_j / W_k). rx_dnu: sum_k nu_ki per reaction.

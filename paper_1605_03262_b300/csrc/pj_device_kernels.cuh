@@ -1125,15 +1125,15 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
         double *Jout = io.jac + st * io.ldj;
         constexpr int kDense = 4;
         double acc = 0.0;
-        int2 comb = make_int2(0, 0);                 // this chunk's split-entry list
-        int4 crec = make_int4(0, 0, 0, 0);
+        int2 comb = make_int2(0, 0);                 // this chunk's combine passes (first, count)
+        int2 crec = make_int2(0, 0);                 // this lane's record of the chunk's first pass
         walk<SB, true, true>(m.s_chunk, m.n_row_chunks, wg, NW, m.s_rec, lane,
              [&](int c) {                               // dense part of chunk c
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
                  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                  __syncwarp();                          // the previous chunk's bulk copy has read the stage
                  stage = stage0 + ((!CONC && (reinterpret_cast<uintptr_t>(Jout + (long long)r0 * ld) & 15)) ? 1 : 0);
-                 comb = __ldg(m.s_comb_chunk + c);     // split entries of this chunk
+                 comb = __ldg(m.s_comb_chunk + c);     // combine passes of this chunk's split entries
                  if (RPC == 1 && r0 > 0) {              // one species row: its constants once
                      const int k = r0 - 1;
                      const double a = sA[k], ck = sCk[k], jk0 = sJk0[k];
@@ -1154,7 +1154,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                          for (int u = 0; u < kDense; ++u) stage[x + 32 * u] = v[u];
                      }
                      for (; x < ld; x += 32) stage[x] = value1(x);
-                     crec = lane < comb.y ? __ldg(m.s_comb + comb.x + lane) : make_int4(0, 0, 0, 0);
+                     crec = comb.y > 0 ? __ldg(m.s_comb + 32 * comb.x + lane) : make_int2(0, 0);
                      __syncwarp();
                      return;
                  }
@@ -1206,7 +1206,7 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
                      stage[x0] = value(rr, j);
                      step();
                  }
-                 crec = lane < comb.y ? __ldg(m.s_comb + comb.x + lane) : make_int4(0, 0, 0, 0);
+                 crec = comb.y > 0 ? __ldg(m.s_comb + 32 * comb.x + lane) : make_int2(0, 0);
                  __syncwarp();
              },
              // sparse part: the chunk's lane-balanced schedule. An entry's sum starts from its dense
@@ -1225,11 +1225,21 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
              [&](int c) {                               // 16-byte streaming stores of the finished rows
                  const int r0 = c * RPC, nel = (min(r0 + RPC, ld) - r0) * ld;
                  __syncwarp();
-                 for (int e = lane; e < comb.y; e += 32) {   // split entries: add the partials in order
-                     const int4 cr = e == lane ? crec : __ldg(m.s_comb + comb.x + e);
-                     double v = stage[cr.x];
-                     for (int q = 0; q < cr.z; ++q) v += pbuf[cr.y + q];
-                     stage[cr.x] = v;
+                 // split entries: each entry's segment [staged value, partial sums of its later
+                 // pieces] lies on consecutive lanes of a pass and is summed by a fixed pairwise tree
+                 // (lane pos adds lane pos + d when pos is a multiple of 2d), so that all lanes of the
+                 // pass add at once instead of one lane per entry adding its partials in a row
+                 for (int q = 0; q < comb.y; ++q) {
+                     const int2 cr = q == 0 ? crec : __ldg(m.s_comb + 32 * (comb.x + q) + lane);
+                     const int pos = cr.y & 255, len = (cr.y >> 8) & 255, levels = cr.y >> 16;
+                     double v = 0.0;
+                     if (len) v = cr.x >= 0 ? stage[cr.x] : pbuf[-1 - cr.x];
+                     for (int l = 0; l < levels; ++l) {
+                         const int d = 1 << l;
+                         const double o = __shfl_down_sync(0xffffffffu, v, d);
+                         if ((pos & (2 * d - 1)) == 0 && pos + d < len) v += o;
+                     }
+                     if (len && pos == 0) stage[cr.x] = v;
                  }
                  // the finished rows go out as one bulk copy (TMA engine) of their 16-byte aligned
                  // middle, issued by lane 0 after the warp's shared-memory writes are fenced for the

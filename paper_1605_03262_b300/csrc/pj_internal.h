@@ -41,7 +41,7 @@ struct HostImage {
     std::vector<uint32_t> g_rec, h_rec, c_rec, s_rec;       // 2, 4, 4, 4 words per record
     std::vector<int> g_chunk, h_chunk, c_chunk, s_chunk;   // (record offset, rows) per chunk
     int s_npart = 0;
-    std::vector<int> s_comb_chunk, s_comb;                 // (offset, count) per chunk; 4 ints per entry
+    std::vector<int> s_comb_chunk, s_comb;                 // (first pass, passes) per chunk; 32 x 2 ints per pass
     // molar-concentration basis: species-row pattern (DevModel::cc_ptr / cc_col / cc_wr), sum_k nu_ki
     std::vector<int> cc_ptr, cc_col;
     std::vector<double> cc_wr, rx_dnu;

@@ -11,6 +11,7 @@
 //     b-slots for the energy row, and (row k, column l) -> (b-slot, nu_ki) for the sparse block.
 // The derivation of these terms from the paper's Section 3 chain rule is given in pj_kernels.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -836,13 +837,15 @@ HostImage build_image(const void *buf, size_t len) {
             const size_t plen = std::max<size_t>(2, (total + 31) / 32);
             std::vector<Task> pieces;
             int npart = 0;
-            const int coff = int(im.s_comb.size() / 4);
+            std::vector<std::array<int, 3>> split;   // (staged position, first partial slot, partials)
             for (const Task &t : tasks) {
                 const size_t n = t.idx.size();
+                // at most 32 pieces, so that an entry's value and partials fit one warp's lanes
+                const size_t len = std::max(plen, (n + 31) / 32);
                 int first_part = -1, nparts = 0;
-                for (size_t b = 0; b < n; b += plen) {
+                for (size_t b = 0; b < n; b += len) {
                     Task p;
-                    const size_t e = std::min(n, b + plen);
+                    const size_t e = std::min(n, b + len);
                     for (size_t q = b; q < e; ++q) {
                         p.idx.push_back(t.idx[q]);
                         p.code.push_back(t.code[q]);
@@ -859,21 +862,45 @@ HostImage build_image(const void *buf, size_t len) {
                     }
                     pieces.push_back(std::move(p));
                 }
-                if (nparts > 0) {
-                    im.s_comb.push_back(t.dst);
-                    im.s_comb.push_back(first_part);
-                    im.s_comb.push_back(nparts);
-                    im.s_comb.push_back(0);
-                }
+                if (nparts > 0) split.push_back({t.dst, first_part, nparts});
             }
-            im.s_comb_chunk.push_back(coff);
-            im.s_comb_chunk.push_back(int(im.s_comb.size() / 4) - coff);
+            // combine passes: the split entries' segments [staged value, partial 0, partial 1, ...]
+            // packed onto the 32 lanes of a warp in entry order, each pass summed by a fixed pairwise
+            // tree within every segment (levels: enough for the pass's longest segment)
+            const int first_pass = int(im.s_comb.size() / 64);
+            int npass = 0;
+            for (size_t a = 0; a < split.size();) {
+                size_t b = a;
+                int lanes = 0, longest = 0;
+                while (b < split.size() && lanes + split[b][2] + 1 <= 32) {
+                    lanes += split[b][2] + 1;
+                    longest = std::max(longest, split[b][2] + 1);
+                    ++b;
+                }
+                int levels = 0;
+                while ((1 << levels) < longest) ++levels;
+                std::vector<int> rec(64, 0);
+                int l = 0;
+                for (size_t e = a; e < b; ++e) {
+                    const int seg = split[e][2] + 1;
+                    for (int q = 0; q < seg; ++q, ++l) {
+                        rec[2 * l] = q == 0 ? split[e][0] : -1 - (split[e][1] + q - 1);
+                        rec[2 * l + 1] = q | (seg << 8) | (levels << 16);
+                    }
+                }
+                for (; l < 32; ++l) rec[2 * l + 1] = levels << 16;   // idle lanes (segment length 0)
+                im.s_comb.insert(im.s_comb.end(), rec.begin(), rec.end());
+                ++npass;
+                a = b;
+            }
+            im.s_comb_chunk.push_back(first_pass);
+            im.s_comb_chunk.push_back(npass);
             im.s_npart = std::max(im.s_npart, npart);
             std::vector<const Task *> ptrs;
             for (auto &t : pieces) ptrs.push_back(&t);
             emit_chunk(ptrs, zero_slot, zero_code, 0, kRecCoef, im.s_rec, im.s_chunk);
         }
-        if (im.s_comb.empty()) im.s_comb.assign(4, 0);
+        if (im.s_comb.empty()) im.s_comb.assign(64, 0);
     }
     return im;
 }
