@@ -160,7 +160,7 @@ def work_model(model) -> dict:
 
 # FP64 operations of one call of the table-driven exp and log (Tang's methods, as implemented):
 # range reduction, polynomial and reconstruction. Division is weighted by its measured throughput.
-EXP_OPS, LOG_OPS = 10.0, 12.0
+EXP_OPS, LOG_OPS = 9.0, 12.0
 
 
 def dfma_equivalents(work: dict, ratios: dict) -> float:

@@ -2,8 +2,8 @@
 // rate is the binding limit. Both follow P. T. P. Tang's table-driven methods, written here from
 // the methods' description:
 //   exp: "Table-driven implementation of the exponential function in IEEE floating-point
-//        arithmetic", ACM TOMS 15(2), 1989. x = (256 m + j) ln2/256 + r with |r| <= ln2/512;
-//        exp(x) = 2^m 2^(j/256) exp(r), exp(r) - 1 by a degree-5 polynomial.
+//        arithmetic", ACM TOMS 15(2), 1989. x = (512 m + j) ln2/512 + r with |r| <= ln2/1024;
+//        exp(x) = 2^m 2^(j/512) exp(r), exp(r) - 1 by a degree-4 polynomial.
 //   log: "Table-driven implementation of the logarithm function in IEEE floating-point
 //        arithmetic", ACM TOMS 16(4), 1990. x = 2^m y, F = 1 + j/256 nearest to y,
 //        log x = m ln2 + log F + log(1 + (y - F)/F), the last by a degree-6 polynomial; the leading
@@ -21,7 +21,7 @@
 
 namespace pj {
 
-constexpr int kExpTableSize = 256;   // 2^(j/256), j = 0..255
+constexpr int kExpTableSize = 512;   // 2^(j/512), j = 0..511
 constexpr int kLogTableSize = 257;   // F = 1 + j/256, j = 0..256
 
 struct MathTables {
@@ -29,9 +29,9 @@ struct MathTables {
     double logF_hi[kLogTableSize];   // log F rounded to a multiple of 2^-42
     double logF_lo[kLogTableSize];   // log F - logF_hi
     double invF[kLogTableSize];      // 1/F rounded
-    double exp_invL;                 // 256 / ln 2
-    double exp_L1;                   // ln2/256 with its low bits cleared (exact k * L1 for |k| < 2^18)
-    double exp_L2;                   // ln2/256 - exp_L1
+    double exp_invL;                 // 512 / ln 2
+    double exp_L1;                   // ln2/512 with its low bits cleared (exact k * L1 for |k| < 2^20)
+    double exp_L2;                   // ln2/512 - exp_L1
     double ln2_hi;                   // ln 2 rounded to a multiple of 2^-42
     double ln2_lo;                   // ln 2 - ln2_hi
     double pad;
@@ -40,7 +40,7 @@ struct MathTables {
 #ifndef __CUDACC_RTC__
 inline void build_math_tables(MathTables &t) {
     const long double ln2 = logl(2.0L);
-    for (int j = 0; j < kExpTableSize; ++j) t.exp2j[j] = double(exp2l((long double)j / 256.0L));
+    for (int j = 0; j < kExpTableSize; ++j) t.exp2j[j] = double(exp2l((long double)j / 512.0L));
     const long double q42 = ldexpl(1.0L, 42);
     for (int j = 0; j < kLogTableSize; ++j) {
         const long double F = 1.0L + (long double)j / 256.0L;
@@ -50,9 +50,9 @@ inline void build_math_tables(MathTables &t) {
         t.logF_lo[j] = double(lf - hi);
         t.invF[j] = double(1.0L / F);
     }
-    const long double L = ln2 / 256.0L;
+    const long double L = ln2 / 512.0L;
     t.exp_invL = double(1.0L / L);
-    const long double q = ldexpl(1.0L, 43);            // L < 2^-8: 35 significant bits, k * L1 exact for |k| < 2^18
+    const long double q = ldexpl(1.0L, 42);            // L < 2^-9: 33 significant bits, k * L1 exact for |k| < 2^20
     const long double l1 = roundl(L * q) / q;
     t.exp_L1 = double(l1);
     t.exp_L2 = double(L - l1);
@@ -65,24 +65,23 @@ inline void build_math_tables(MathTables &t) {
 
 #ifdef __CUDACC__
 
-// exp(x): 10 FP64 operations on |x| <= 700.
+// exp(x): 9 FP64 operations on |x| <= 700.
 __device__ __forceinline__ double fast_exp(double x, const MathTables *__restrict__ tb) {
     const int hi = __double2hiint(x) & 0x7fffffff;
     if (hi >= 0x4085e000) return exp(x);           // |x| >= 700, inf or NaN: library path
-    constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52: x * 256/ln2 + kShift rounds to an integer
+    constexpr double kShift = 6755399441055744.0;  // 1.5 * 2^52: x * 512/ln2 + kShift rounds to an integer
     const double t = fma(x, __ldg(&tb->exp_invL), kShift);
     const int k = __double2loint(t);
     const double kd = t - kShift;
     double r = fma(-kd, __ldg(&tb->exp_L1), x);
     r = fma(-kd, __ldg(&tb->exp_L2), r);
-    // exp(r) - 1, |r| <= 1.36e-3: the r^6 term is below 1e-20
-    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    q = fma(q, r, 1.0 / 6.0);
+    // exp(r) - 1, |r| <= 6.8e-4: the r^5 term is below 2e-18
+    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     q = fma(q, r, 0.5);
     const double p = fma(q, r * r, r);
     const double tj = __ldg(&tb->exp2j[k & (kExpTableSize - 1)]);
-    const double v = fma(tj, p, tj);               // 2^(j/256) exp(r), in [1, 2.01)
-    const long long m = static_cast<long long>(k >> 8);
+    const double v = fma(tj, p, tj);               // 2^(j/512) exp(r), in [1, 2.01)
+    const long long m = static_cast<long long>(k >> 9);
     return __longlong_as_double(__double_as_longlong(v) + (m << 52));
 }
 
