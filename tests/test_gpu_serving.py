@@ -164,3 +164,65 @@ def test_chunked_request_equals_unchunked_result(host):
         assert torch.equal(torch.as_tensor(res).cuda(), ref)
     # the big request did not hold the small ones back until its end: some finished before it
     assert min(f.request.t_done for f in f_small) <= f_big.request.t_done
+
+
+
+def test_input_kinds_give_the_same_results():
+    """Requests given as numpy arrays (float64 or float32), pageable or pinned host tensors, or
+    CUDA tensors return the plain launch's bits, in launches that merge host inputs only, device
+    inputs only, both kinds, or hold a single request (host or device)."""
+    from paper_1605_03262_b300.serving import Server
+    models = _models()
+    name = synth.CONFIGS[1]["name"]
+    N = models[name].n_species
+    kinds = {"numpy": lambda a: a, "numpy32": lambda a: a.astype(np.float32),
+             "pageable": lambda a: torch.from_numpy(a), "pinned": lambda a: torch.from_numpy(a).pin_memory(),
+             "cuda": lambda a: torch.as_tensor(a, device="cuda")}
+    phases = [["numpy", "pageable", "pinned", "numpy32"], ["cuda", "cuda", "cuda"],
+              ["cuda", "numpy", "pinned", "cuda"], ["pinned"], ["cuda"]]
+    seed = 300
+    for phase in phases:
+        reqs = []
+        for kind in phase:
+            seed += 1
+            T, P, Y = synth.generate_states(N, 5 + seed % 37, seed=seed)
+            if kind == "numpy32":
+                T, P, Y = (a.astype(np.float32).astype(np.float64) for a in (T, P, Y))
+            reqs.append(((T, P, Y), tuple(kinds[kind](np.ascontiguousarray(a)) for a in (T, P, Y))))
+        srv = Server(models, max_inflight=1)
+        futs = [srv.submit(name, *given) for _, given in reqs]   # queued before the loop starts
+        srv.start()
+        try:
+            res = [f.result(timeout=120) for f in futs]
+        finally:
+            srv.stop()
+        assert srv.stats["merged_requests"] == len(reqs) - 1   # one launch for the phase
+        for ((T, P, Y), _), J in zip(reqs, res):
+            ref = models[name].eval_jacobian(*(torch.as_tensor(a, device="cuda") for a in (T, P, Y)))
+            assert torch.equal(J, ref)
+
+
+def test_chunked_requests_proceed_while_a_new_one_waits_for_memory():
+    """With room for two large requests, four of them cut into chunks that rotate through the
+    queue: when a request that has not started waits for memory at the head of the queue, the
+    started ones still get their next chunks (they free the memory it waits for), and all four
+    complete with the plain launch's results."""
+    from paper_1605_03262_b300.serving import Server
+    models = _models()
+    name = synth.CONFIGS[1]["name"]
+    N = models[name].n_species
+    n = 2000
+    per_request = Server._bytes(models[name], n)
+    reqs = [synth.generate_states(N, n, seed=400 + k) for k in range(4)]
+    srv = Server(models, hbm_budget=int(2.5 * per_request), max_inflight=2, chunk_ms=0.02)
+    srv.start()
+    try:
+        futs = [srv.submit(name, *r) for r in reqs]
+        res = [f.result(timeout=60) for f in futs]
+        stats = dict(srv.stats)
+    finally:
+        srv.stop(drain=False)
+    assert stats["chunked_requests"] == 4 and stats["waits_for_memory"] > 0
+    for (T, P, Y), J in zip(reqs, res):
+        ref = models[name].eval_jacobian(*(torch.as_tensor(a, device="cuda") for a in (T, P, Y)))
+        assert torch.equal(J, ref)
