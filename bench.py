@@ -747,7 +747,8 @@ def batched_form(steps: int, warmup: int):
                                    "tiles": dflt.n_tiles, "kernel": "data-driven"},
                "batched_tuned": {"ms": timed(tuned.run), "graph_ms": timed(tuned_graph.replay), "launches": 1,
                                  "tiles": tuned.n_tiles, "choice": rep["choice"], "item_shapes": rep["item_shapes"],
-                                 "tuning_ms": rep["timings"], "specialised": rep["specialised"]}}
+                                 "tuning_ms": rep["timings"], "specialised_ms": rep["specialised_ms"],
+                                 "specialised": rep["specialised"]}}
         for k in ("plain_sequential", "batched_default", "batched_tuned"):
             out[k]["jacobians_per_s"] = n_states / (out[k]["ms"] * 1e-3)
         del dflt, dflt_graph, tuned, tuned_graph, plain_graph

@@ -153,6 +153,7 @@ int pj_batch_create_ex(const pj_batch_item *items, int n_items, int which, const
         bi[i].pad = slot;
     }
     bt->items = bi;
+    bt->tiles = tiles;
     bt->which = which;
     bt->device = dev;
     bt->threads = threads;
@@ -162,7 +163,7 @@ int pj_batch_create_ex(const pj_batch_item *items, int n_items, int which, const
     bt->ntiles = int(tiles.size());
     const size_t o_items = 0, o_tiles = (sizeof(pj::BatchItem) * n_items + 255) & ~size_t(255);
     const size_t o_ctr = (o_tiles + sizeof(pj::BatchTile) * std::max<size_t>(1, tiles.size()) + 255) & ~size_t(255);
-    const size_t bytes = o_ctr + 256;
+    const size_t bytes = o_ctr + sizeof(int) * pj::kBatchSpecMaxSlots;
     if ((e = cudaMalloc(&bt->dev, bytes)) != cudaSuccess) {
         delete bt;
         cudaGetLastError();
@@ -194,12 +195,17 @@ int pj_batch_run(pj_batch *b, void *stream) {
     if (e != cudaSuccess) return bcuda(e, "cudaGetDevice");
     if (cur != b->device) return bfail(PJ_EINVAL, "pj_batch_run: the current device is not the plan's device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if ((e = cudaMemsetAsync(b->params.counter, 0, sizeof(int), st)) != cudaSuccess) return bcuda(e, "counter reset");
+    const int counters = b->spec ? b->spec->slots : 1;  // the specialised kernel: one per slot
+    if ((e = cudaMemsetAsync(b->params.counter, 0, sizeof(int) * counters, st)) != cudaSuccess)
+        return bcuda(e, "counter reset");
     const int blocks = std::max(1, std::min(b->sms * b->ctas_per_sm, b->ntiles));
     if (b->spec) {                                    // the kernel specialised for this plan
         const void *k = reinterpret_cast<const void *>(b->spec->kern);
-        void *args[] = {&b->params};
-        e = cudaLaunchKernel(k, dim3(blocks), dim3(b->threads), args, b->smem, st);
+        pj::BatchParams p = b->params;
+        p.items = b->spec->items;
+        p.tiles = b->spec->tiles;
+        void *args[] = {&p};
+        e = cudaLaunchKernel(k, dim3(blocks), dim3(b->threads), args, b->spec->smem, st);
     } else {
         // the kernel's dynamic shared memory limit is one per process: another plan may have set
         // a smaller one since this plan was built
@@ -232,18 +238,13 @@ int pj_batch_specialize(pj_batch *b, int enable) {
     std::string err;
     const int rc = pj::specialize_batch(b, &err);
     if (rc != PJ_OK) return bfail(rc, "pj_batch_specialize: " + err);
-    if (b->spec && (e = cudaFuncSetAttribute(reinterpret_cast<const void *>(b->spec->kern),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem))) != cudaSuccess) {
-        pj::batch_spec_release(b);
-        return bcuda(e, "specialised batch kernel attribute");
-    }
     return PJ_OK;
 }
 
 int pj_batch_spec_info(const pj_batch *b, int *active, int *slots, double *compile_seconds, size_t *cubin_bytes) {
     if (!b) return bfail(PJ_EINVAL, "pj_batch_spec_info: null plan");
     if (active) *active = b->spec != nullptr;
-    if (slots) *slots = int(b->slot_mech.size());
+    if (slots) *slots = b->spec ? b->spec->slots : int(b->slot_mech.size());
     if (compile_seconds) *compile_seconds = b->spec ? b->spec->compile_seconds : 0.0;
     if (cubin_bytes) *cubin_bytes = b->spec ? b->spec->cubin_bytes : 0;
     return PJ_OK;

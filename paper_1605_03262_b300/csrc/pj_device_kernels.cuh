@@ -900,6 +900,12 @@ __device__ __forceinline__ void conc_tv(const DevModel &m, const Scratch &sc, do
     group_sync<WPS>(g);
 }
 
+// The CTA's counters: the reaction stage's next run of items, and the specialised batched kernel's
+// next tile. Declared once for the module, so that a kernel that instantiates the stages for
+// several models still holds one of each in shared memory.
+__shared__ int s_next_item;
+__shared__ int s_slot_tile;
+
 // One round of a CTA: each group evaluates one state (prep, gathers, rows), and the reaction stage
 // of the round's states runs over the whole CTA. All threads of the CTA call this together.
 // active = false: a thread without a state in this round (a group past the last state, or a
@@ -934,7 +940,6 @@ __device__ __forceinline__ void eval_state(const DevModel &m, const Scratch &sc,
     // small reaction classes. Warps take runs of 32 items from a shared counter, the costliest
     // families first, so warps that drew falloff items take fewer of the rest and the stage ends
     // balanced. The arithmetic of a reaction does not depend on who evaluates it.
-    __shared__ int s_next_item;
     if (threadIdx.x == 0) s_next_item = blockDim.x;     // every warp's first run is its own
     __syncthreads();
     const int nitems = R * gact;
@@ -1388,17 +1393,18 @@ __global__ void __launch_bounds__(512, 1) pj_batch_kernel(const __grid_constant_
     }
 }
 
-// Batched form, specialised for a plan's models (kernels generated by pj_nvrtc.cu). The model of
-// the CTA's current tile sits in s_batch_model (shared memory, visible to every function of the
-// kernel); each (model, group width) pair of the plan is a slot whose sizes, offsets and width
-// Spec supplies as compile-time constants.
-__shared__ DevModel s_batch_model;
-
+// Batched form, specialised for a plan's models (kernels generated by pj_nvrtc.cu): each (model,
+// group width) pair of the plan is a slot whose sizes, offsets and width Spec supplies as
+// compile-time constants, and whose DevModel (the model image's device pointers) Spec::dev() reads
+// from the generated module's constant memory. Held there, like the plain kernel's parameters,
+// the pointers are operands of the instructions that use them; copied from shared memory into a
+// local DevModel they took registers of their own, and the one-model plan of the 360-species
+// model ran 1.55 x the plain kernel's time.
 template <bool JAC, int WPS, class Spec>
 __device__ __forceinline__ void run_tile_spec(const BatchItem *itp, long long begin, long long end, bool fresh) {
     extern __shared__ __align__(16) double smem[];
     const BatchItem &it = *itp;
-    DevModel m = s_batch_model;
+    DevModel m = Spec::dev();
     Spec::spec_model(m);
     Scratch sc;
     Spec::spec_scratch(sc);
@@ -1425,30 +1431,26 @@ __device__ __forceinline__ void run_tile_spec(const BatchItem *itp, long long be
     }
 }
 
-// Persistent loop of the specialised batched kernel: CTAs take tiles from the plan's counter and
-// run(slot, item, begin, end, fresh) evaluates one (fresh: the item differs from the CTA's last).
-template <class Run>
-__device__ __forceinline__ void batch_spec_body(const BatchParams &p, Run &&run) {
-    __shared__ int s_tile;
+// One slot's part of the specialised batched kernel: CTAs take the slot's tiles, [first, end) of
+// the plan's tile table, from the slot's counter, and evaluate them with the slot's constants.
+// The kernel runs the slots' parts one after another (a CTA moves on when the slot's tiles are
+// all taken, without waiting for other CTAs), each part inlined on its own: no switch or call
+// between models inside the loop, so each part gets the registers of a single-model kernel.
+template <bool JAC, int WPS, class Spec>
+__device__ __forceinline__ void run_slot_seq(const BatchParams &p, int slot, int first, int end) {
     int cur = -1;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(p.counter, 1);
+        if (threadIdx.x == 0) s_slot_tile = first + atomicAdd(p.counter + slot, 1);
         __syncthreads();
-        const int tile = s_tile;
-        if (tile >= p.ntiles) break;
+        const int tile = s_slot_tile;
+        if (tile >= end) break;
         const BatchTile tl = p.tiles[tile];
-        const BatchItem *it = p.items + tl.item;
         const bool fresh = tl.item != cur;
-        if (fresh) {
-            const int *src = reinterpret_cast<const int *>(it->m);
-            int *dst = reinterpret_cast<int *>(&s_batch_model);
-            for (int w = threadIdx.x; w < int(sizeof(DevModel) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-            __syncthreads();
-        }
-        run(it->pad, it, tl.begin, tl.begin + tl.count, fresh);
+        run_tile_spec<JAC, WPS, Spec>(p.items + tl.item, tl.begin, tl.begin + tl.count, fresh);
         cur = tl.item;
         __syncthreads();
     }
+    __syncthreads();                                    // every thread has read s_slot_tile
 }
 
 }  // namespace pj

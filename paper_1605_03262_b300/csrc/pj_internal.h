@@ -106,6 +106,10 @@ struct pj_batch_spec {
     double compile_seconds = 0.0;
     size_t cubin_bytes = 0;
     int slots = 0;
+    void *dev = nullptr;              // device: items | tiles of the specialised kernel
+    pj::BatchItem *items = nullptr;   // the plan's items at the specialised kernel's group widths
+    pj::BatchTile *tiles = nullptr;   // the plan's tiles grouped by slot, in the kernel's slot order
+    size_t smem = 0;                  // its dynamic shared memory per CTA
 };
 
 // A batched plan (pj_batch.cu): launch shape, device copies of the item table and tiles, and the
@@ -119,12 +123,21 @@ struct pj_batch {
     void *dev = nullptr;           // items | tiles | counter
     pj::BatchParams params{};
     std::vector<pj::BatchItem> items;        // host copy; pad = the item's slot
+    std::vector<pj::BatchTile> tiles;        // host copy, in the data-driven kernel's order
     std::vector<const pj_mech *> slot_mech;  // per slot: its model
     std::vector<int> slot_wps;               // per slot: warps per state
     pj_batch_spec *spec = nullptr;
 };
 
 namespace pj {
+// Tile counters in a plan's device buffer: one, or one per slot for the specialised kernel, which
+// is compiled for at most this many (model, group width) slots.
+constexpr int kBatchSpecMaxSlots = 64;
+// Static shared memory the specialised batched kernel may use (its tile and reaction-stage
+// counters, one of each whatever the number of slots); the item shapes of its plan leave this much
+// of the CTA's shared memory free.
+constexpr size_t kSpecBatchStaticSmem = 64;
+
 // Group width, states per CTA and scratch of one model in a batched launch of `threads` threads
 // and `budget` bytes of dynamic shared memory per CTA: the model's configured width, halved while
 // it exceeds the CTA or while one state's working set does not fit. False if no width fits.

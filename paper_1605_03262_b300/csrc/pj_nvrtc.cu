@@ -10,6 +10,7 @@
 // NVRTC is loaded on first use (dlopen), so the library itself does not depend on it.
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <chrono>
 #include <map>
 #include <cstdio>
@@ -201,22 +202,29 @@ int nvrtc_compile(const NvrtcApi &api, const std::string &src, const char *name,
     return PJ_OK;
 }
 
+// Slots of a batched plan's specialised kernel: the distinct (model, warps per state) pairs.
+struct SpecSlots {
+    std::vector<const pj_mech *> mech;
+    std::vector<int> wps;
+};
+
 // Source of a batched plan's specialised kernel: per slot a Spec type with the model's sizes and
-// scratch layout, a function that evaluates a tile of that slot with the slot's group width, and
-// a switch over the slots in the persistent loop. With several slots each slot's function is a
-// separate (non-inlined) function, so that the register allocation of one branch does not weigh
-// on the others.
-std::string batch_spec_source(const pj_batch &b) {
-    const bool jac = b.which == 0;
+// scratch layout, then the slots' parts of the persistent loop one after another (run_slot_seq),
+// in `order`, each over its range [first[k], first[k + 1]) of the grouped tile table. Launch
+// bounds: the plan's CTA size (a CTA of fewer than 512 threads leaves each thread more registers).
+std::string batch_spec_source(bool jac, int threads, const SpecSlots &sl, const std::vector<int> &order,
+                              const std::vector<int> &first) {
     const char *J = jac ? "true" : "false";
-    const int ns = int(b.slot_mech.size());
-    std::string s = "#include \"pj_device_kernels.cuh\"\nnamespace {\n";
+    const int ns = int(sl.mech.size());
+    std::string s = "#include \"pj_device_kernels.cuh\"\nextern \"C\" {\n";
+    for (int k = 0; k < ns; ++k)   // each slot's DevModel, written by specialize_batch after loading
+        s += "__constant__ pj::DevModel pj_slot_model" + std::to_string(k) + ";\n";
+    s += "}\nnamespace {\n";
     for (int k = 0; k < ns; ++k) {
-        const pj_mech &m = *b.slot_mech[k];
-        const std::string sk = std::to_string(k);
+        const pj_mech &m = *sl.mech[k];
         std::string body;
         emit_model(body, m.dev);
-        emit_scratch(body, "spec_scratch", make_scratch(m.dev, jac, b.slot_wps[k]));
+        emit_scratch(body, "spec_scratch", make_scratch(m.dev, jac, sl.wps[k]));
         // emit_model / emit_scratch write free functions; wrap them as static members of Slot<k>
         std::string wrapped;
         size_t pos = 0;
@@ -228,18 +236,20 @@ std::string batch_spec_source(const pj_batch &b) {
             wrapped += line + "\n";
             pos = e + 1;
         }
-        s += "struct Slot" + sk + " {\n" + wrapped + "};\n";
-        s += std::string("__device__ ") + (ns > 1 ? "__noinline__" : "__forceinline__") + " void run_slot" + sk +
-             "(const pj::BatchItem *it, long long b, long long e, bool f) {\n"
-             "    pj::run_tile_spec<" + J + ", " + std::to_string(b.slot_wps[k]) + ", Slot" + sk + ">(it, b, e, f);\n}\n";
+        s += "struct Slot" + std::to_string(k) + " {\n" + wrapped +
+             "    static __device__ __forceinline__ const pj::DevModel &dev() { return pj_slot_model" +
+             std::to_string(k) + "; }\n};\n";
     }
     s += "}  // namespace\n";
-    s += "extern \"C\" __global__ void __launch_bounds__(512, 1) pj_spec_batch(const __grid_constant__ pj::BatchParams p) {\n"
-         "    pj::batch_spec_body(p, [](int slot, const pj::BatchItem *it, long long b, long long e, bool f) {\n"
-         "        switch (slot) {\n";
-    for (int k = 0; k < ns; ++k)
-        s += "        case " + std::to_string(k) + ": run_slot" + std::to_string(k) + "(it, b, e, f); break;\n";
-    s += "        default: break;\n        }\n    });\n}\n";
+    s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(threads) +
+         ", 1) pj_spec_batch(const __grid_constant__ pj::BatchParams p) {\n";
+    for (int x = 0; x < ns; ++x) {
+        const int k = order[x];
+        s += "    pj::run_slot_seq<" + std::string(J) + ", " + std::to_string(sl.wps[k]) + ", Slot" +
+             std::to_string(k) + ">(p, " + std::to_string(k) + ", " + std::to_string(first[x]) + ", " +
+             std::to_string(first[x + 1]) + ");\n";
+    }
+    s += "}\n";
     return s;
 }
 
@@ -274,29 +284,145 @@ int specialize(pj_mech *m, std::string *err) {
     return PJ_OK;
 }
 
-// Compiles and loads the kernel of a batched plan specialised for its slots.
+// Compiles and loads the kernel of a batched plan specialised for its models. Its item table is
+// the plan's, except that an item whose group width the data-driven plan had to halve gets its
+// model's own width back where the working set fits: the data-driven batched kernel keeps a
+// DevModel (432 bytes) in static shared memory, which left the 360-species model's 16-warp
+// working set no room, and at 8 warps per state that model ran 1.45 x the plain kernel's time.
+// Tiles are grouped by slot (slots in decreasing work per state, so that the last part has the
+// finest tiles; within a slot, the plan's order). Items and tiles are uploaded to device memory of
+// the specialisation's own.
+// Work (the plan's per-state cost units) of one tile of the specialised kernel at most: four rounds
+// of seven states of the 53-species model, about 0.4 ms.
+constexpr double kTileWork = 6.3e5;
+
 int specialize_batch(pj_batch *b, std::string *err) {
-    if (b->slot_mech.empty()) {
+    const bool jac = b->which == 0;
+    const int n = int(b->items.size());
+    if (n == 0) {
         *err = "the plan has no items";
         return PJ_EINVAL;
     }
-    const std::string src = batch_spec_source(*b);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    const size_t budget = size_t(optin) > kSpecBatchStaticSmem ? size_t(optin) - kSpecBatchStaticSmem : 0;
+    std::vector<BatchItem> items = b->items;
+    SpecSlots sl;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        BatchItem &it = items[i];
+        const pj_mech *m = b->slot_mech[it.pad];
+        const int w = (jac ? m->jac_cfg : m->dydt_cfg).wps;
+        if (w > it.wps && w * 32 <= b->threads) {
+            const Scratch sc = make_scratch(m->dev, jac, w);
+            int gmax = b->threads / (32 * w);
+            if (w > 1) gmax = std::min(gmax, 15);
+            while (gmax > 0 && (size_t(it.shared_const) + size_t(sc.total) * gmax) * 8 > budget) --gmax;
+            if (gmax >= 1) {
+                it.wps = w;
+                it.sc = sc;
+                it.groups = gmax;
+            }
+        }
+        smem = std::max(smem, (size_t(it.shared_const) + size_t(it.sc.total) * it.groups) * 8);
+        int slot = -1;
+        for (size_t k = 0; k < sl.mech.size(); ++k)
+            if (sl.mech[k] == m && sl.wps[k] == it.wps) slot = int(k);
+        if (slot < 0) {
+            slot = int(sl.mech.size());
+            sl.mech.push_back(m);
+            sl.wps.push_back(it.wps);
+        }
+        it.pad = slot;
+    }
+    const int ns = int(sl.mech.size());
+    if (ns > kBatchSpecMaxSlots) {
+        *err = "the plan has more than " + std::to_string(kBatchSpecMaxSlots) + " (model, group width) slots";
+        return PJ_EUNSUPPORTED;
+    }
+    std::vector<int> order(ns);
+    for (int k = 0; k < ns; ++k) order[k] = k;
+    auto work = [&](int k) { const pj_mech &m = *sl.mech[k]; return double(m.R) * 60.0 + double(m.N + 1) * (m.N + 1); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
+    // tiles of costly models are cut to at most kTileWork of work (but whole rounds), so that the
+    // persistent loop's end is not one CTA finishing a long tile of the 360-species model
+    std::vector<BatchTile> grouped;
+    std::vector<int> first(ns + 1, 0);
+    for (int x = 0; x < ns; ++x) {
+        first[x] = int(grouped.size());
+        const long long per = std::max<long long>(1, (long long)(kTileWork / work(order[x])));
+        for (const BatchTile &t : b->tiles) {
+            if (items[t.item].pad != order[x]) continue;
+            const long long g = items[t.item].groups;
+            const long long step = std::max(g, per / g * g);
+            for (long long a = 0; a < t.count; a += step) {
+                BatchTile u = t;
+                u.begin = t.begin + a;
+                u.count = std::min(step, t.count - a);
+                grouped.push_back(u);
+            }
+        }
+    }
+    first[ns] = int(grouped.size());
+    const std::string src = batch_spec_source(jac, b->threads, sl, order, first);
     pj_batch_spec *sp = new pj_batch_spec();
     int rc = compile_and_load(src, "pj_spec_batch.cu", &sp->lib, &sp->cubin_bytes, &sp->compile_seconds, err);
-    if (rc == PJ_OK) {
-        const cudaError_t e = cudaLibraryGetKernel(&sp->kern, sp->lib, "pj_spec_batch");
+    cudaError_t e = cudaSuccess;
+    if (rc == PJ_OK && (e = cudaLibraryGetKernel(&sp->kern, sp->lib, "pj_spec_batch")) != cudaSuccess) {
+        *err = std::string("loading the specialised batch kernel failed: ") + cudaGetErrorString(e);
+        rc = PJ_ECUDA;
+    }
+    for (int k = 0; k < ns && rc == PJ_OK; ++k) {  // the slots' DevModels into constant memory
+        void *dptr = nullptr;
+        size_t bytes = 0;
+        const std::string name = "pj_slot_model" + std::to_string(k);
+        e = cudaLibraryGetGlobal(&dptr, &bytes, sp->lib, name.c_str());
+        if (e == cudaSuccess && bytes != sizeof(DevModel)) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess) e = cudaMemcpy(dptr, &sl.mech[k]->dev, sizeof(DevModel), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
-            cudaGetLastError();
-            *err = std::string("loading the specialised batch kernel failed: ") + cudaGetErrorString(e);
+            *err = "writing " + name + ": " + cudaGetErrorString(e);
             rc = PJ_ECUDA;
         }
     }
+    if (rc == PJ_OK) {                             // the kernel's static shared memory fits beside
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(sp->kern));
+        if (e == cudaSuccess && fa.sharedSizeBytes > kSpecBatchStaticSmem) {
+            *err = "the specialised batch kernel's static shared memory exceeds its reserve";
+            rc = PJ_EUNSUPPORTED;
+        } else if (e == cudaSuccess) {
+            e = cudaFuncSetAttribute(reinterpret_cast<const void *>(sp->kern),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        }
+        if (rc == PJ_OK && e != cudaSuccess) {
+            *err = std::string("specialised batch kernel attributes: ") + cudaGetErrorString(e);
+            rc = PJ_ECUDA;
+        }
+    }
+    if (rc == PJ_OK) {                             // items | tiles in one device buffer
+        const size_t o_tiles = (sizeof(BatchItem) * n + 255) & ~size_t(255);
+        const size_t bytes = o_tiles + sizeof(BatchTile) * std::max<size_t>(1, grouped.size());
+        e = cudaMalloc(&sp->dev, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(sp->dev, items.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !grouped.empty())
+            e = cudaMemcpy(static_cast<char *>(sp->dev) + o_tiles, grouped.data(), sizeof(BatchTile) * grouped.size(),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            *err = std::string("the specialised kernel's item and tile tables: ") + cudaGetErrorString(e);
+            rc = PJ_ECUDA;
+        }
+        sp->items = static_cast<BatchItem *>(sp->dev);
+        sp->tiles = reinterpret_cast<BatchTile *>(static_cast<char *>(sp->dev) + o_tiles);
+    }
     if (rc != PJ_OK) {
+        cudaGetLastError();
+        if (sp->dev) cudaFree(sp->dev);
         if (sp->lib) cudaLibraryUnload(sp->lib);
         delete sp;
         return rc;
     }
-    sp->slots = int(b->slot_mech.size());
+    sp->slots = ns;
+    sp->smem = smem;
     batch_spec_release(b);
     b->spec = sp;
     return PJ_OK;
@@ -304,6 +430,7 @@ int specialize_batch(pj_batch *b, std::string *err) {
 
 void batch_spec_release(pj_batch *b) {
     if (!b->spec) return;
+    if (b->spec->dev) cudaFree(b->spec->dev);
     if (b->spec->lib) cudaLibraryUnload(b->spec->lib);
     delete b->spec;
     b->spec = nullptr;
