@@ -284,6 +284,8 @@ int pj_mech_load(const void *buf, size_t len, pj_mech **out) {
     d.cc_wr = reinterpret_cast<const double *>(b + o_ccw);
     d.cc_col = reinterpret_cast<const int *>(b + o_ccc);
     d.rx_dnu = reinterpret_cast<const double *>(b + o_dnu);
+    d.image = b;
+    d.image_bytes = (long long)(blob.size() & ~size_t(15));
     m->dev_model = reinterpret_cast<const pj::DevModel *>(b + o_dm);
     e = cudaMemcpy(b + o_dm, &d, sizeof(d), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

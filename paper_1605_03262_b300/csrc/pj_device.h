@@ -105,6 +105,9 @@ struct DevModel {
     int cc_nnz;
     const int *cc_ptr, *cc_col;
     const double *cc_wr, *rx_dnu;
+    // the whole image (every array above lies in it): 256-byte aligned, image_bytes a multiple of 16
+    const char *image;
+    long long image_bytes;
 };
 
 // Doubles of one warp's row stage: rpc staged rows and the partial slots of split entries.
