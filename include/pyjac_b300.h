@@ -286,8 +286,9 @@ PJ_API void pj_batch_free(pj_batch *b);
  * model's sizes, shared-memory offsets and group width as compile-time constants and its device
  * pointers in constant memory; the parts run one after another (models in decreasing work per
  * state; a CTA moves to the next part when the current one has no tile left), and pj_batch_run
- * launches it; enable == 0 returns to the data-driven kernel. An item whose group width the
- * data-driven plan had to halve for shared memory runs at its model's own width where that fits,
+ * launches it; enable == 0 returns to the data-driven kernel. An item whose group width the plan
+ * chose (not the caller) and had to halve for shared memory runs at its model's own width where
+ * that fits,
  * and tiles of costly models are cut into shorter ones. Same results, bit for bit. Takes seconds
  * (one compile per plan); call it before capturing pj_batch_run into a graph. pj_batch_spec_info
  * reports whether the plan runs it, its number of parts, the compile time and code size (any

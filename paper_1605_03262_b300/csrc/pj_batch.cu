@@ -123,11 +123,15 @@ int pj_batch_create_ex(const pj_batch_item *items, int n_items, int which, const
         b.shared_const = sconst;
         cost[i] = double(m->R) * 60.0 + double(m->N + 1) * (m->N + 1);   // rough per-state work
     }
-    // tiles: consecutive states of one item, costliest first
+    // tiles: consecutive states of one item, costliest first; by default four rounds of the item's
+    // groups, but at most pj::kTileWork of work (whole rounds), so that the launch does not end on
+    // one CTA finishing a long tile of a costly model
     std::vector<pj::BatchTile> tiles;
     for (int i = 0; i < n_items; ++i) {
+        const long long g = bi[i].groups;
+        const long long by_work = std::max<long long>(g, (long long)(pj::kTileWork / cost[i]) / g * g);
         const long long ts = (item_shapes && item_shapes[i].tile_states > 0) ? item_shapes[i].tile_states
-                             : tile_req > 0 ? tile_req : 4LL * bi[i].groups;
+                             : tile_req > 0 ? tile_req : std::min(4LL * g, by_work);
         for (long long b = 0; b < items[i].n; b += ts) {
             pj::BatchTile t{};
             t.item = i;
@@ -154,6 +158,8 @@ int pj_batch_create_ex(const pj_batch_item *items, int n_items, int which, const
     }
     bt->items = bi;
     bt->tiles = tiles;
+    for (int i = 0; i < n_items; ++i)
+        bt->auto_width.push_back(!(item_shapes && item_shapes[i].warps_per_state > 0));
     bt->which = which;
     bt->device = dev;
     bt->threads = threads;

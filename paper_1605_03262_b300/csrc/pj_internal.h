@@ -124,6 +124,7 @@ struct pj_batch {
     pj::BatchParams params{};
     std::vector<pj::BatchItem> items;        // host copy; pad = the item's slot
     std::vector<pj::BatchTile> tiles;        // host copy, in the data-driven kernel's order
+    std::vector<char> auto_width;            // per item: the plan chose its group width (the caller did not)
     std::vector<const pj_mech *> slot_mech;  // per slot: its model
     std::vector<int> slot_wps;               // per slot: warps per state
     pj_batch_spec *spec = nullptr;
@@ -137,6 +138,10 @@ constexpr int kBatchSpecMaxSlots = 64;
 // counters, one of each whatever the number of slots); the item shapes of its plan leave this much
 // of the CTA's shared memory free.
 constexpr size_t kSpecBatchStaticSmem = 64;
+// Work of one batched tile at most, in the plans' per-state cost units (R * 60 + (N+1)^2): four
+// rounds of seven states of the 53-species model, about 0.4 ms (default tiles and the specialised
+// kernel's tiles; a tile length the caller sets is kept).
+constexpr double kTileWork = 6.3e5;
 
 // Group width, states per CTA and scratch of one model in a batched launch of `threads` threads
 // and `budget` bytes of dynamic shared memory per CTA: the model's configured width, halved while

@@ -183,7 +183,6 @@ static __device__ __align__(256) int g_noalloc_scratch[kNoAllocScratchInts];
 template <bool JAC>
 __global__ void __launch_bounds__(512, 1) pj_batch_noalloc_kernel(const __grid_constant__ NoAllocTable p) {
     extern __shared__ __align__(16) double smem[];
-    __shared__ DevModel s_m;
     __shared__ int s_tile, s_item;
     int cur = -1;
     for (;;) {
@@ -210,17 +209,14 @@ __global__ void __launch_bounds__(512, 1) pj_batch_noalloc_kernel(const __grid_c
         g.lane = threadIdx.x & 31;
         g.wg = g.t >> 5;
         double *S = smem + it.shared_const + size_t(g.grp) * it.sc.total;
+        const DevModel *__restrict__ mp = it.m;       // read in place (see pj_batch_kernel)
         if (item != cur) {
-            const int *src = reinterpret_cast<const int *>(it.m);
-            int *dst = reinterpret_cast<int *>(&s_m);
-            for (int w = threadIdx.x; w < int(sizeof(DevModel) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
-            __syncthreads();
-            load_model_consts(s_m, smem);
-            if (g.grp < it.groups) init_neutral<JAC>(s_m, it.sc, S, g.t);
+            load_model_consts(*mp, smem);
+            if (g.grp < it.groups) init_neutral<JAC>(*mp, it.sc, S, g.t);
             cur = item;
             __syncthreads();
         }
-        run_tile<JAC>(s_m, it, smem, begin, end, g);
+        run_tile<JAC>(*mp, it, smem, begin, end, g);
         __syncthreads();
     }
 }

@@ -285,17 +285,12 @@ int specialize(pj_mech *m, std::string *err) {
 }
 
 // Compiles and loads the kernel of a batched plan specialised for its models. Its item table is
-// the plan's, except that an item whose group width the data-driven plan had to halve gets its
-// model's own width back where the working set fits: the data-driven batched kernel keeps a
-// DevModel (432 bytes) in static shared memory, which left the 360-species model's 16-warp
-// working set no room, and at 8 warps per state that model ran 1.45 x the plain kernel's time.
-// Tiles are grouped by slot (slots in decreasing work per state, so that the last part has the
-// finest tiles; within a slot, the plan's order). Items and tiles are uploaded to device memory of
-// the specialisation's own.
-// Work (the plan's per-state cost units) of one tile of the specialised kernel at most: four rounds
-// of seven states of the 53-species model, about 0.4 ms.
-constexpr double kTileWork = 6.3e5;
-
+// the plan's, except that an item whose group width the data-driven plan chose and had to halve
+// gets its model's own width back where the working set fits beside this kernel's smaller static
+// shared memory (a width the caller set is kept; at 8 instead of 16 warps per state the
+// 360-species model ran 1.45 x the plain kernel's time). Tiles are grouped by slot (slots in decreasing work per state,
+// so that the last part has the finest tiles; within a slot, the plan's order). Items and tiles
+// are uploaded to device memory of the specialisation's own.
 int specialize_batch(pj_batch *b, std::string *err) {
     const bool jac = b->which == 0;
     const int n = int(b->items.size());
@@ -313,7 +308,7 @@ int specialize_batch(pj_batch *b, std::string *err) {
         BatchItem &it = items[i];
         const pj_mech *m = b->slot_mech[it.pad];
         const int w = (jac ? m->jac_cfg : m->dydt_cfg).wps;
-        if (w > it.wps && w * 32 <= b->threads) {
+        if (b->auto_width[i] && w > it.wps && w * 32 <= b->threads) {
             const Scratch sc = make_scratch(m->dev, jac, w);
             int gmax = b->threads / (32 * w);
             if (w > 1) gmax = std::min(gmax, 15);

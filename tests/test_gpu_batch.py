@@ -128,6 +128,33 @@ def test_specialised_batch_kernel_equals_plain_launches(which):
     assert not plan.specialize(False)["active"]
 
 
+def test_specialised_plan_with_chosen_widths_and_an_empty_item():
+    """Widths left to the plan (the 360-species model's among them, which the specialised kernel
+    may widen to the model's own), an item without states between others, a tile table cut into
+    shorter tiles for the costly models: the specialised plan still gives the plain launches'
+    bits, and a plan that runs only the data-driven kernel gives the same."""
+    import paper_1605_03262_b300 as pj
+    items = _items(seed=17)
+    for g, _, _, _ in items:
+        g.specialize()                                  # the models' own widths, as a server has them
+    g1, T1, P1, Y1 = items[1]
+    items.insert(2, (g1, T1[:0], P1[:0], Y1[:0]))       # no states
+    outs = _jac_items(items)
+    plan_items = [(g, T, P, Y, J) for (g, T, P, Y), (J, f) in zip(items, outs)]
+    plan = pj.BatchPlan(plan_items, tile_states=64)
+    refs = [g.eval_jacobian(T, P, Y) for g, T, P, Y in items]
+    plan.run()
+    torch.cuda.synchronize()
+    for (J, _), ref in zip(outs, refs):
+        assert torch.equal(J, ref)
+        J.fill_(float("nan"))
+    assert plan.specialize()["active"]
+    plan.run()
+    torch.cuda.synchronize()
+    for (J, _), ref in zip(outs, refs):
+        assert torch.equal(J, ref)
+
+
 def test_batch_autotuner_picks_a_timed_candidate_and_keeps_results():
     import paper_1605_03262_b300 as pj
     from paper_1605_03262_b300 import autotune
