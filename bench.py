@@ -1172,6 +1172,43 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# the autotuner's launch shapes of the four models (warps per state, states per CTA, CTAs per SM),
+# fixed for profiling runs so that no tuning launches precede the profiled one
+TUNED_SHAPES = {0: (1, 8, 2), 1: (2, 7, 1), 2: (4, 3, 1), 3: (16, 1, 1)}
+
+
+def run_profile_batch(warmup: int, data_driven: bool = False):
+    """--profile-batch -- the batched form for ncu: the 64 small requests of the benchmark's batched
+    form (16-1,024 states each over the four models) as one plan of 512-thread CTAs with default
+    tiles, its kernel specialised for the plan (--data-driven: the data-driven batched kernel);
+    warm-up launches, then the profiled one."""
+    import torch
+    import paper_1605_03262_b300 as pj
+    torch.cuda.set_device(0)
+    models = []
+    for cfg in (0, 1, 2, 3):
+        g = pj.Model(synth.to_bytes(synth.config_model(cfg)))
+        g.set_launch(*TUNED_SHAPES[cfg])
+        models.append(g)
+    rng = np.random.default_rng(17)
+    items = []
+    for x in range(64):
+        g = models[x % 4]
+        n = int(np.exp(rng.uniform(np.log(16), np.log(1024))))
+        N = g.n_species
+        T, P, Y = synth.generate_states(N, n, seed=3000 + x)
+        Td, Pd, Yd = (torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in (T, P, Y))
+        items.append((g, Td, Pd, Yd, torch.empty((n, N + 1, N + 1), dtype=torch.float64, device="cuda")))
+    plan = pj.BatchPlan(items, threads_per_cta=512)
+    if not data_driven:
+        plan.specialize()
+    for _ in range(warmup + 1):
+        plan.run()
+    torch.cuda.synchronize()
+    print("profile case done: batched form, 64 requests, %d tiles, %s kernel" %
+          (plan.n_tiles, "data-driven" if data_driven else "specialised"))
+
+
 def run_profile_case(spec: str, warmup: int, data_driven: bool = False, conc: bool = False, dydt: bool = False):
     """--profile CFG:N[:WPS,GROUPS[,CTAS]] -- a small case for ncu: warm-up launches, then one Jacobian
     launch of the first N states of configuration CFG (inputs larger than L2 once N is a few
@@ -1233,6 +1270,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference comparison")
     ap.add_argument("--profile", default=None, metavar="CFG:N[:WPS,GROUPS[,CTAS]]", help="one small profiling case (for ncu)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="one batched launch of 64 small requests over the four models (for ncu)")
     ap.add_argument("--data-driven", action="store_true", help="with --profile: the data-driven kernel")
     ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
     ap.add_argument("--dydt", action="store_true", help="with --profile: the source-term kernel")
@@ -1244,6 +1283,8 @@ def main():
     args = ap.parse_args()
     if args.profile:
         return run_profile_case(args.profile, args.warmup, args.data_driven, args.conc, args.dydt)
+    if args.profile_batch:
+        return run_profile_batch(args.warmup, args.data_driven)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
