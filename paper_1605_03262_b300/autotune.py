@@ -196,7 +196,7 @@ def autotune_batch(items, which: str = "jacobian", specialise: bool = True, reps
     The choice is cached by the mix's shape (models' sizes and launch shapes, log2 of each item's
     state count)."""
     import torch
-    from . import BatchPlan
+    from . import BatchPlan, LibraryError
     key = _mix_key(items, which)
     cands = candidates if candidates is not None else batch_candidates(items, which)
     hit = None
@@ -234,15 +234,19 @@ def autotune_batch(items, which: str = "jacobian", specialise: bool = True, reps
         else:
             plan.close()
     choice = next(c for c in cands if "%d threads, %d rounds per tile" % (c["threads_per_cta"], c["rounds"]) == best)
-    spec_ms = None
+    spec_ms, spec_error = None, None
     use_spec = bool(hit[2]) if hit and len(hit) > 2 else None
     if specialise and use_spec is not False:
-        best_plan.specialize()
-        spec_ms = time_plan(best_plan)
-        if use_spec is None:
-            use_spec = spec_ms < timings[best]
-        if not use_spec:
-            best_plan.specialize(False)
+        try:
+            best_plan.specialize()
+        except LibraryError as exc:     # NVRTC missing, or a plan it cannot specialise: data-driven
+            spec_error, use_spec = str(exc), False
+        else:
+            spec_ms = time_plan(best_plan)
+            if use_spec is None:
+                use_spec = spec_ms < timings[best]
+            if not use_spec:
+                best_plan.specialize(False)
     del flush
     if use_cache:
         with _lock:
@@ -250,5 +254,5 @@ def autotune_batch(items, which: str = "jacobian", specialise: bool = True, reps
             cache[key] = [choice["threads_per_cta"], choice["rounds"], bool(use_spec)]
             _store_cache(cache)
     return best_plan, {"choice": best, "ms": spec_ms if use_spec else timings[best], "timings": timings,
-                       "specialised_ms": spec_ms, "item_shapes": choice["item_shapes"],
+                       "specialised_ms": spec_ms, "specialise_error": spec_error, "item_shapes": choice["item_shapes"],
                        "specialised": best_plan.spec_info()}
