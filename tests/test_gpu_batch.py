@@ -99,7 +99,7 @@ def _jac_items(items):
 
 @pytest.mark.parametrize("which", ["jacobian", "dydt"])
 def test_specialised_batch_kernel_equals_plain_launches(which):
-    """The plan's kernel compiled for its models (NVRTC; one branch per (model, group width)) gives
+    """The plan's kernel compiled for its models (NVRTC; one part per (model, group width)) gives
     the plain per-model results bit for bit, with per-item shapes, also from a graph."""
     import paper_1605_03262_b300 as pj
     items = _items(seed=11)
