@@ -1043,10 +1043,9 @@ def compact_forms(batched, serving, dyf, cvf, fd, concf) -> dict:
 
 
 def detail_path(args):
-    if args.detail:
-        return args.detail
-    d = os.path.join(os.getcwd(), "gpurun_out")
-    return os.path.join(d, "bench_detail.json") if os.path.isdir(d) else None
+    """Where the full measurement records go: --detail, else bench_detail.json in the working
+    directory."""
+    return args.detail if args.detail else os.path.join(os.getcwd(), "bench_detail.json")
 
 
 def run_ours(args):
@@ -1294,8 +1293,8 @@ def main():
     ap.add_argument("--conc", action="store_true", help="with --profile: the molar-concentration basis kernel")
     ap.add_argument("--dydt", action="store_true", help="with --profile: the source-term kernel")
     ap.add_argument("--detail", default=None, metavar="PATH",
-                    help="file for the full measurement records (default gpurun_out/bench_detail.json if that "
-                         "directory exists)")
+                    help="file for the full measurement records (default: bench_detail.json in the working "
+                         "directory)")
     ap.add_argument("--launch", default=None, metavar="WPS,GROUPS,CTAS",
                     help="fixed launch shape of the headline model (skips the autotuner, e.g. for ncu runs)")
     args = ap.parse_args()
