@@ -27,9 +27,9 @@ result is bitwise the unchunked one. A request that has started holds its device
 its last chunk, so when the head of the queue waits for memory, the started requests behind it
 still get their chunks (they are what frees the memory).
 
-The scheduler thread, not the GPU, bounds the throughput of small requests: an iteration costs it
-0.3-0.5 ms of host time (packing inputs into pinned staging, allocations, the launch), so on the
-four-model trace the GPU is about half busy at 1,600 requests/s.
+An iteration costs the scheduler thread 0.3-0.5 ms of host time (packing inputs into pinned
+staging, allocations, the launch): on the four-model trace at 1,600 requests/s the thread is about
+half busy and the GPU a little less.
 
 Model images stay resident for the server's lifetime. Each request's latency is measured from
 :meth:`submit` to the completion event of its iteration (results in device memory), and, with
@@ -51,7 +51,7 @@ __all__ = ["Server", "Request"]
 
 class Request:
     __slots__ = ("rid", "name", "T", "P", "Y", "n", "t_submit", "t_done", "future", "dydt", "chunks", "next",
-                 "left", "dev", "out", "host", "bytes", "ready", "queued")
+                 "left", "out", "host", "bytes", "ready", "queued")
 
     def __init__(self, rid, name, T, P, Y, dydt, t_submit):
         self.rid, self.name, self.T, self.P, self.Y = rid, name, T, P, Y
@@ -63,10 +63,18 @@ class Request:
         self.chunks = None        # state ranges of a chunked request, else None
         self.next = 0             # next chunk to admit
         self.left = 0             # chunks not yet completed
-        self.dev = self.out = self.host = None   # device inputs, device outputs, host outputs
+        self.out = self.host = None   # device outputs, host outputs (chunked requests)
         self.bytes = 0
         self.ready = None         # event: the request's inputs are on the device (chunked requests)
         self.queued = True        # False once a merged launch has taken it
+
+
+class _Slice:
+    """States [a, b) of a request, as the input staging reads a request."""
+    __slots__ = ("n", "T", "P", "Y")
+
+    def __init__(self, r, a, b):
+        self.n, self.T, self.P, self.Y = b - a, r.T[a:b], r.P[a:b], r.Y[a:b]
 
 
 class _Iteration:
@@ -323,7 +331,7 @@ class Server:
                         if self.host_results:
                             J, F = J.numpy(), F.numpy() if F is not None else None
                         r.future.set_result((J, F) if r.dydt else J)
-                    r.dev = r.out = r.host = r.ready = None
+                    r.out = r.host = r.ready = None
                     self._held -= r.bytes
                 self._free_streams.append(it.stream)
                 continue
@@ -434,7 +442,9 @@ class Server:
 
     def _admit_chunk(self, r: Request, model) -> None:
         """One chunk of a chunked request on a free stream, into its slice of the request's output
-        (inputs and outputs of the whole request are allocated at its first chunk)."""
+        (allocated, for the whole request, at its first chunk). Each chunk stages and copies only
+        its own inputs, so that the first chunk of a large request does not hold the scheduler
+        for the copy of all of them."""
         torch = self.torch
         a, b = r.chunks[r.next]
         it = _Iteration()
@@ -445,7 +455,6 @@ class Server:
             if r.next == 0:
                 r.bytes = self._bytes(model, r.n)
                 self._held += r.bytes
-                r.dev = self._inputs_for(it, [r], N)
                 J = torch.empty((r.n, N + 1, N + 1), dtype=torch.float64, device=self.device)
                 F = torch.empty((r.n, N + 1), dtype=torch.float64, device=self.device) if r.dydt else None
                 r.out = (J, F)
@@ -453,13 +462,13 @@ class Server:
                     r.host = (torch.empty((r.n, N + 1, N + 1), dtype=torch.float64, pin_memory=True),
                               torch.empty((r.n, N + 1), dtype=torch.float64, pin_memory=True) if r.dydt else None)
                 r.ready = torch.cuda.Event()
-                r.ready.record(it.stream)                  # the inputs are on the device
+                r.ready.record(it.stream)                  # the outputs' memory is this stream's
                 self.stats["chunked_requests"] += 1
             else:
                 it.stream.wait_event(r.ready)             # later chunks run on other streams
-            T, P, Y = r.dev
+            T, P, Y = self._inputs_for(it, [_Slice(r, a, b)], N)
             J, F = r.out
-            self._launch(model, T[a:b], P[a:b], Y[a:b], J[a:b], F[a:b] if F is not None else None, it.stream)
+            self._launch(model, T, P, Y, J[a:b], F[a:b] if F is not None else None, it.stream)
             if self.host_results:
                 if self.discard_results:                  # the copy counts, its result is dropped
                     self._copy_to_host(it.stream, J[a:b])
