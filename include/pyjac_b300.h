@@ -282,18 +282,17 @@ PJ_API void pj_batch_free(pj_batch *b);
 /*
  * The plan's kernel specialised for its models (the per-mechanism code generation of Sections 4
  * and 6, as pj_mech_specialize, for a mixed batch): enable != 0 compiles with NVRTC one persistent
- * kernel in which every distinct (model, warps per state) pair of the plan is a part with that
- * model's sizes, shared-memory offsets and group width as compile-time constants and its device
- * pointers in constant memory; the parts run one after another (models in decreasing work per
- * state; a CTA moves to the next part when the current one has no tile left), and pj_batch_run
- * launches it; enable == 0 returns to the data-driven kernel. An item whose group width the plan
- * chose (not the caller) and had to halve for shared memory runs at its model's own width where
- * that fits,
- * and tiles of costly models are cut into shorter ones. Same results, bit for bit. Takes seconds
- * (one compile per plan); call it before capturing pj_batch_run into a graph. pj_batch_spec_info
- * reports whether the plan runs it, its number of parts, the compile time and code size (any
- * output may be NULL). Errors as pj_mech_specialize, and PJ_EUNSUPPORTED for a plan of more than
- * 64 (model, width) pairs.
+ * kernel in which every distinct (model, warps per state, states per round) triple of the plan is
+ * a part with that model's sizes, shared-memory offsets, group width and states per round as
+ * compile-time constants and its device pointers in constant memory; the parts run one after
+ * another (models in decreasing work per state; a CTA moves to the next part when the current one
+ * has no tile left), and pj_batch_run launches it; enable == 0 returns to the data-driven kernel.
+ * An item whose group width the plan chose (not the caller) and had to halve for shared memory
+ * runs at its model's own width where that fits, and tiles of costly models are cut into shorter
+ * ones. Same results, bit for bit. Takes seconds (one compile per plan); call it before capturing
+ * pj_batch_run into a graph. pj_batch_spec_info reports whether the plan runs it, its number of
+ * parts, the compile time and code size (any output may be NULL). Errors as pj_mech_specialize,
+ * and PJ_EUNSUPPORTED for a plan of more than 64 such parts.
  */
 PJ_API int pj_batch_specialize(pj_batch *b, int enable);
 PJ_API int pj_batch_spec_info(const pj_batch *b, int *active, int *slots, double *compile_seconds,

@@ -1430,8 +1430,8 @@ __device__ __forceinline__ void run_tile_spec(const BatchItem *itp, long long be
     g.t = threadIdx.x - g.grp * g.G;
     g.lane = threadIdx.x & 31;
     g.wg = g.t >> 5;
-    const int groups = it.groups;
-    double *S0 = smem + it.shared_const;
+    const int groups = Spec::kGroups;                   // the slot's states per round, as a constant
+    double *S0 = smem + Spec::kSharedConst;
     double *S = S0 + size_t(g.grp) * sc.total;
     const bool member = g.grp < groups;
     if (fresh) {
@@ -1439,7 +1439,7 @@ __device__ __forceinline__ void run_tile_spec(const BatchItem *itp, long long be
         if (member) init_neutral<JAC>(m, sc, S, g.t);
         __syncthreads();
     }
-    const StateIO io = it.io;
+    const StateIO &io = it.io;            // read in place (a local copy cost the mix 1.7 %)
     for (long long base = begin; base < end; base += groups) {
         const int gact = int(min((long long)groups, end - base));
         eval_state<JAC, WPS>(m, sc, S, smem, io, base + g.grp, g, member && g.grp < gact, gact, S0, sc.total);

@@ -202,10 +202,11 @@ int nvrtc_compile(const NvrtcApi &api, const std::string &src, const char *name,
     return PJ_OK;
 }
 
-// Slots of a batched plan's specialised kernel: the distinct (model, warps per state) pairs.
+// Slots of a batched plan's specialised kernel: the distinct (model, warps per state, states per
+// round) triples.
 struct SpecSlots {
     std::vector<const pj_mech *> mech;
-    std::vector<int> wps;
+    std::vector<int> wps, groups;
 };
 
 // Source of a batched plan's specialised kernel: per slot a Spec type with the model's sizes and
@@ -237,6 +238,8 @@ std::string batch_spec_source(bool jac, int threads, const SpecSlots &sl, const 
             pos = e + 1;
         }
         s += "struct Slot" + std::to_string(k) + " {\n" + wrapped +
+             "    static constexpr int kGroups = " + std::to_string(sl.groups[k]) +
+             ", kSharedConst = " + std::to_string(shared_const_doubles(m.N)) + ";\n"
              "    static __device__ __forceinline__ const pj::DevModel &dev() { return pj_slot_model" +
              std::to_string(k) + "; }\n};\n";
     }
@@ -322,17 +325,18 @@ int specialize_batch(pj_batch *b, std::string *err) {
         smem = std::max(smem, (size_t(it.shared_const) + size_t(it.sc.total) * it.groups) * 8);
         int slot = -1;
         for (size_t k = 0; k < sl.mech.size(); ++k)
-            if (sl.mech[k] == m && sl.wps[k] == it.wps) slot = int(k);
+            if (sl.mech[k] == m && sl.wps[k] == it.wps && sl.groups[k] == it.groups) slot = int(k);
         if (slot < 0) {
             slot = int(sl.mech.size());
             sl.mech.push_back(m);
             sl.wps.push_back(it.wps);
+            sl.groups.push_back(it.groups);
         }
         it.pad = slot;
     }
     const int ns = int(sl.mech.size());
     if (ns > kBatchSpecMaxSlots) {
-        *err = "the plan has more than " + std::to_string(kBatchSpecMaxSlots) + " (model, group width) slots";
+        *err = "the plan has more than " + std::to_string(kBatchSpecMaxSlots) + " parts ((model, group width, states per round) triples)";
         return PJ_EUNSUPPORTED;
     }
     std::vector<int> order(ns);
