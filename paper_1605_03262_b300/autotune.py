@@ -159,8 +159,8 @@ def autotune(model, blob: bytes, which: str = "jacobian", probe: Optional[Sequen
 # the batched form: one persistent launch over items of several models
 
 def batch_candidates(items, which: str = "jacobian") -> List[dict]:
-    """Candidate plans for a batched launch: CTA sizes (512, 448 or 384 threads) and tiles of 2, 4, 8
-    or 16 rounds of each item's states per CTA (states per CTA from the model's tuned launch shape;
+    """Candidate plans for a batched launch: CTA sizes (512, 448 or 384 threads) and tiles of 1, 2, 4,
+    8 or 16 rounds of each item's states per CTA (states per CTA from the model's tuned launch shape;
     the group width is the model's, halved by the library where a state does not fit the CTA, so
     that the candidates of one CTA size share one specialised kernel)."""
     out = []
@@ -169,7 +169,7 @@ def batch_candidates(items, which: str = "jacobian") -> List[dict]:
         for it in items:
             wps, groups, _ = it[0].get_launch(which)
             base.append(max(1, min(groups, threads // (32 * wps))))
-        for rounds in (2, 4, 8, 16):
+        for rounds in (1, 2, 4, 8, 16):
             # width 0: the model's own, halved by the library while a state does not fit the CTA
             out.append({"threads_per_cta": threads, "rounds": rounds,
                         "item_shapes": [(0, g, rounds * g) for g in base]})
@@ -187,12 +187,16 @@ def _mix_key(items, which: str) -> str:
     return "batch|%s|%s|%s" % (torch.cuda.get_device_name(items[0][0].device), which, ";".join(parts))
 
 
+TOP = 2   # batched candidates specialised after the data-driven ranking
+
+
 def autotune_batch(items, which: str = "jacobian", specialise: bool = True, reps: int = 3,
                    use_cache: bool = True, candidates: Optional[List[dict]] = None):
     """Choose the batched launch's CTA size and per-item tile sizes for this item mix by timing
     candidate plans on the data-driven batched kernel (each run after a write larger than L2;
-    median of ``reps``), then, with ``specialise``, the fastest candidate again with its kernel
-    specialised for the mix's models (NVRTC), keeping whichever is faster. Returns (plan, report).
+    median of ``reps``), then, with ``specialise``, the ``TOP`` fastest candidates again with their
+    kernels specialised for the mix's models (NVRTC), keeping the fastest plan of all. Returns
+    (plan, report).
     The choice is cached by the mix's shape (models' sizes and launch shapes, log2 of each item's
     state count)."""
     import torch
@@ -222,31 +226,47 @@ def autotune_batch(items, which: str = "jacobian", specialise: bool = True, reps
         torch.cuda.synchronize()
         return float(np.median([s.elapsed_time(e) for s, e in ev]))
 
-    timings, best, best_plan = {}, None, None
+    def name_of(c):
+        return "%d threads, %d rounds per tile" % (c["threads_per_cta"], c["rounds"])
+
+    timings, kept = {}, []                  # kept: the TOP fastest (time, candidate, plan)
     for c in cands:
         plan = BatchPlan(items, which=which, threads_per_cta=c["threads_per_cta"], item_shapes=c["item_shapes"])
-        name = "%d threads, %d rounds per tile" % (c["threads_per_cta"], c["rounds"])
-        timings[name] = time_plan(plan)
-        if best is None or timings[name] < timings[best]:
-            if best_plan is not None:
-                best_plan.close()
-            best, best_plan = name, plan
-        else:
-            plan.close()
-    choice = next(c for c in cands if "%d threads, %d rounds per tile" % (c["threads_per_cta"], c["rounds"]) == best)
+        timings[name_of(c)] = time_plan(plan)
+        kept.append((timings[name_of(c)], len(kept), c, plan))
+        kept.sort(key=lambda x: (x[0], x[1]))
+        for _, _, _, p in kept[TOP:]:
+            p.close()
+        kept = kept[:TOP]
+    best_ms, _, choice, best_plan = kept[0]
+    best = name_of(choice)
     spec_ms, spec_error = None, None
     use_spec = bool(hit[2]) if hit and len(hit) > 2 else None
     if specialise and use_spec is not False:
-        try:
-            best_plan.specialize()
-        except LibraryError as exc:     # NVRTC missing, or a plan it cannot specialise: data-driven
-            spec_error, use_spec = str(exc), False
-        else:
-            spec_ms = time_plan(best_plan)
+        # the kept candidates again with their kernels specialised (the ranking can change)
+        spec_times = []
+        for _, _, c, plan in kept:
+            try:
+                plan.specialize()
+            except LibraryError as exc:  # NVRTC missing, or a plan it cannot specialise: data-driven
+                spec_error = str(exc)
+                break
+            spec_times.append((time_plan(plan), c, plan))
+        if spec_times:
+            s_ms, s_c, s_plan = min(spec_times, key=lambda x: x[0])
             if use_spec is None:
-                use_spec = spec_ms < timings[best]
-            if not use_spec:
-                best_plan.specialize(False)
+                use_spec = s_ms < best_ms
+            if use_spec:
+                choice, best, best_plan, spec_ms = s_c, name_of(s_c), s_plan, s_ms
+            else:
+                spec_ms = spec_times[0][0]          # the fastest data-driven candidate's, specialised
+        else:
+            use_spec = False
+        if not use_spec:
+            best_plan.specialize(False)
+    for _, _, _, plan in kept:
+        if plan is not best_plan:
+            plan.close()
     del flush
     if use_cache:
         with _lock:
